@@ -1,0 +1,473 @@
+"""Hybrid compressible LBM time step, plain numpy FP64 (oracle).
+
+Implements, in the paper's order and notation:
+  * Eq. LB   pull-form lattice Boltzmann update with the shifted variable f-bar
+  * Eq. fi   Guo-type force populations with the Hermite force moment a^{F,(2)}
+  * Eq. feq  thermal equilibrium with the (w_i - delta_0i) rho (theta-1) term
+  * Eq. fneq / pi2 / pi3   hybrid recursive regularized off-equilibrium
+  * Eq. energy / deltata / fluxx-z / linear   total-energy equation with
+    LB-consistent mass and momentum fluxes and MUSCL-Hancock face values
+  * Sec. 2.5 steps 1-5 (IB forcing from oracle.ib, then LBM + energy)
+
+Arrays are stored with the x axis last: a field has shape (ny, nx) in 2D and
+(nz, ny, nx) in 3D; populations have a leading Q axis, vectors a leading D
+axis.  Lattice units dx = dt = 1, c_s^2 = 1/3, T_ref = 1 (so theta = T and
+R = c_s^2).
+
+Readings where the paper is silent or garbled (each also listed in the
+design notes of the repository):
+  Q3  third-order Hermite terms use the orthogonal projection 1/N_k with
+      N_k = sum_i w_i H3r_k,i^2 (2 c_s^6 for the '+' and 6 c_s^6 for the '-'
+      D3Q19 combinations) in place of the printed single 1/(6 c_s^6).
+  Q4  the trace projection in Eq. pi2 uses delta/D (delta/3 in 3D as printed).
+  Q6  a^C (Eq. af2, only cited): with m = rho (1 - theta) u,
+      a^C_ab = c_s^2 [d_b m_a + d_a m_b - (2/D) d_ab div m] - d_ab d_a(rho u_a^3),
+      the divergence of the defect of the equilibrium third moment with
+      respect to the Maxwellian at temperature theta, less the trace that the
+      explicit delta_ab terms of Eq. af2 already carry.  PARITY UNPINNED
+      against the paper; pinned by physics tests (shear viscosity equals mu
+      at theta != 1 and in a moving frame).
+  Q7  spatial derivatives are 2nd-order central; time derivative of
+      rho(1-theta) is the backward difference with the stored previous value.
+  Q8  the F_i(t - dt) term of Eq. pi2 enters through its traceless second
+      moment, the stored deviator of a^F of the previous step.
+  Q9  tau_LB = mu / (rho c_s^2 theta) ("theta-scaled", default) or
+      mu / (rho c_s^2) ("literal", Eq. LB); the finite-difference part of
+      Eq. pi2 uses rho c_s^2 theta^m tau-bar with the same m, so that it is
+      the Chapman-Enskog estimate -tau-bar p S of the f-bar stress.
+  Q12 face values of h, k and u_beta in the energy flux are the arithmetic
+      mean of the two cells sharing the face.
+  Q14 no limiter; sign(0) = 0; u_alpha ~ = 0 takes the '+' branch; the
+      velocity in the face value and in eta is the reconstructing cell's.
+  Q15 the IB energy forcing f_E = w + q is added once to rho E before the
+      fluxes are formed.
+  Q24 far field: inlet and far-field faces are reset to the free-stream
+      equilibrium, the outlet is a zero-gradient copy; stencil reads
+      outside a non-periodic axis are clamped to the edge node.
+"""
+import numpy as np
+
+from . import lattice as L
+from . import ib as IB
+
+CS2 = L.CS2
+
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD = 0, 1, 2, 3
+TAU_THETA, TAU_LITERAL = 0, 1
+
+
+def theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, dim):
+    """Q11: T_ref is free (App. A: it sets the CFL number); theta_inf = T_inf/T_ref
+    is the largest value <= 1 that keeps (a) u_inf = Ma sqrt(gamma c_s^2 theta)
+    <= 0.35 and (b) the explicit conduction number kappa = lambda/(rho C_v)
+    = mu gamma / Pr <= KAPPA_MAX[dim] (mu = u_inf L / Re scales with sqrt(theta))."""
+    u1 = mach * np.sqrt(gamma * CS2)
+    k1 = (u1 * ref_length / reynolds) * gamma / prandtl
+    th = 1.0
+    if u1 > 0.35:
+        th = min(th, (0.35 / u1) ** 2)
+    if k1 > KAPPA_MAX[dim]:
+        th = min(th, (KAPPA_MAX[dim] / k1) ** 2)
+    return th
+
+
+KAPPA_MAX = {2: 0.10, 3: 0.0667}
+
+
+class Params:
+    """Physical and numerical parameters, derived as in Sec. 3 / Q10-Q11.
+
+    Re = rho_inf u_inf L / mu (Sec. 2.4), Ma = u_inf / c_inf with
+    c_inf = sqrt(gamma R T_inf); Pr fixes lambda = mu C_p / Pr; C_v = R/(gamma-1).
+    """
+
+    def __init__(self, lattice, shape, mach, reynolds, ref_length, prandtl=0.71,
+                 gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98,
+                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_THETA, use_ac=True, mu=None):
+        self.lat = L.get(lattice)
+        D = self.lat.D
+        self.shape = tuple(int(s) for s in shape)  # (nx, ny[, nz])
+        assert len(self.shape) == D
+        self.gamma = gamma
+        self.R = CS2
+        self.Cv = self.R / (gamma - 1.0)
+        self.Cp = gamma * self.R / (gamma - 1.0)
+        self.theta_inf = (theta_inf if theta_inf > 0 else
+                          theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, D))
+        self.rho_inf = 1.0
+        c_inf = np.sqrt(gamma * self.R * self.theta_inf)
+        self.u_mag = mach * c_inf
+        d = np.array(inflow_dir[:D], dtype=np.float64)
+        d = d / np.sqrt((d * d).sum())
+        self.u_inf = self.u_mag * d
+        self.mu = self.rho_inf * self.u_mag * ref_length / reynolds if mu is None else float(mu)
+        self.lam = self.mu * self.Cp / prandtl
+        self.sigma = sigma
+        self.d_n = d_n
+        self.method = method
+        self.tau_mode = tau_mode
+        self.use_ac = use_ac
+        if bc is None:
+            bc = [BC_PERIODIC] * (2 * D)
+        self.bc = list(bc)[: 2 * D]
+        self.ref_length = ref_length
+
+
+# --------------------------------------------------------------------------
+# neighbour access with periodic wrap or edge clamping per axis
+# --------------------------------------------------------------------------
+class Grid:
+    def __init__(self, prm):
+        self.D = prm.lat.D
+        self.n = prm.shape  # (nx, ny, nz)
+        self.periodic = [prm.bc[2 * a] == BC_PERIODIC for a in range(self.D)]
+
+    def idx(self, a, off):
+        n = self.n[a]
+        i = np.arange(n) + off
+        if self.periodic[a]:
+            return np.mod(i, n)
+        return np.clip(i, 0, n - 1)
+
+    def at(self, field, off):
+        """field evaluated at x + off (off = (dx, dy[, dz])); field has the
+        grid as its trailing axes (x last)."""
+        D = self.D
+        out = field
+        for a in range(D):
+            if off[a] == 0:
+                continue
+            out = np.take(out, self.idx(a, off[a]), axis=out.ndim - 1 - a)
+        return out
+
+    def unit(self, a, s=1):
+        o = [0] * self.D
+        o[a] = s
+        return tuple(o)
+
+
+# --------------------------------------------------------------------------
+# equilibrium, forcing, regularized collision
+# --------------------------------------------------------------------------
+def equilibrium(lat, rho, u, theta):
+    """Eq. feq: f^eq_i = w_i [rho + (w_i - d_0i)/w_i rho (theta - 1)
+    + H1.rho u / c_s^2 + H2:rho u u / (2 c_s^4) + sum_k H3r_k A_k / N_k],
+    with A_k the H3r combinations of rho u_a u_b u_g (reading Q3)."""
+    D, Q = lat.D, lat.Q
+    c = lat.c.astype(np.float64)
+    feq = np.empty((Q,) + rho.shape)
+    T3 = [[[rho * u[a] * u[b] * u[g] for g in range(D)] for b in range(D)] for a in range(D)]
+    A = lat.combo3(T3)
+    for i in range(Q):
+        wi = lat.w[i]
+        t0 = rho
+        tth = ((wi - (1.0 if i == 0 else 0.0)) / wi) * rho * (theta - 1.0)
+        t1 = sum(c[i, a] * rho * u[a] for a in range(D)) / CS2
+        t2 = 0.0
+        for a in range(D):
+            for b in range(D):
+                t2 = t2 + lat.H2(a, b)[i] * rho * u[a] * u[b]
+        t2 = t2 / (2.0 * CS2 * CS2)
+        t3 = 0.0
+        for k in range(len(A)):
+            t3 = t3 + lat.H3r[k, i] * A[k] / lat.N3r[k]
+        feq[i] = wi * (t0 + tth + t1 + t2 + t3)
+    return feq
+
+
+def force_populations(lat, fu, aF):
+    """Eq. fi: F_i = w_i [H1_a f_u,a / c_s^2 + H2_ab a^F_ab / (2 c_s^4)]."""
+    D, Q = lat.D, lat.Q
+    c = lat.c.astype(np.float64)
+    F = np.empty((Q,) + fu.shape[1:])
+    for i in range(Q):
+        t1 = sum(c[i, a] * fu[a] for a in range(D)) / CS2
+        t2 = 0.0
+        for a in range(D):
+            for b in range(D):
+                t2 = t2 + lat.H2(a, b)[i] * aF[a][b]
+        F[i] = lat.w[i] * (t1 + t2 / (2.0 * CS2 * CS2))
+    return F
+
+
+def regularized_neq(lat, u, Pi):
+    """Eq. fneq with Eq. pi3: f-bar^neq_i = w_i [H2:Pi/(2 c_s^4)
+    + sum_k H3r_k A_k^neq / N_k], A^neq = combos of
+    Pi3_abg = u_a Pi_bg + u_b Pi_ga + u_g Pi_ab."""
+    D, Q = lat.D, lat.Q
+    T3 = [[[u[a] * Pi[b][g] + u[b] * Pi[g][a] + u[g] * Pi[a][b] for g in range(D)]
+           for b in range(D)] for a in range(D)]
+    A = lat.combo3(T3)
+    out = np.empty((Q,) + u.shape[1:])
+    for i in range(Q):
+        t2 = 0.0
+        for a in range(D):
+            for b in range(D):
+                t2 = t2 + lat.H2(a, b)[i] * Pi[a][b]
+        t2 = t2 / (2.0 * CS2 * CS2)
+        t3 = 0.0
+        for k in range(len(A)):
+            t3 = t3 + lat.H3r[k, i] * A[k] / lat.N3r[k]
+        out[i] = lat.w[i] * (t2 + t3)
+    return out
+
+
+def deviator(lat, T):
+    D = lat.D
+    tr = sum(T[a][a] for a in range(D))
+    return [[T[a][b] - (tr / D if a == b else 0.0) for b in range(D)] for a in range(D)]
+
+
+def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
+    """Sec. 2.2 / App. A collision at every node.
+
+    Returns f^col = f^eq + (1 - 1/tau-bar) f-bar^neq + F/2 (Eq. LB with
+    dt = 1), the new rho(1-theta) and the deviator of a^F (stored for the
+    F(t - dt) term of the next step, reading Q8).
+    """
+    lat = prm.lat
+    D = lat.D
+    c = lat.c.astype(np.float64)
+    # velocity gradient, central differences (Q7): du[a][b] = d u_a / d x_b
+    du = [[(grid.at(u[a], grid.unit(b, +1)) - grid.at(u[a], grid.unit(b, -1))) * 0.5
+           for b in range(D)] for a in range(D)]
+    div = sum(du[a][a] for a in range(D))
+    P = rho * (1.0 - theta)
+    dPdt = P - P_prev
+    # a^C (reading Q6): deviatoric divergence of the theta-defect of the
+    # equilibrium third moment plus the diagonal u^3 defect of the lattice
+    if prm.use_ac:
+        def cdiff(g, b):
+            return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
+        m = [rho * (1.0 - theta) * u[a] for a in range(D)]
+        dm = [[cdiff(m[a], b) for b in range(D)] for a in range(D)]
+        divm = sum(dm[g][g] for g in range(D))
+        aC = [[None] * D for _ in range(D)]
+        for a in range(D):
+            for b in range(D):
+                v = CS2 * (dm[a][b] + dm[b][a])
+                if a == b:
+                    v = v - CS2 * (2.0 / D) * divm - cdiff(rho * u[a] ** 3, a)
+                aC[a][b] = v
+    else:
+        aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
+    # Eq. af2
+    aF = [[None] * D for _ in range(D)]
+    for a in range(D):
+        for b in range(D):
+            v = aC[a][b] + fu[a] * u[b] + fu[b] * u[a]
+            if a == b:
+                v = v + (2.0 / D) * rho * CS2 * div - CS2 * dPdt
+            aF[a][b] = v
+    feq = equilibrium(lat, rho, u, theta)
+    # relaxation time (Eq. LB, reading Q9)
+    th_m = theta if prm.tau_mode == TAU_THETA else 1.0
+    tau_lb = prm.mu / (rho * CS2 * th_m)
+    tau_bar = tau_lb + 0.5
+    # Eq. pi2 (HRR), traceless projection with delta/D (Q4)
+    sig = prm.sigma
+    Pi = [[None] * D for _ in range(D)]
+    c2 = (c * c).sum(axis=1)
+    for a in range(D):
+        for b in range(D):
+            proj = c[:, a] * c[:, b] - (c2 / D if a == b else 0.0)
+            s = 0.0
+            for i in range(lat.Q):
+                s = s + proj[i] * (f[i] - feq[i])
+            s = s + 0.5 * devAF_prev[a][b]
+            S = du[a][b] + du[b][a] - ((2.0 / D) * div if a == b else 0.0)
+            Pi[a][b] = sig * s - (1.0 - sig) * rho * CS2 * th_m * tau_bar * S
+    fneq = regularized_neq(lat, u, Pi)
+    F = force_populations(lat, fu, aF)
+    fcol = feq + (1.0 - 1.0 / tau_bar) * fneq + 0.5 * F
+    return fcol, P, deviator(lat, aF)
+
+
+# --------------------------------------------------------------------------
+# energy equation (Eq. energy, App. A)
+# --------------------------------------------------------------------------
+def lb_face_fluxes(prm, grid, fcol, axis):
+    """Eqs. fluxx-z and the momentum rule below them: mass flux F^rho and
+    momentum fluxes F^{rho u_b} through the face x + e_axis/2."""
+    lat = prm.lat
+    D = lat.D
+    Frho = 0.0
+    Fm = [0.0] * D
+    for (i, off, coef) in lat.flux_table(axis):
+        v = coef * grid.at(fcol[i], off)
+        Frho = Frho + v
+        for b in range(D):
+            if lat.c[i, b] != 0:
+                Fm[b] = Fm[b] + float(lat.c[i, b]) * v
+    return Frho, Fm
+
+
+def muscl_face(grid, phi, ua, axis):
+    """Eq. linear: MUSCL-Hancock face value F*_{+axis/2}(phi) at x + e/2.
+
+    Slope Delta = 1/2 {(1+eta)(phi - phi_{-1}) + (1-eta)(phi_{+1} - phi)},
+    eta = (2u - sign(u))/3; phi_+- = phi +- Delta/2;
+    phibar_+- = phi_+- + (u/2)(phi_- - phi_+); upwind on
+    u~ = (u(x) + u(x+e))/2 >= 0.
+    """
+    e = grid.unit(axis, +1)
+    m = grid.unit(axis, -1)
+    eta = (2.0 * ua - np.sign(ua)) / 3.0
+    delta = 0.5 * ((1.0 + eta) * (phi - grid.at(phi, m)) + (1.0 - eta) * (grid.at(phi, e) - phi))
+    phi_p = phi + 0.5 * delta
+    phi_m = phi - 0.5 * delta
+    bar_p = phi_p + 0.5 * ua * (phi_m - phi_p)
+    bar_m = phi_m + 0.5 * ua * (phi_m - phi_p)
+    ut = 0.5 * (ua + grid.at(ua, e))
+    return np.where(ut >= 0.0, bar_p, grid.at(bar_m, e))
+
+
+def energy_update(prm, grid, fcol, rho, u, theta, E):
+    """Eq. energy: (rho E)^{n+1} = (rho E) - sum_a delta_a F^{rho E}_{+a/2},
+    with F^{rho E} = F*(rho H u_a) + (h - k)[F^rho - F*(rho u_a)]
+    + u_b [F^{rho u_b} - F*(rho u_a u_b + p d_ab)] - lambda delta_a T(x + e_a).
+    E here already contains the IB energy forcing (Q15)."""
+    D = prm.lat.D
+    p = rho * CS2 * theta
+    h = prm.Cp * theta            # gamma R T / (gamma - 1), T = theta
+    k = 0.5 * sum(u[b] * u[b] for b in range(D))
+    Enew = E.copy()
+    for a in range(D):
+        e = grid.unit(a, +1)
+        m = grid.unit(a, -1)
+        Frho, Fm = lb_face_fluxes(prm, grid, fcol, a)
+        ua = u[a]
+        FH = muscl_face(grid, (E + p) * ua, ua, a)
+        Fr = muscl_face(grid, rho * ua, ua, a)
+        hk = 0.5 * ((h - k) + grid.at(h - k, e))
+        FE = FH + hk * (Frho - Fr)
+        for b in range(D):
+            phib = rho * ua * u[b] + (p if a == b else 0.0)
+            Fb = muscl_face(grid, phib, ua, a)
+            ub = 0.5 * (u[b] + grid.at(u[b], e))
+            FE = FE + ub * (Fm[b] - Fb)
+        FE = FE - prm.lam * (grid.at(theta, e) - theta)
+        Enew = Enew - (FE - grid.at(FE, m))
+    return Enew
+
+
+def stream(prm, grid, fcol):
+    """Eq. LB pull form: f-bar_i(x, t+1) = f^col_i(x - c_i)."""
+    lat = prm.lat
+    out = np.empty_like(fcol)
+    for i in range(lat.Q):
+        out[i] = grid.at(fcol[i], tuple(-int(v) for v in lat.c[i]))
+    return out
+
+
+def freestream(prm, shape_zyx):
+    lat = prm.lat
+    D = lat.D
+    rho = np.full(shape_zyx, prm.rho_inf)
+    u = np.stack([np.full(shape_zyx, prm.u_inf[a]) for a in range(D)])
+    th = np.full(shape_zyx, prm.theta_inf)
+    f = equilibrium(lat, rho, u, th)
+    E = rho * (0.5 * sum(u[a] ** 2 for a in range(D)) + prm.Cv * th)
+    return f, E
+
+
+def apply_bc(prm, f, E):
+    """Q24 far field on the outermost nodes of non-periodic axes: outlet faces
+    copy the neighbouring inner plane first, then inlet / far-field faces are
+    set to the free-stream equilibrium (so edges and corners are free-stream)."""
+    D = prm.lat.D
+    zyx = f.shape[1:]
+    feq1, E1 = freestream(prm, ())
+    for a in range(D):
+        ax = len(zyx) - 1 - a
+        for side in (0, 1):
+            if prm.bc[2 * a + side] != BC_OUTLET:
+                continue
+            n = zyx[ax]
+            sl_d = [slice(None)] * len(zyx)
+            sl_s = [slice(None)] * len(zyx)
+            sl_d[ax] = 0 if side == 0 else n - 1
+            sl_s[ax] = 1 if side == 0 else n - 2
+            f[(slice(None),) + tuple(sl_d)] = f[(slice(None),) + tuple(sl_s)]
+            E[tuple(sl_d)] = E[tuple(sl_s)]
+    for a in range(D):
+        ax = len(zyx) - 1 - a
+        for side in (0, 1):
+            if prm.bc[2 * a + side] not in (BC_INLET, BC_FARFIELD):
+                continue
+            n = zyx[ax]
+            sl = [slice(None)] * len(zyx)
+            sl[ax] = 0 if side == 0 else n - 1
+            f[(slice(None),) + tuple(sl)] = feq1.reshape((prm.lat.Q,) + (1,) * (len(zyx) - 1))
+            E[tuple(sl)] = E1
+
+
+class Sim:
+    """Oracle state and the Sec. 2.5 time step.
+
+    State: f (post-stream f-bar), E (rho E without the current IB forcing),
+    P_prev (rho(1-theta) of the previous step), devAF_prev (deviator of
+    a^F of the previous step), step counter.
+    """
+
+    def __init__(self, prm, geometry=None):
+        self.prm = prm
+        self.grid = Grid(prm)
+        D = prm.lat.D
+        self.zyx = tuple(reversed(prm.shape))
+        self.f, self.E = freestream(prm, self.zyx)
+        rho = np.full(self.zyx, prm.rho_inf)
+        self.P_prev = rho * (1.0 - prm.theta_inf)
+        self.devAF_prev = [[np.zeros(self.zyx) for _ in range(D)] for _ in range(D)]
+        self.ib = None
+        if geometry is not None:
+            self.ib = IB.Setup(prm, self.grid, geometry)
+        self.last_loads = None
+        self.nstep = 0
+
+    # Sec. 2.2: rho = sum f-bar, j = sum c f-bar (moments before forcing)
+    def moments(self):
+        lat = self.prm.lat
+        c = lat.c.astype(np.float64)
+        rho = self.f.sum(axis=0)
+        j = np.stack([np.tensordot(c[:, a], self.f, axes=(0, 0)) for a in range(lat.D)])
+        return rho, j
+
+    def predicted(self):
+        """Predicted (pre-forcing) rho, rho u, u, T (Sec. 2.5 step 1)."""
+        prm = self.prm
+        rho, j = self.moments()
+        u = j / rho
+        T = (self.E / rho - 0.5 * (u * u).sum(axis=0)) / prm.Cv
+        return rho, j, u, T
+
+    def step(self):
+        prm, grid = self.prm, self.grid
+        D = prm.lat.D
+        rho, j, ustar, Tstar = self.predicted()
+        # Sec. 2.5 steps 1-4: interpolation, projection points, forces, spreading
+        fu = np.zeros((D,) + self.zyx)
+        wq = np.zeros(self.zyx)
+        if self.ib is not None:
+            fu, wq, self.last_loads = self.ib.force(rho, j, ustar, Tstar)
+        # corrected macroscopic quantities (Sec. 2.2, Q15)
+        u = (j + 0.5 * fu) / rho
+        E = self.E + wq
+        theta = (E / rho - 0.5 * (u * u).sum(axis=0)) / prm.Cv
+        # Sec. 2.5 step 5: collision, energy fluxes, streaming, boundaries
+        fcol, P, devAF = collide(prm, grid, self.f, rho, u, theta, fu, self.P_prev, self.devAF_prev)
+        Enew = energy_update(prm, grid, fcol, rho, u, theta, E)
+        fnew = stream(prm, grid, fcol)
+        apply_bc(prm, fnew, Enew)
+        self.f, self.E = fnew, Enew
+        self.P_prev, self.devAF_prev = P, devAF
+        self.nstep += 1
+
+    def run(self, n):
+        for _ in range(n):
+            self.step()
+
+    def fields(self):
+        """rho, u, T, p from the current state (predicted moments)."""
+        rho, j, u, T = self.predicted()
+        return rho, u, T, rho * self.prm.R * T

@@ -1,0 +1,130 @@
+"""Physics pins of the oracle's time step: exact invariants and linearized
+Navier-Stokes closed forms (Sec. 2.1-2.2).  CPU only, a few seconds each."""
+import numpy as np
+import pytest
+
+from oracle import ib, lbm
+from paper_2607_07432_b300 import inputs
+
+
+def _periodic(lattice, shape, mu, theta=1.0, U=(0.0, 0.0, 0.0), **kw):
+    prm = lbm.Params(lattice, shape, mach=0.1, reynolds=1.0, ref_length=1.0, mu=mu,
+                     theta_inf=theta, **kw)
+    D = prm.lat.D
+    prm.u_inf = np.array(U[:D], dtype=float)
+    return prm
+
+
+def _set(sim, rho, u, th):
+    prm = sim.prm
+    sim.f = lbm.equilibrium(prm.lat, rho, u, th)
+    sim.E = rho * (0.5 * (u * u).sum(0) + prm.Cv * th)
+    sim.P_prev = rho * (1.0 - th)
+
+
+@pytest.mark.parametrize("lattice,shape", [("D2Q9", (12, 10)), ("D3Q19", (6, 5, 4))])
+def test_uniform_flow_invariant(lattice, shape):
+    """A uniform state at any Ma and theta is a fixed point of the scheme."""
+    prm = _periodic(lattice, shape, mu=0.03, theta=0.6, U=(0.12, -0.05, 0.07))
+    sim = lbm.Sim(prm)
+    f0, E0 = sim.f.copy(), sim.E.copy()
+    sim.run(5)
+    assert np.abs(sim.f - f0).max() < 1e-15
+    assert np.abs(sim.E - E0).max() < 1e-14
+
+
+def test_discrete_continuity_matches_flux_tables():
+    """Mass update of one step equals minus the divergence of the LB mass
+    fluxes built from the flux tables (Eqs. fluxx-z): the tables are the
+    exact face decomposition of pull streaming."""
+    prm = _periodic("D3Q19", (6, 5, 4), mu=0.03)
+    g = lbm.Grid(prm)
+    rng = np.random.default_rng(7)
+    fcol = prm.lat.w[:, None, None, None] * (1 + 0.1 * rng.standard_normal((19, 4, 5, 6)))
+    rho0 = fcol.sum(0)
+    rho1 = lbm.stream(prm, g, fcol).sum(0)
+    div = 0.0
+    for a in range(3):
+        Fr, _ = lbm.lb_face_fluxes(prm, g, fcol, a)
+        div = div + (Fr - g.at(Fr, g.unit(a, -1)))
+    assert np.abs(rho1 - (rho0 - div)).max() < 1e-15
+
+
+def test_conservation_with_body():
+    """Periodic box with an immersed cylinder: sum rho is exact, sum rho u
+    increases by sum f_u = sum_l F_l W_l and sum rho E by sum (w + q) each step."""
+    geo = inputs.cylinder((16.3, 15.6), 10.0, 32, tbc=0, t_value=1.05)
+    prm = lbm.Params("D2Q9", (36, 32), mach=0.2, reynolds=30, ref_length=10, method=ib.FODIBM_R)
+    sim = lbm.Sim(prm, geo)
+    for _ in range(6):
+        rho, j, _, _ = sim.predicted()
+        m0, p0, e0 = rho.sum(), j.reshape(2, -1).sum(1), sim.E.sum()
+        sim.step()
+        L = sim.last_loads
+        rho, j, _, _ = sim.predicted()
+        fsum = (L["F"] * sim.ib.W[:, None]).sum(0)
+        esum = ((L["W"] + L["Q"]) * sim.ib.W).sum()
+        assert abs(rho.sum() - m0) < 1e-11
+        assert np.allclose(j.reshape(2, -1).sum(1) - p0, fsum, atol=1e-11)
+        assert abs(sim.E.sum() - e0 - esum) < 1e-10
+
+
+def _shear_rate(theta, U, mu=0.02, nx=48, steps=240, lattice="D2Q9"):
+    if lattice == "D2Q9":
+        prm = _periodic("D2Q9", (nx, 2), mu=mu, theta=theta, U=(U, 0.0))
+        zyx = (2, nx)
+    else:
+        prm = _periodic("D3Q19", (nx, 2, 2), mu=mu, theta=theta, U=(U, 0.0, 0.0))
+        zyx = (2, 2, nx)
+    D = prm.lat.D
+    sim = lbm.Sim(prm)
+    x = np.arange(nx)
+    rho = np.ones(zyx)
+    u = np.stack([np.full(zyx, U)] + [np.broadcast_to(1e-4 * np.sin(2 * np.pi * x / nx), zyx).copy()]
+                 + [np.zeros(zyx)] * (D - 2))
+    _set(sim, rho, u, np.full(zyx, theta))
+    amps = []
+    for _ in range(steps):
+        sim.step()
+        _, uu, _, _ = sim.fields()
+        amps.append(np.abs(np.fft.rfft(uu[1].reshape(-1, nx)[0]))[1] * 2 / nx)
+    amps = np.array(amps)
+    n0 = steps // 3
+    rate = -np.polyfit(np.arange(n0, steps), np.log(amps[n0:]), 1)[0]
+    return rate / (2 * np.pi / nx) ** 2 / mu
+
+
+@pytest.mark.parametrize("theta,U", [(1.0, 0.0), (0.5, 0.0), (0.5, 0.15), (0.25, 0.1)])
+def test_shear_wave_viscosity(theta, U):
+    """Linearized N-S: a shear wave decays at nu k^2 with nu = mu/rho, at any
+    theta and in a moving frame (Galilean invariance).  This pins the
+    theta-scaled relaxation (Q9) and the a^C reading (Q6): without the
+    off-diagonal theta-defect correction the measured viscosity is mu/theta."""
+    assert abs(_shear_rate(theta, U) - 1.0) < 0.02
+
+
+def test_shear_wave_viscosity_3d():
+    assert abs(_shear_rate(0.6, 0.1, lattice="D3Q19", steps=180) - 1.0) < 0.02
+
+
+def test_entropy_mode_decay():
+    """Linearized N-S at rest: an isobaric temperature wave decays at
+    lambda k^2 / (rho C_p)."""
+    nx = 48
+    prm = _periodic("D2Q9", (nx, 2), mu=0.03, theta=1.0)
+    sim = lbm.Sim(prm)
+    x = np.arange(nx)
+    s = np.broadcast_to(np.sin(2 * np.pi * x / nx), (2, nx))
+    A = 1e-4
+    th = 1.0 + A * s
+    rho = 1.0 / th
+    _set(sim, rho, np.zeros((2, 2, nx)), th)
+    amps = []
+    for _ in range(300):
+        sim.step()
+        _, _, T, _ = sim.fields()
+        amps.append(np.abs(np.fft.rfft(T[0]))[1] * 2 / nx)
+    amps = np.array(amps)
+    rate = -np.polyfit(np.arange(100, 300), np.log(amps[100:]), 1)[0]
+    expect = prm.lam / prm.Cp * (2 * np.pi / nx) ** 2
+    assert abs(rate / expect - 1.0) < 0.03
