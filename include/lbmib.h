@@ -1,0 +1,195 @@
+/*
+ * lbmib.h -- C ABI of the B300 hybrid compressible lattice Boltzmann solver
+ * with the fully one-sided diffuse-interface immersed boundary method and
+ * target-value reconstruction (FODIBM-R), arXiv 2607.07432.
+ *
+ * One handle = one simulation case on one GPU.  The library owns every
+ * device buffer it allocates; buffers passed in by the caller stay owned by
+ * the caller and are only read or written during the call.  Every entry
+ * point returns an lbm_status; no exception or C++ type crosses the ABI.
+ * A handle must be used by one host thread at a time.  Work is issued on
+ * the CUDA stream given in lbm_config.stream (NULL = legacy default stream);
+ * calls that return data to the caller synchronize that stream.
+ *
+ * Units are lattice units: dx = dt = 1, c_s^2 = 1/3, T_ref = 1.  Node (i,j,k)
+ * sits at coordinates (i,j,k); arrays over nodes are x-fastest
+ * (index = i + nx*(j + ny*k)).  Geometry is given in the same units.
+ *
+ * Errors: LBM_EINVAL bad argument, LBM_ENOMEM allocation failure, LBM_ECUDA a
+ * CUDA runtime error (text in lbm_last_error), LBM_EGEOM an immersed-boundary
+ * stencil that leaves the domain or a point with no interior node,
+ * LBM_ENAN a non-finite or non-positive density/temperature found by the
+ * health check (sticky until lbm_set_state / lbm_set_fields),
+ * LBM_ESTATE a call out of order (e.g. a step before geometry when a body
+ * was declared), LBM_EUNSUPPORTED a precision/lattice combination not built.
+ */
+#ifndef LBMIB_H
+#define LBMIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,
+  LBM_ENOMEM = 2,
+  LBM_ECUDA = 3,
+  LBM_EGEOM = 4,
+  LBM_ENAN = 5,
+  LBM_ETIMEOUT = 6,
+  LBM_ESTATE = 7,
+  LBM_EUNSUPPORTED = 8
+} lbm_status;
+
+/* lattice (Sec. 2.2 and App. A; D2Q9 is the standard 2D set) */
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+/* population storage / arithmetic: FP64 everywhere; FP32 everywhere;
+ * FP16 or BF16 storage of f_i - w_i with FP32 arithmetic.  The immersed
+ * boundary sums and wall loads are FP64 in every mode. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_BF16DEV = 3 };
+/* immersed boundary method (Sec. 2.3, 2.4, Table 1) */
+enum { IB_DIBM = 0, IB_FODIBM = 1, IB_FODIBM_R = 2 };
+/* per-face domain boundary: periodic; free-stream equilibrium (inlet or far
+ * field); zero-gradient outlet.  Faces: x-, x+, y-, y+, z-, z+. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_INLET = 1, LBM_BC_OUTLET = 2, LBM_BC_FARFIELD = 3 };
+/* relaxation time: tau_LB = mu/(rho c_s^2 theta) or mu/(rho c_s^2) (Eq. LB) */
+enum { LBM_TAU_THETA = 0, LBM_TAU_LITERAL = 1 };
+/* temperature condition at a Lagrangian point (velocity is always Dirichlet) */
+enum { IB_T_DIRICHLET = 0, IB_T_NEUMANN = 1 };
+/* body shape used to classify Eulerian nodes as inside (Omega') or not */
+enum { IB_SHAPE_SPHERE = 0, IB_SHAPE_ELLIPSE = 1, IB_SHAPE_POLYGON = 2, IB_SHAPE_MASK = 3 };
+
+typedef struct {
+  size_t struct_size;      /* = sizeof(lbm_config) */
+  int lattice;             /* LBM_D2Q9 or LBM_D3Q19 */
+  int precision;           /* LBM_FP64 .. LBM_BF16DEV */
+  int nx, ny, nz;          /* nz = 1 for D2Q9 */
+  double mach;             /* free-stream Mach number u_inf / sqrt(gamma R T_inf) */
+  double reynolds;         /* rho_inf u_inf L / mu */
+  double ref_length;       /* L in cells */
+  double prandtl;          /* lambda = mu C_p / Pr (default 0.71) */
+  double gamma;            /* ratio of specific heats (default 1.4) */
+  double theta_inf;        /* T_inf / T_ref; <= 0 selects the built-in rule */
+  double inflow_dir[3];    /* direction of u_inf (normalized by the library) */
+  double sigma_hrr;        /* HRR weight of Eq. pi2 (default 0.98) */
+  double d_n;              /* projection distance d_PB in cells (default 1.5) */
+  int method;              /* IB_DIBM / IB_FODIBM / IB_FODIBM_R */
+  int bc[6];               /* LBM_BC_* per face */
+  int tau_mode;            /* LBM_TAU_THETA (default) or LBM_TAU_LITERAL */
+  int use_ac;              /* 1: include the a^C term of Eq. af2 (default) */
+  int device;              /* CUDA device ordinal */
+  void* stream;            /* cudaStream_t, or NULL */
+} lbm_config;
+
+typedef struct {
+  size_t struct_size;      /* = sizeof(ib_geometry) */
+  int n_points;            /* number of Lagrangian points N_L */
+  const double* X;         /* host, N_L*D, point coordinates (cells) */
+  const double* normals;   /* host, N_L*D, outward unit normals */
+  const int* tbc;          /* host, N_L, IB_T_*; NULL = all Dirichlet */
+  const double* u_target;  /* host, N_L*D, wall velocity u^Bt; NULL = 0 */
+  const double* t_value;   /* host, N_L, T^Bt (Dirichlet) or dT/dn (Neumann) */
+  int shape;               /* IB_SHAPE_* */
+  double center[3];        /* sphere / circle / ellipse centre */
+  double radius;           /* sphere / circle radius */
+  double radii[2];         /* ellipse semi-axes */
+  double cos_a, sin_a;     /* ellipse rotation */
+  int n_poly;              /* polygon vertex count (2D) */
+  const double* poly;      /* host, n_poly*2, closed polygon vertices */
+  const uint8_t* mask;     /* host, nodes, 1 = inside (IB_SHAPE_MASK) */
+} ib_geometry;
+
+/* Fill *cfg with defaults (D2Q9, FP32, Pr 0.71, gamma 1.4, sigma 0.98,
+ * d_n 1.5, FODIBM-R, periodic faces, theta-scaled tau, a^C on). */
+lbm_status lbm_config_default(lbm_config* cfg);
+
+/* Create a case (Sec. 2.2): validates *cfg, derives u_inf, mu, lambda,
+ * theta_inf, allocates the device state and initializes every node to the
+ * free-stream equilibrium.  *out receives a handle owned by the caller until
+ * lbm_destroy. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out);
+
+/* Free every device buffer of the handle.  NULL is accepted. */
+void lbm_destroy(lbm_handle* h);
+
+/* Text of the last error on this handle (valid until the next call). */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* Immersed-boundary geometry (Sec. 2.3, 2.4): classifies nodes (Omega' =
+ * strict interior), builds on the device the one-sided stencils, phi_l
+ * (Eq. phi), the Lagrangian weights W_l (Eq. weight), the effective
+ * boundary X*_l (Eq. xeffect), d_BV, the projection points P_l and their
+ * d = 1 stencils, and the Eulerian-side spreading CSR (Eq. spr2).  Host
+ * arrays are copied; the call may be repeated to replace the body. */
+lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* g);
+
+/* Advance n_steps time steps (Sec. 2.5 steps 1-5), asynchronously on the
+ * configured stream.  Returns a sticky error found by a previous step. */
+lbm_status lbm_step(lbm_handle* h, int n_steps);
+
+/* Synchronize the stream and run the health check (Eq. feq needs rho > 0,
+ * theta > 0); LBM_ENAN if any node is non-finite or non-positive. */
+lbm_status lbm_check(lbm_handle* h);
+
+/* Macroscopic fields of the current state: rho = sum f, u = sum c f / rho,
+ * T = (rho E / rho - |u|^2/2) / C_v, p = rho R T (Sec. 2.2).  Each output
+ * is N doubles (u is D planes of N); any pointer may be NULL.  dst_is_device
+ * selects device or host destination pointers. */
+lbm_status lbm_get_fields(lbm_handle* h, int dst_is_device, double* rho, double* u,
+                          double* T, double* p);
+
+/* Raw state as FP64: populations f-bar (Q planes of N) and rho E (N). */
+lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* rhoE);
+
+/* Replace the state: populations (Q*N) and rho E (N).  The stored
+ * previous-step auxiliaries are reset as for a fresh start. */
+lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, const double* rhoE);
+
+/* Set the state to the equilibrium of given fields (warm start): rho (N),
+ * u (D*N), T (N). */
+lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho,
+                          const double* u, const double* T);
+
+/* Wall loads of the last step, FP64, deterministic fixed-order sums:
+ * force on the body = -sum_l F_l W_l (D components, rest 0),
+ * heat = sum_l Q_l W_l and work = sum_l W^IB_l W_l injected into the fluid.
+ * per_point (optional, host) receives N_L rows of (F_l[D], W^IB_l, Q_l). */
+lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, double* work,
+                              double* per_point);
+
+/* Derived constants: out[0..7] = u_inf magnitude, mu, lambda, theta_inf,
+ * C_v, C_p, rho_inf, gamma. */
+lbm_status lbm_get_constants(const lbm_handle* h, double out[8]);
+
+/* Sizes of the immersed-boundary setup: rows and nonzeros of the spreading
+ * CSR, number of points. */
+lbm_status ib_get_sizes(const lbm_handle* h, int* n_rows, int* nnz, int* n_points);
+
+/* Copy the immersed-boundary setup to host arrays (any may be NULL):
+ * phi (N_L), W (N_L), Xstar (N_L*D), dBV (N_L), inside (N nodes, 0/1),
+ * row_ptr (n_rows+1), cell_id (n_rows), col (nnz), wt (nnz). */
+lbm_status ib_get_setup(lbm_handle* h, double* phi, double* W, double* Xstar, double* dBV,
+                        uint8_t* inside, int* row_ptr, int* cell_id, int* col, double* wt);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream:
+ * enable (1) or disable (0); reset clears the counters. */
+lbm_status lbm_profile(lbm_handle* h, int enable, int reset);
+
+/* Accumulated profile: for kernel class k (0 = fused LBM step, 1 = IB
+ * interpolation/forcing, 2 = IB spreading, 3 = boundaries, 4 = other),
+ * ms[k] total milliseconds and launches[k] count since the last reset. */
+lbm_status lbm_get_profile(lbm_handle* h, double ms[5], long long launches[5]);
+
+/* Number of kernels this handle has launched since creation. */
+long long lbm_launch_count(const lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMIB_H */

@@ -23,8 +23,10 @@ Readings (paper silent or ambiguous):
   FODIBM with a Neumann temperature condition uses T^t = T^{P*} - g d_n,
   which is the paper's T^t = T^{P*} for the adiabatic case g = 0.
 """
+import functools
 import math
 
+import mpmath
 import numpy as np
 
 DIBM, FODIBM, FODIBM_R = 0, 1, 2
@@ -35,11 +37,36 @@ class GeometryError(ValueError):
     pass
 
 
+def _plain_sum(values):
+    acc = 0.0
+    for v in values:
+        acc = acc + v
+    return acc
+
+
+@functools.lru_cache(maxsize=None)
+def cos_rn(x):
+    """cos(x) correctly rounded to the nearest double: evaluated with 128-bit
+    mpmath and rounded once.  (Library cosines differ from it in the last
+    bit for about 0.1% of arguments; the correctly rounded value is the one
+    any implementation can reproduce exactly.)"""
+    with mpmath.workprec(128):
+        return float(mpmath.cos(mpmath.mpf(float(x))))
+
+
+def _delta_scalar(r, d):
+    if not abs(r) < d:
+        return 0.0
+    return (1.0 / (2.0 * d)) * (1.0 + cos_rn((np.pi * r) / d))
+
+
 def delta_tilde(r, d):
-    """1D regularized cosine delta, zero outside the strict support |r| < d."""
+    """1D regularized cosine delta (Sec. 2.3), zero outside the strict support
+    |r| < d (reading Q17)."""
     r = np.asarray(r, dtype=np.float64)
-    val = (1.0 / (2.0 * d)) * (1.0 + np.cos((np.pi * r) / d))
-    return np.where(np.abs(r) < d, val, 0.0)
+    if r.ndim == 0:
+        return np.float64(_delta_scalar(float(r), float(d)))
+    return np.array([_delta_scalar(float(v), float(d)) for v in r.ravel()]).reshape(r.shape)
 
 
 # --------------------------------------------------------------------------
@@ -169,9 +196,10 @@ class Setup:
             S_w.append(wts)
             S_x.append(np.array(xs))
         self.S_nodes, self.S_w = S_nodes, S_w
-        # Eq. phi
+        # Eq. phi (plain in-order sum: Python's built-in sum() over floats is
+        # compensated, which would not be the sum the equation writes)
         if one_sided:
-            self.phi = np.array([1.0 / sum(w) for w in S_w])
+            self.phi = np.array([1.0 / _plain_sum(w) for w in S_w])
         else:
             self.phi = np.ones(NL)
         # s_i = sum_k phi_k delta_ik  (inner sum of Eq. weight)

@@ -247,7 +247,7 @@ def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
             for b in range(D):
                 v = CS2 * (dm[a][b] + dm[b][a])
                 if a == b:
-                    v = v - CS2 * (2.0 / D) * divm - cdiff(rho * u[a] ** 3, a)
+                    v = v - CS2 * (2.0 / D) * divm - cdiff(rho * (u[a] * u[a] * u[a]), a)
                 aC[a][b] = v
     else:
         aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
@@ -427,10 +427,19 @@ class Sim:
 
     # Sec. 2.2: rho = sum f-bar, j = sum c f-bar (moments before forcing)
     def moments(self):
+        """Sums in population order i = 0..Q-1 (no library reduction), so
+        that near-zero momenta (far-field faces, symmetry lines) carry the
+        same rounding as any other in-order evaluation; the sign of u enters
+        the MUSCL slope (Eq. linear) discontinuously."""
         lat = self.prm.lat
         c = lat.c.astype(np.float64)
-        rho = self.f.sum(axis=0)
-        j = np.stack([np.tensordot(c[:, a], self.f, axes=(0, 0)) for a in range(lat.D)])
+        rho = np.zeros(self.zyx)
+        j = np.zeros((lat.D,) + self.zyx)
+        for i in range(lat.Q):
+            rho = rho + self.f[i]
+            for a in range(lat.D):
+                if c[i, a] != 0:
+                    j[a] = j[a] + c[i, a] * self.f[i]
         return rho, j
 
     def predicted(self):

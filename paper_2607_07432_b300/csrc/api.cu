@@ -1,0 +1,612 @@
+// C ABI of the solver (include/lbmib.h): handle management, derived
+// constants, immersed-boundary setup orchestration and the time loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cub/cub.cuh>
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+#include "ib.cuh"
+
+using namespace lbmib;
+using namespace lbmib_host;
+
+namespace {
+
+const Ops* pick_ops(int lattice, int precision) {
+  if (lattice == LBM_D2Q9) {
+    switch (precision) {
+      case LBM_FP64: return ops_d2q9_fp64();
+      case LBM_FP32: return ops_d2q9_fp32();
+      case LBM_FP16DEV: return ops_d2q9_fp16();
+      case LBM_BF16DEV: return ops_d2q9_bf16();
+    }
+  } else if (lattice == LBM_D3Q19) {
+    switch (precision) {
+      case LBM_FP64: return ops_d3q19_fp64();
+      case LBM_FP32: return ops_d3q19_fp32();
+      case LBM_FP16DEV: return ops_d3q19_fp16();
+      case LBM_BF16DEV: return ops_d3q19_bf16();
+    }
+  }
+  return nullptr;
+}
+
+// reading Q11: largest theta_inf <= 1 with u_inf <= 0.35 and kappa <= kappa_max
+double theta_rule(double mach, double gamma, double re, double L, double pr, int D) {
+  const double u1 = mach * std::sqrt(gamma * (1.0 / 3.0));
+  const double k1 = (u1 * L / re) * gamma / pr;
+  const double kmax = D == 2 ? 0.10 : 0.0667;
+  double th = 1.0;
+  if (u1 > 0.35) th = std::fmin(th, (0.35 / u1) * (0.35 / u1));
+  if (k1 > kmax) th = std::fmin(th, (kmax / k1) * (kmax / k1));
+  return th;
+}
+
+void free_ib(lbm_handle* h) {
+  void* ptrs[] = {h->inside, h->X, h->nrm, h->uB, h->tB, h->tbc, h->sten_node, h->psten_node, h->sten_w,
+                  h->sten_x, h->psten_w, h->phi, h->W, h->Xstar, h->dBV, h->row_ptr, h->cell_id, h->col,
+                  h->slot_of_entry, h->wt, h->row_of_node, h->G, h->FU, h->WQ, h->loads};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->inside = nullptr;
+  h->X = h->nrm = h->uB = h->tB = nullptr;
+  h->tbc = nullptr;
+  h->sten_node = h->psten_node = nullptr;
+  h->sten_w = h->sten_x = h->psten_w = h->phi = h->W = h->Xstar = h->dBV = nullptr;
+  h->row_ptr = h->cell_id = h->col = h->slot_of_entry = nullptr;
+  h->wt = nullptr;
+  h->row_of_node = nullptr;
+  h->G = h->FU = h->WQ = h->loads = nullptr;
+  h->has_ib = false;
+  h->NL = h->n_rows = h->nnz = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_config_default(lbm_config* c) {
+  if (!c) return LBM_EINVAL;
+  std::memset(c, 0, sizeof(*c));
+  c->struct_size = sizeof(lbm_config);
+  c->lattice = LBM_D2Q9;
+  c->precision = LBM_FP32;
+  c->nx = 64;
+  c->ny = 64;
+  c->nz = 1;
+  c->mach = 0.1;
+  c->reynolds = 100;
+  c->ref_length = 10;
+  c->prandtl = 0.71;
+  c->gamma = 1.4;
+  c->theta_inf = 0.0;
+  c->inflow_dir[0] = 1.0;
+  c->sigma_hrr = 0.98;
+  c->d_n = 1.5;
+  c->method = IB_FODIBM_R;
+  c->tau_mode = LBM_TAU_THETA;
+  c->use_ac = 1;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
+  if (!cfg || !out || cfg->struct_size != sizeof(lbm_config)) return LBM_EINVAL;
+  *out = nullptr;
+  const int D = cfg->lattice == LBM_D3Q19 ? 3 : 2;
+  if ((cfg->lattice != LBM_D2Q9 && cfg->lattice != LBM_D3Q19) || cfg->nx < 3 || cfg->ny < 3 ||
+      (D == 3 && cfg->nz < 3) || (D == 2 && cfg->nz != 1) || cfg->mach <= 0 || cfg->reynolds <= 0 ||
+      cfg->ref_length <= 0 || cfg->gamma <= 1.0 || cfg->prandtl <= 0 || cfg->precision < 0 ||
+      cfg->precision > LBM_BF16DEV || cfg->method < IB_DIBM || cfg->method > IB_FODIBM_R)
+    return LBM_EINVAL;
+  for (int f = 0; f < 2 * D; ++f)
+    if (cfg->bc[f] < LBM_BC_PERIODIC || cfg->bc[f] > LBM_BC_FARFIELD) return LBM_EINVAL;
+  for (int a = 0; a < D; ++a)
+    if ((cfg->bc[2 * a] == LBM_BC_PERIODIC) != (cfg->bc[2 * a + 1] == LBM_BC_PERIODIC)) return LBM_EINVAL;
+  const Ops* ops = pick_ops(cfg->lattice, cfg->precision);
+  if (!ops) return LBM_EUNSUPPORTED;
+  lbm_handle* h = new lbm_handle();
+  h->cfg = *cfg;
+  h->ops = ops;
+  h->D = D;
+  h->Q = D == 3 ? 19 : 9;
+  h->NDEV = D == 3 ? 5 : 2;
+  h->g.n[0] = cfg->nx;
+  h->g.n[1] = cfg->ny;
+  h->g.n[2] = D == 3 ? cfg->nz : 1;
+  for (int a = 0; a < 3; ++a) h->g.per[a] = a < D ? (cfg->bc[2 * a] == LBM_BC_PERIODIC) : 1;
+  h->g.N = (long long)h->g.n[0] * h->g.n[1] * h->g.n[2];
+  h->st = (cudaStream_t)cfg->stream;
+  h->csize = cfg->precision == LBM_FP64 ? 8 : 4;
+  h->ssize = cfg->precision == LBM_FP64 ? 8 : (cfg->precision == LBM_FP32 ? 4 : 2);
+  // derived constants (Sec. 2.1; readings Q10, Q11)
+  h->gamma = cfg->gamma;
+  h->R = 1.0 / 3.0;
+  h->Cv = h->R / (h->gamma - 1.0);
+  h->Cp = h->gamma * h->R / (h->gamma - 1.0);
+  h->theta_inf = cfg->theta_inf > 0 ? cfg->theta_inf
+                                    : theta_rule(cfg->mach, cfg->gamma, cfg->reynolds, cfg->ref_length,
+                                                 cfg->prandtl, D);
+  h->rho_inf = 1.0;
+  const double c_inf = std::sqrt(h->gamma * h->R * h->theta_inf);
+  h->u_mag = cfg->mach * c_inf;
+  double dn = 0.0;
+  for (int a = 0; a < D; ++a) dn += cfg->inflow_dir[a] * cfg->inflow_dir[a];
+  dn = std::sqrt(dn);
+  if (!(dn > 0)) {
+    delete h;
+    return LBM_EINVAL;
+  }
+  for (int a = 0; a < D; ++a) h->u_inf[a] = h->u_mag * (cfg->inflow_dir[a] / dn);
+  h->mu = h->rho_inf * h->u_mag * cfg->ref_length / cfg->reynolds;
+  h->lam = h->mu * h->Cp / cfg->prandtl;
+  double k = 0.0;
+  for (int a = 0; a < D; ++a) k += h->u_inf[a] * h->u_inf[a];
+  h->E_inf = h->rho_inf * (0.5 * k + h->Cv * h->theta_inf);
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    delete h;
+    return LBM_ECUDA;
+  }
+  const long long N = h->g.N;
+  lbm_status s = LBM_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (s) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s = fail(h, LBM_ENOMEM, "device allocation failed");
+    }
+  };
+  alloc(&h->f, N * h->Q * h->ssize);
+  alloc(&h->fcol, N * h->Q * (h->use_fused ? h->ssize : h->csize));
+  alloc(&h->M, N * (D + 3) * h->csize);
+  alloc(&h->E, N * h->csize);
+  for (int k2 = 0; k2 < 2; ++k2) {
+    alloc(&h->P[k2], N * h->csize);
+    alloc(&h->A[k2], N * h->NDEV * h->csize);
+  }
+  alloc(&h->feq_inf, 32 * h->csize);
+  alloc((void**)&h->d_bad, sizeof(unsigned long long));
+  if (!s) s = h->ops->init(h);
+  if (!s && cudaStreamSynchronize(h->st) != cudaSuccess) s = fail(h, LBM_ECUDA, "init");
+  if (s) {
+    lbm_destroy(h);
+    return s;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_ib(h);
+  void* ptrs[] = {h->f, h->fcol, h->M, h->E, h->P[0], h->P[1], h->A[0], h->A[1], h->feq_inf, h->d_bad};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& e : h->ev_pool) cudaEventDestroy(e);
+  for (auto& e : h->ev_used) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
+  if (!h || !gm || gm->struct_size != sizeof(ib_geometry) || gm->n_points <= 0 || !gm->X || !gm->normals ||
+      !gm->t_value)
+    return fail(h, LBM_EINVAL, "invalid geometry arguments");
+  if (gm->shape < IB_SHAPE_SPHERE || gm->shape > IB_SHAPE_MASK) return fail(h, LBM_EINVAL, "invalid shape");
+  if (gm->shape == IB_SHAPE_POLYGON && (gm->n_poly < 3 || !gm->poly || h->D != 2))
+    return fail(h, LBM_EINVAL, "invalid polygon");
+  if (gm->shape == IB_SHAPE_ELLIPSE && h->D != 2) return fail(h, LBM_EINVAL, "ellipse is 2D only");
+  if (gm->shape == IB_SHAPE_MASK && !gm->mask) return fail(h, LBM_EINVAL, "mask missing");
+  CK(cudaStreamSynchronize(h->st));
+  free_ib(h);
+  const int D = h->D, NL = gm->n_points;
+  const int KS = D == 2 ? 16 : 64, KP = D == 2 ? 4 : 8;
+  const long long N = h->g.N;
+  h->NL = NL;
+  double* dpoly = nullptr;
+  unsigned char* dmask = nullptr;
+  int* derr = nullptr;
+  unsigned long long *keys = nullptr, *keys_sorted = nullptr;
+  int *count = nullptr, *head = nullptr, *head_scan = nullptr;
+  double* s_row = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  lbm_status s = LBM_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (s) return;
+    if (cudaMalloc(p, bytes ? bytes : 8) != cudaSuccess) {
+      cudaGetLastError();
+      s = fail(h, LBM_ENOMEM, "device allocation failed");
+    }
+  };
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (s) return;
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+      s = fail(h, LBM_ECUDA, "upload failed");
+  };
+  alloc((void**)&h->inside, N);
+  alloc((void**)&h->X, NL * D * 8);
+  alloc((void**)&h->nrm, NL * D * 8);
+  alloc((void**)&h->uB, NL * D * 8);
+  alloc((void**)&h->tB, NL * 8);
+  alloc((void**)&h->tbc, NL * 4);
+  alloc((void**)&h->sten_node, (size_t)NL * KS * 4);
+  alloc((void**)&h->sten_w, (size_t)NL * KS * 8);
+  alloc((void**)&h->sten_x, (size_t)NL * KS * 3 * 8);
+  alloc((void**)&h->psten_node, (size_t)NL * KP * 4);
+  alloc((void**)&h->psten_w, (size_t)NL * KP * 8);
+  alloc((void**)&h->phi, NL * 8);
+  alloc((void**)&h->W, NL * 8);
+  alloc((void**)&h->Xstar, NL * D * 8);
+  alloc((void**)&h->dBV, NL * 8);
+  alloc((void**)&h->G, NL * (D + 2) * 8);
+  alloc((void**)&h->loads, 8 * 8);
+  alloc((void**)&h->row_of_node, N * 4);
+  alloc((void**)&derr, 4);
+  alloc((void**)&keys, (size_t)NL * KS * 8);
+  alloc((void**)&keys_sorted, (size_t)NL * KS * 8);
+  alloc((void**)&count, 4);
+  if (s) goto done;
+  {
+    std::vector<double> zeros((size_t)NL * D, 0.0);
+    std::vector<int> tb(NL, 0);
+    if (gm->tbc)
+      for (int l = 0; l < NL; ++l) tb[l] = gm->tbc[l];
+    up(h->X, gm->X, NL * D * 8);
+    up(h->nrm, gm->normals, NL * D * 8);
+    up(h->uB, gm->u_target ? gm->u_target : zeros.data(), NL * D * 8);
+    up(h->tB, gm->t_value, NL * 8);
+    up(h->tbc, tb.data(), NL * 4);
+    if (s) goto done;
+    ShapeDev sd{};
+    sd.kind = gm->shape;
+    for (int a = 0; a < 3; ++a) sd.c[a] = gm->center[a];
+    sd.r = gm->radius;
+    sd.ra = gm->radii[0];
+    sd.rb = gm->radii[1];
+    sd.cs = gm->cos_a;
+    sd.sn = gm->sin_a;
+    sd.n_poly = gm->n_poly;
+    if (gm->shape == IB_SHAPE_POLYGON) {
+      alloc((void**)&dpoly, gm->n_poly * 2 * 8);
+      up(dpoly, gm->poly, gm->n_poly * 2 * 8);
+      sd.poly = dpoly;
+    }
+    if (gm->shape == IB_SHAPE_MASK) {
+      alloc((void**)&dmask, N);
+      up(dmask, gm->mask, N);
+      sd.mask = dmask;
+    }
+    if (s) goto done;
+    CK(cudaMemsetAsync(derr, 0, 4, h->st));
+    CK(cudaMemsetAsync(count, 0, 4, h->st));
+    CK(cudaMemsetAsync(h->row_of_node, 0xff, N * 4, h->st));
+    if ((s = launch(h, kProfOther, [&] { k_classify<<<nblk(N, 256), 256, 0, h->st>>>(h->g, D, sd, h->inside); })))
+      goto done;
+    IBSetupDev sdv;
+    sdv.D = D;
+    sdv.NL = NL;
+    sdv.one_sided = h->cfg.method != IB_DIBM;
+    sdv.d_n = h->cfg.d_n;
+    sdv.X = h->X;
+    sdv.nrm = h->nrm;
+    sdv.inside = h->inside;
+    sdv.sten_node = h->sten_node;
+    sdv.sten_w = h->sten_w;
+    sdv.sten_x = h->sten_x;
+    sdv.phi = h->phi;
+    sdv.psten_node = h->psten_node;
+    sdv.psten_w = h->psten_w;
+    sdv.err = derr;
+    if ((s = launch(h, kProfOther, [&] { k_stencils<<<nblk(NL, 64), 64, 0, h->st>>>(h->g, sdv); }))) goto done;
+    if ((s = launch(h, kProfOther, [&] {
+           k_csr_keys<<<nblk((long long)NL * KS, 256), 256, 0, h->st>>>(NL, KS, h->sten_node, keys, count);
+         })))
+      goto done;
+    int herr = 0, hcount = 0;
+    CK(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&hcount, count, 4, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (herr) {
+      s = fail(h, LBM_EGEOM, herr == 1 ? "an immersed-boundary stencil leaves the domain"
+                                       : "a Lagrangian point has no interior node in its support");
+      goto done;
+    }
+    const int nnz = hcount;
+    h->nnz = nnz;
+    // sort (node, point, slot) keys: rows ascending, entries ascending in l
+    const int bits = 64;
+    cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, keys, keys_sorted, nnz, 0, bits, h->st);
+    alloc(&tmp, tmp_bytes);
+    alloc((void**)&head, (size_t)nnz * 4);
+    alloc((void**)&head_scan, (size_t)nnz * 4);
+    if (s) goto done;
+    CK(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, keys, keys_sorted, nnz, 0, bits, h->st));
+    const int NLKS = NL * KS;
+    if ((s = launch(h, kProfOther, [&] {
+           k_csr_heads<<<nblk(nnz, 256), 256, 0, h->st>>>(nnz, NLKS, keys_sorted, head);
+         })))
+      goto done;
+    size_t tmp2 = 0;
+    cub::DeviceScan::InclusiveSum(nullptr, tmp2, head, head_scan, nnz, h->st);
+    if (tmp2 > tmp_bytes) {
+      CK(cudaStreamSynchronize(h->st));
+      cudaFree(tmp);
+      tmp = nullptr;
+      tmp_bytes = tmp2;
+      alloc(&tmp, tmp_bytes);
+      if (s) goto done;
+    }
+    CK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, head, head_scan, nnz, h->st));
+    int nrows = 0;
+    CK(cudaMemcpyAsync(&nrows, head_scan + (nnz - 1), 4, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->n_rows = nrows;
+    alloc((void**)&h->row_ptr, (size_t)(nrows + 1) * 4);
+    alloc((void**)&h->cell_id, (size_t)nrows * 4);
+    alloc((void**)&h->col, (size_t)nnz * 4);
+    alloc((void**)&h->slot_of_entry, (size_t)nnz * 4);
+    alloc((void**)&h->wt, (size_t)nnz * 8);
+    alloc((void**)&s_row, (size_t)nrows * 8);
+    alloc((void**)&h->FU, (size_t)nrows * D * 8);
+    alloc((void**)&h->WQ, (size_t)nrows * 8);
+    if (s) goto done;
+    CK(cudaMemcpyAsync(h->row_ptr + nrows, &h->nnz, 4, cudaMemcpyHostToDevice, h->st));
+    if ((s = launch(h, kProfOther, [&] {
+           k_csr_fill<<<nblk(nnz, 256), 256, 0, h->st>>>(nnz, NLKS, KS, keys_sorted, head_scan, h->row_ptr,
+                                                          h->cell_id, h->col, h->slot_of_entry);
+         })))
+      goto done;
+    if ((s = launch(h, kProfOther, [&] {
+           k_row_density<<<nblk(nrows, 256), 256, 0, h->st>>>(nrows, h->row_ptr, h->slot_of_entry, h->col,
+                                                               h->phi, h->sten_w, s_row);
+         })))
+      goto done;
+    if ((s = launch(h, kProfOther, [&] {
+           k_weights<<<nblk(NL, 64), 64, 0, h->st>>>(D, NL, KS, nrows, h->cell_id, s_row, h->sten_node,
+                                                     h->sten_w, h->sten_x, h->phi, h->X, h->nrm, h->W,
+                                                     h->Xstar, h->dBV);
+         })))
+      goto done;
+    if ((s = launch(h, kProfOther, [&] {
+           k_csr_weights<<<nblk(nnz, 256), 256, 0, h->st>>>(nnz, h->col, h->slot_of_entry, h->phi, h->W,
+                                                            h->sten_w, h->wt);
+         })))
+      goto done;
+    if ((s = launch(h, kProfOther, [&] {
+           k_row_map<<<nblk(nrows, 256), 256, 0, h->st>>>(nrows, h->cell_id, h->row_of_node);
+         })))
+      goto done;
+    CK(cudaMemsetAsync(h->G, 0, NL * (D + 2) * 8, h->st));
+    CK(cudaMemsetAsync(h->FU, 0, (size_t)nrows * D * 8, h->st));
+    CK(cudaMemsetAsync(h->WQ, 0, (size_t)nrows * 8, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->has_ib = true;
+  }
+done:
+  cudaStreamSynchronize(h->st);
+  void* tmps[] = {dpoly, dmask, derr, keys, keys_sorted, count, head, head_scan, s_row, tmp};
+  for (void* p : tmps)
+    if (p) cudaFree(p);
+  if (s) free_ib(h);
+  return s;
+}
+
+lbm_status lbm_step(lbm_handle* h, int n_steps) {
+  if (!h || n_steps < 0) return LBM_EINVAL;
+  if (h->sticky) return (lbm_status)h->sticky;
+  for (int k = 0; k < n_steps; ++k) {
+    lbm_status s = h->ops->step(h);
+    if (s) return s;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_check(lbm_handle* h) {
+  if (!h) return LBM_EINVAL;
+  CK(cudaMemsetAsync(h->d_bad, 0, sizeof(unsigned long long), h->st));
+  lbm_status s = h->ops->health(h, h->d_bad);
+  if (s) return s;
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (bad) {
+    h->sticky = LBM_ENAN;
+    return fail(h, LBM_ENAN, std::to_string(bad) + " nodes with non-finite or non-positive rho / T");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_handle* h, int dst_is_device, double* rho, double* u, double* T, double* p) {
+  if (!h) return LBM_EINVAL;
+  const long long N = h->g.N;
+  if (dst_is_device) {
+    lbm_status s = h->ops->fields(h, rho, u, T, p);
+    if (s) return s;
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+  }
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, N * 8 * (h->D + 3)));
+  double *dr = buf, *du = buf + N, *dT = buf + N * (1 + h->D), *dp = buf + N * (2 + h->D);
+  lbm_status s = h->ops->fields(h, rho ? dr : nullptr, u ? du : nullptr, T ? dT : nullptr, p ? dp : nullptr);
+  if (!s) {
+    if (rho) cudaMemcpyAsync(rho, dr, N * 8, cudaMemcpyDeviceToHost, h->st);
+    if (u) cudaMemcpyAsync(u, du, N * 8 * h->D, cudaMemcpyDeviceToHost, h->st);
+    if (T) cudaMemcpyAsync(T, dT, N * 8, cudaMemcpyDeviceToHost, h->st);
+    if (p) cudaMemcpyAsync(p, dp, N * 8, cudaMemcpyDeviceToHost, h->st);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) s = fail(h, LBM_ECUDA, "get_fields copy");
+  }
+  cudaFree(buf);
+  return s;
+}
+
+lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* E) {
+  if (!h || !f || !E) return LBM_EINVAL;
+  const long long N = h->g.N;
+  if (dst_is_device) {
+    lbm_status s = h->ops->get_state(h, f, E);
+    if (s) return s;
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+  }
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, N * 8 * (h->Q + 1)));
+  lbm_status s = h->ops->get_state(h, buf, buf + N * h->Q);
+  if (!s) {
+    cudaMemcpyAsync(f, buf, N * 8 * h->Q, cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(E, buf + N * h->Q, N * 8, cudaMemcpyDeviceToHost, h->st);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) s = fail(h, LBM_ECUDA, "get_state copy");
+  }
+  cudaFree(buf);
+  return s;
+}
+
+lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, const double* E) {
+  if (!h || !f || !E) return LBM_EINVAL;
+  const long long N = h->g.N;
+  if (src_is_device) {
+    lbm_status s = h->ops->set_state(h, f, E);
+    if (s) return s;
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+  }
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, N * 8 * (h->Q + 1)));
+  lbm_status s = LBM_OK;
+  if (cudaMemcpyAsync(buf, f, N * 8 * h->Q, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(buf + N * h->Q, E, N * 8, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+    s = fail(h, LBM_ECUDA, "set_state copy");
+  if (!s) s = h->ops->set_state(h, buf, buf + N * h->Q);
+  cudaStreamSynchronize(h->st);
+  cudaFree(buf);
+  return s;
+}
+
+lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho, const double* u,
+                          const double* T) {
+  if (!h || !rho || !u || !T) return LBM_EINVAL;
+  const long long N = h->g.N;
+  if (src_is_device) {
+    lbm_status s = h->ops->set_fields(h, rho, u, T);
+    if (s) return s;
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+  }
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, N * 8 * (h->D + 2)));
+  lbm_status s = LBM_OK;
+  if (cudaMemcpyAsync(buf, rho, N * 8, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(buf + N, u, N * 8 * h->D, cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+      cudaMemcpyAsync(buf + N * (1 + h->D), T, N * 8, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+    s = fail(h, LBM_ECUDA, "set_fields copy");
+  if (!s) s = h->ops->set_fields(h, buf, buf + N, buf + N * (1 + h->D));
+  cudaStreamSynchronize(h->st);
+  cudaFree(buf);
+  return s;
+}
+
+lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, double* work, double* per_point) {
+  if (!h) return LBM_EINVAL;
+  if (!h->has_ib) return fail(h, LBM_ESTATE, "no immersed body");
+  lbm_status s = launch(h, kProfOther, [&] { k_wall_loads<<<1, 256, 0, h->st>>>(h->D, h->NL, h->G, h->W, h->loads); });
+  if (s) return s;
+  double out[5];
+  CK(cudaMemcpyAsync(out, h->loads, 5 * 8, cudaMemcpyDeviceToHost, h->st));
+  if (per_point) CK(cudaMemcpyAsync(per_point, h->G, (size_t)h->NL * (h->D + 2) * 8, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (force)
+    for (int a = 0; a < 3; ++a) force[a] = out[a];
+  if (heat) *heat = out[3];
+  if (work) *work = out[4];
+  return LBM_OK;
+}
+
+lbm_status lbm_get_constants(const lbm_handle* h, double out[8]) {
+  if (!h || !out) return LBM_EINVAL;
+  out[0] = h->u_mag;
+  out[1] = h->mu;
+  out[2] = h->lam;
+  out[3] = h->theta_inf;
+  out[4] = h->Cv;
+  out[5] = h->Cp;
+  out[6] = h->rho_inf;
+  out[7] = h->gamma;
+  return LBM_OK;
+}
+
+lbm_status ib_get_sizes(const lbm_handle* h, int* n_rows, int* nnz, int* n_points) {
+  if (!h) return LBM_EINVAL;
+  if (n_rows) *n_rows = h->n_rows;
+  if (nnz) *nnz = h->nnz;
+  if (n_points) *n_points = h->NL;
+  return LBM_OK;
+}
+
+lbm_status ib_get_setup(lbm_handle* h, double* phi, double* W, double* Xstar, double* dBV, uint8_t* inside,
+                        int* row_ptr, int* cell_id, int* col, double* wt) {
+  if (!h) return LBM_EINVAL;
+  if (!h->has_ib) return fail(h, LBM_ESTATE, "no immersed body");
+  const int NL = h->NL, D = h->D;
+  if (phi) CK(cudaMemcpyAsync(phi, h->phi, NL * 8, cudaMemcpyDeviceToHost, h->st));
+  if (W) CK(cudaMemcpyAsync(W, h->W, NL * 8, cudaMemcpyDeviceToHost, h->st));
+  if (Xstar) CK(cudaMemcpyAsync(Xstar, h->Xstar, NL * D * 8, cudaMemcpyDeviceToHost, h->st));
+  if (dBV) CK(cudaMemcpyAsync(dBV, h->dBV, NL * 8, cudaMemcpyDeviceToHost, h->st));
+  if (inside) CK(cudaMemcpyAsync(inside, h->inside, h->g.N, cudaMemcpyDeviceToHost, h->st));
+  if (row_ptr) CK(cudaMemcpyAsync(row_ptr, h->row_ptr, (size_t)(h->n_rows + 1) * 4, cudaMemcpyDeviceToHost, h->st));
+  if (cell_id) CK(cudaMemcpyAsync(cell_id, h->cell_id, (size_t)h->n_rows * 4, cudaMemcpyDeviceToHost, h->st));
+  if (col) CK(cudaMemcpyAsync(col, h->col, (size_t)h->nnz * 4, cudaMemcpyDeviceToHost, h->st));
+  if (wt) CK(cudaMemcpyAsync(wt, h->wt, (size_t)h->nnz * 8, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_handle* h, int enable, int reset) {
+  if (!h) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  if (reset) {
+    for (auto& e : h->ev_used) {
+      h->ev_pool.push_back(e.second.first);
+      h->ev_pool.push_back(e.second.second);
+    }
+    h->ev_used.clear();
+    for (int k = 0; k < kProfClasses; ++k) {
+      h->prof_ms[k] = 0;
+      h->prof_n[k] = 0;
+    }
+  }
+  h->prof = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_profile(lbm_handle* h, double ms[5], long long launches[5]) {
+  if (!h) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  for (auto& e : h->ev_used) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e.second.first, e.second.second);
+    h->prof_ms[e.first] += t;
+    h->prof_n[e.first] += 1;
+    h->ev_pool.push_back(e.second.first);
+    h->ev_pool.push_back(e.second.second);
+  }
+  h->ev_used.clear();
+  for (int k = 0; k < kProfClasses; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_n[k];
+  }
+  return LBM_OK;
+}
+
+long long lbm_launch_count(const lbm_handle* h) { return h ? h->launches : -1; }
+
+}  // extern "C"

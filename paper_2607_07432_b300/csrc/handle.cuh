@@ -1,0 +1,132 @@
+// Handle of one simulation case and the host-side helpers shared by the
+// C ABI (api.cu) and the per-configuration kernel instantiations.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbmib.h"
+#include "grid.cuh"
+
+namespace lbmib_host {
+using namespace lbmib;
+constexpr int kProfClasses = 5;
+enum { kProfStep = 0, kProfIBForce = 1, kProfIBSpread = 2, kProfBC = 3, kProfOther = 4 };
+
+struct Ops;
+}  // namespace lbmib_host
+
+struct lbm_handle {
+  lbm_config cfg;
+  int D = 2, Q = 9, NDEV = 2;
+  lbmib::Grid g{};
+  cudaStream_t st = nullptr;
+  // derived constants (Sec. 2.1, readings Q10-Q11)
+  double R = 1.0 / 3.0, gamma = 1.4, Cv = 0, Cp = 0, theta_inf = 1, rho_inf = 1, u_mag = 0, mu = 0, lam = 0;
+  double u_inf[3] = {0, 0, 0};
+  double E_inf = 0;
+  size_t csize = 8, ssize = 8;  // compute / storage element sizes
+  // device state
+  void* f = nullptr;
+  void* fcol = nullptr;
+  void* M = nullptr;
+  void* E = nullptr;
+  void* P[2] = {nullptr, nullptr};
+  void* A[2] = {nullptr, nullptr};
+  void* feq_inf = nullptr;
+  int cur = 0;
+  int use_fused = 0;
+  unsigned long long* d_bad = nullptr;
+  // immersed boundary
+  bool has_ib = false;
+  int NL = 0, n_rows = 0, nnz = 0;
+  unsigned char* inside = nullptr;
+  double *X = nullptr, *nrm = nullptr, *uB = nullptr, *tB = nullptr;
+  int* tbc = nullptr;
+  int *sten_node = nullptr, *psten_node = nullptr;
+  double *sten_w = nullptr, *sten_x = nullptr, *psten_w = nullptr;
+  double *phi = nullptr, *W = nullptr, *Xstar = nullptr, *dBV = nullptr;
+  int *row_ptr = nullptr, *cell_id = nullptr, *col = nullptr, *slot_of_entry = nullptr;
+  double* wt = nullptr;
+  int* row_of_node = nullptr;
+  double *G = nullptr, *FU = nullptr, *WQ = nullptr, *loads = nullptr;
+  // bookkeeping
+  std::string err;
+  long long launches = 0;
+  int sticky = LBM_OK;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  double prof_ms[lbmib_host::kProfClasses] = {0, 0, 0, 0, 0};
+  long long prof_n[lbmib_host::kProfClasses] = {0, 0, 0, 0, 0};
+  const lbmib_host::Ops* ops = nullptr;
+};
+
+namespace lbmib_host {
+
+inline lbm_status fail(lbm_handle* h, lbm_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(h, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+inline cudaEvent_t ev_get(lbm_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// launch wrapper: counts launches and records profiling events
+template <class F>
+inline lbm_status launch(lbm_handle* h, int cls, F&& fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->prof) {
+    a = ev_get(h);
+    b = ev_get(h);
+    cudaEventRecord(a, h->st);
+  }
+  fn();
+  h->launches++;
+  if (h->prof) {
+    cudaEventRecord(b, h->st);
+    h->ev_used.push_back({cls, {a, b}});
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, LBM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct Ops {
+  lbm_status (*init)(lbm_handle*);
+  lbm_status (*step)(lbm_handle*);
+  lbm_status (*fields)(lbm_handle*, double*, double*, double*, double*);
+  lbm_status (*get_state)(lbm_handle*, double*, double*);
+  lbm_status (*set_state)(lbm_handle*, const double*, const double*);
+  lbm_status (*set_fields)(lbm_handle*, const double*, const double*, const double*);
+  lbm_status (*health)(lbm_handle*, unsigned long long*);
+};
+
+
+const Ops* ops_d2q9_fp64();
+const Ops* ops_d2q9_fp32();
+const Ops* ops_d2q9_fp16();
+const Ops* ops_d2q9_bf16();
+const Ops* ops_d3q19_fp64();
+const Ops* ops_d3q19_fp32();
+const Ops* ops_d3q19_fp16();
+const Ops* ops_d3q19_bf16();
+}  // namespace lbmib_host

@@ -1,0 +1,330 @@
+// Device arithmetic of the hybrid LBM time step (arXiv 2607.07432,
+// Sec. 2.2 and App. A): equilibrium (Eq. feq), HRR regularized collision
+// (Eqs. fneq, pi2, pi3) with the force populations (Eqs. fi, af2), the
+// finite-difference quantities it needs, and the face flux of the total
+// energy (Eq. energy with Eqs. fluxx-z and the MUSCL-Hancock face values of
+// Eq. linear).  The functions are templated on the lattice L and the
+// compute type C and take accessors for neighbouring data, so that the
+// same arithmetic serves the global-memory and the shared-memory kernels.
+#pragma once
+#include "lattice.cuh"
+
+namespace lbmib {
+
+template <class C>
+struct Phys {
+  C cs2, Cv, Cp, mu, lam, sigma;
+  int theta_tau;  // 1: tau_LB = mu / (rho c_s^2 theta)
+  int use_ac;
+};
+
+// corrected macroscopic state of one node (after the IB forcing)
+template <class C>
+struct Macro {
+  C rho, u[3], th, E;
+};
+
+// Eq. feq for population I (compile-time index)
+template <class L, class C, int I>
+__device__ __forceinline__ C feq_i(C rho, const C* u, C th) {
+  constexpr int D = L::D;
+  const C cs2 = C(kCs2);
+  C t1 = C(0);
+  sfor<0, D>([&](auto A) {
+    constexpr int a = decltype(A)::value;
+    if constexpr (L::c(I, a) != 0) t1 += C(L::c(I, a)) * rho * u[a];
+  });
+  t1 = t1 / cs2;
+  C t2 = C(0);
+  sfor<0, D>([&](auto A) {
+    sfor<0, D>([&](auto B) {
+      constexpr int a = decltype(A)::value, b = decltype(B)::value;
+      constexpr double h = H2<L>(I, a, b);
+      if constexpr (h != 0.0) t2 += C(h) * rho * u[a] * u[b];
+    });
+  });
+  t2 = t2 / (C(2) * cs2 * cs2);
+  C t3 = C(0);
+  sfor<0, L::N3>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr double h = H3r<L>(k, I);
+    if constexpr (h != 0.0) {
+      constexpr double nk = N3r<L>(k);
+      C A = C(0);
+      sfor<0, L::h3terms(k)>([&](auto T) {
+        constexpr int t = decltype(T)::value;
+        constexpr int a = L::h3idx(k, t, 0), b = L::h3idx(k, t, 1), g = L::h3idx(k, t, 2);
+        A += C(L::h3sign(k, t)) * (rho * u[a] * u[b] * u[g]);
+      });
+      t3 += C(h) * A / C(nk);
+    }
+  });
+  constexpr double wi = L::w(I);
+  constexpr double cth = (L::w(I) - (I == 0 ? 1.0 : 0.0)) / L::w(I);
+  const C tth = C(cth) * rho * (th - C(1));
+  return C(wi) * (rho + tth + t1 + t2 + t3);
+}
+
+// Velocity gradient du[a][b] = d u_a / d x_b and a^C (reading of the term
+// of Eq. af2 that the paper only cites): with m = rho (1-theta) u,
+// a^C_ab = c_s^2 [d_b m_a + d_a m_b - (2/D) d_ab div m] - d_ab d_a(rho u_a^3).
+// Central differences; MacroAt(dx,dy,dz) returns the neighbour's Macro.
+template <class L, class C, class MacroAt>
+__device__ __forceinline__ void gradients(const MacroAt& M, C du[3][3], C aC[3][3], int use_ac) {
+  constexpr int D = L::D;
+  C dm[3][3];
+  C dcube[3];
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const Macro<C> p = M(b == 0 ? 1 : 0, b == 1 ? 1 : 0, b == 2 ? 1 : 0);
+    const Macro<C> m = M(b == 0 ? -1 : 0, b == 1 ? -1 : 0, b == 2 ? -1 : 0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      du[a][b] = (p.u[a] - m.u[a]) * C(0.5);
+      const C mp = p.rho * (C(1) - p.th) * p.u[a];
+      const C mm = m.rho * (C(1) - m.th) * m.u[a];
+      dm[a][b] = (mp - mm) * C(0.5);
+    }
+    dcube[b] = (p.rho * (p.u[b] * p.u[b] * p.u[b]) - m.rho * (m.u[b] * m.u[b] * m.u[b])) * C(0.5);
+  }
+  if (!use_ac) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) aC[a][b] = C(0);
+    return;
+  }
+  C divm = C(0);
+#pragma unroll
+  for (int g = 0; g < D; ++g) divm += dm[g][g];
+  const C cs2 = C(kCs2);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      C v = cs2 * (dm[a][b] + dm[b][a]);
+      if (a == b) v = v - cs2 * (C(2) / C(D)) * divm - dcube[a];
+      aC[a][b] = v;
+    }
+}
+
+// expand stored deviator slots to a full symmetric traceless tensor
+template <class L, class C>
+__device__ __forceinline__ void dev_expand(const C* s, C T[3][3]) {
+  constexpr int D = L::D;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const int k = dev_slot<L>(a, b);
+      if (k >= 0) T[a][b] = s[k];
+    }
+  if (D == 2) {
+    T[1][1] = -s[0];
+  } else {
+    T[2][2] = -s[0] - s[1];
+  }
+}
+
+// HRR collision at one node (Eq. LB with dt = 1, Eqs. fi, af2, fneq, pi2,
+// pi3).  fbar: post-stream populations of the node; m: corrected macros;
+// du, aC: gradients; P_prev, dAFp: rho(1-theta) and the deviator of a^F of
+// the previous step; fu: IB force density at the node.  Outputs f^col, the
+// new rho(1-theta) and the deviator of a^F (NDEV slots).
+template <class L, class C>
+__device__ __forceinline__ void collide(const C* fbar, const Macro<C>& m, const C du[3][3],
+                                        const C aC[3][3], C P_prev, const C* dAFp, const C* fu,
+                                        const Phys<C>& ph, C* fcol, C& P_new, C* dAF_new) {
+  constexpr int D = L::D;
+  constexpr int Q = L::Q;
+  const C cs2 = C(kCs2);
+  C div = C(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) div += du[a][a];
+  const C P = m.rho * (C(1) - m.th);
+  const C dPdt = P - P_prev;
+  C aF[3][3];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      C v = aC[a][b] + fu[a] * m.u[b] + fu[b] * m.u[a];
+      if (a == b) v = v + (C(2) / C(D)) * m.rho * cs2 * div - cs2 * dPdt;
+      aF[a][b] = v;
+    }
+  C feq[Q];
+  sfor<0, Q>([&](auto I) { feq[decltype(I)::value] = feq_i<L, C, decltype(I)::value>(m.rho, m.u, m.th); });
+  const C th_m = ph.theta_tau ? m.th : C(1);
+  const C tau_lb = ph.mu / (m.rho * cs2 * th_m);
+  const C tau_bar = tau_lb + C(0.5);
+  C Fp[3][3];
+  dev_expand<L, C>(dAFp, Fp);
+  C Pi[3][3];
+  sfor<0, D>([&](auto A) {
+    sfor<decltype(A)::value, D>([&](auto B) {
+      constexpr int a = decltype(A)::value, b = decltype(B)::value;
+      C s = C(0);
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr double proj = double(L::c(i, a) * L::c(i, b)) - (a == b ? double(c2<L>(i)) / D : 0.0);
+        if constexpr (proj != 0.0) s = s + C(proj) * (fbar[i] - feq[i]);
+      });
+      s = s + C(0.5) * Fp[a][b];
+      const C S = du[a][b] + du[b][a] - (a == b ? (C(2) / C(D)) * div : C(0));
+      Pi[a][b] = ph.sigma * s - (C(1) - ph.sigma) * m.rho * cs2 * th_m * tau_bar * S;
+      Pi[b][a] = Pi[a][b];
+    });
+  });
+  // third-order combinations of Eq. pi3
+  C A3[L::N3];
+  sfor<0, L::N3>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    C A = C(0);
+    sfor<0, L::h3terms(k)>([&](auto T) {
+      constexpr int t = decltype(T)::value;
+      constexpr int a = L::h3idx(k, t, 0), b = L::h3idx(k, t, 1), g = L::h3idx(k, t, 2);
+      A += C(L::h3sign(k, t)) * (m.u[a] * Pi[b][g] + m.u[b] * Pi[g][a] + m.u[g] * Pi[a][b]);
+    });
+    A3[k] = A;
+  });
+  const C omega = C(1) - C(1) / tau_bar;
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    C t2 = C(0);
+    sfor<0, D>([&](auto A) {
+      sfor<0, D>([&](auto B) {
+        constexpr int a = decltype(A)::value, b = decltype(B)::value;
+        constexpr double h = H2<L>(i, a, b);
+        if constexpr (h != 0.0) t2 += C(h) * Pi[a][b];
+      });
+    });
+    t2 = t2 / (C(2) * cs2 * cs2);
+    C t3 = C(0);
+    sfor<0, L::N3>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      constexpr double h = H3r<L>(k, i);
+      constexpr double nk = N3r<L>(k);
+      if constexpr (h != 0.0) t3 += C(h) * A3[k] / C(nk);
+    });
+    const C fneq = C(L::w(i)) * (t2 + t3);
+    C f1 = C(0);
+    sfor<0, D>([&](auto A) {
+      constexpr int a = decltype(A)::value;
+      if constexpr (L::c(i, a) != 0) f1 += C(L::c(i, a)) * fu[a];
+    });
+    f1 = f1 / cs2;
+    C f2 = C(0);
+    sfor<0, D>([&](auto A) {
+      sfor<0, D>([&](auto B) {
+        constexpr int a = decltype(A)::value, b = decltype(B)::value;
+        constexpr double h = H2<L>(i, a, b);
+        if constexpr (h != 0.0) f2 += C(h) * aF[a][b];
+      });
+    });
+    const C Fi = C(L::w(i)) * (f1 + f2 / (C(2) * cs2 * cs2));
+    fcol[i] = feq[i] + omega * fneq + C(0.5) * Fi;
+  });
+  P_new = P;
+  C tr = C(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) tr += aF[a][a];
+  sfor<0, D>([&](auto A) {
+    sfor<decltype(A)::value, D>([&](auto B) {
+      constexpr int a = decltype(A)::value, b = decltype(B)::value;
+      constexpr int k = dev_slot<L>(a, b);
+      if constexpr (k >= 0) dAF_new[k] = aF[a][b] - (a == b ? tr / C(D) : C(0));
+    });
+  });
+}
+
+// MUSCL-Hancock face value of Eq. linear at the face between cells 1 and 2
+// along the axis; phi0..phi3 are the values at cells x-1, x, x+1, x+2 and
+// u1, u2 the axial velocities of cells x and x+1.
+template <class C>
+__device__ __forceinline__ C muscl(C phi0, C phi1, C phi2, C phi3, C u1, C u2) {
+  const C ut = C(0.5) * (u1 + u2);
+  if (ut >= C(0)) {
+    const C sg = u1 > C(0) ? C(1) : (u1 < C(0) ? C(-1) : C(0));
+    const C eta = (C(2) * u1 - sg) / C(3);
+    const C delta = C(0.5) * ((C(1) + eta) * (phi1 - phi0) + (C(1) - eta) * (phi2 - phi1));
+    const C pp = phi1 + C(0.5) * delta;
+    const C pm = phi1 - C(0.5) * delta;
+    return pp + C(0.5) * u1 * (pm - pp);
+  } else {
+    const C sg = u2 > C(0) ? C(1) : (u2 < C(0) ? C(-1) : C(0));
+    const C eta = (C(2) * u2 - sg) / C(3);
+    const C delta = C(0.5) * ((C(1) + eta) * (phi2 - phi1) + (C(1) - eta) * (phi3 - phi2));
+    const C pp = phi2 + C(0.5) * delta;
+    const C pm = phi2 - C(0.5) * delta;
+    return pm + C(0.5) * u2 * (pm - pp);
+  }
+}
+
+// Total-energy flux F^{rhoE}_{+axis/2} through the face x + e_axis/2
+// (Eq. energy).  MacroAlong(k) returns the Macro of cell x + k e_axis
+// (k = -1..2); FcolAt(i, dx, dy, dz) returns f^col_i at x + (dx,dy,dz).
+template <class L, class C, int AX, class MacroAlong, class FcolAt>
+__device__ __forceinline__ C energy_face_flux(const MacroAlong& MA, const FcolAt& FC, const Phys<C>& ph) {
+  constexpr int D = L::D;
+  const C cs2 = C(kCs2);
+  // LB mass and momentum fluxes (Eqs. fluxx-z and the rule below them)
+  C Frho = C(0);
+  C Fm[3] = {C(0), C(0), C(0)};
+  auto add = [&](C v, auto I) {
+    constexpr int i = decltype(I)::value;
+    Frho = Frho + v;
+    sfor<0, D>([&](auto B) {
+      constexpr int b = decltype(B)::value;
+      if constexpr (L::c(i, b) != 0) Fm[b] = Fm[b] + C(L::c(i, b)) * v;
+    });
+  };
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int ca = L::c(i, AX);
+    if constexpr (ca != 0) {
+      constexpr int b0 = (ca < 0 && AX == 0) ? 1 : 0;
+      constexpr int b1 = (ca < 0 && AX == 1) ? 1 : 0;
+      constexpr int b2 = (ca < 0 && AX == 2) ? 1 : 0;
+      constexpr int t = transverse_axis<L>(i, AX);
+      if constexpr (t < 0) {
+        add(C(ca) * FC(i, b0, b1, b2), I);
+      } else {
+        constexpr int o0 = b0 - (t == 0 ? L::c(i, 0) : 0);
+        constexpr int o1 = b1 - (t == 1 ? L::c(i, 1) : 0);
+        constexpr int o2 = b2 - (t == 2 ? L::c(i, 2) : 0);
+        add(C(0.5 * ca) * FC(i, b0, b1, b2), I);
+        add(C(0.5 * ca) * FC(i, o0, o1, o2), I);
+      }
+    }
+  });
+  const Macro<C> m0 = MA(-1), m1 = MA(0), m2 = MA(1), m3 = MA(2);
+  const C p0 = m0.rho * cs2 * m0.th, p1 = m1.rho * cs2 * m1.th;
+  const C p2 = m2.rho * cs2 * m2.th, p3 = m3.rho * cs2 * m3.th;
+  const C u1 = m1.u[AX], u2 = m2.u[AX];
+  const C FH = muscl<C>((m0.E + p0) * m0.u[AX], (m1.E + p1) * m1.u[AX], (m2.E + p2) * m2.u[AX],
+                        (m3.E + p3) * m3.u[AX], u1, u2);
+  const C Fr = muscl<C>(m0.rho * m0.u[AX], m1.rho * m1.u[AX], m2.rho * m2.u[AX], m3.rho * m3.u[AX], u1, u2);
+  C k1 = C(0), k2 = C(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    k1 += m1.u[b] * m1.u[b];
+    k2 += m2.u[b] * m2.u[b];
+  }
+  k1 = C(0.5) * k1;
+  k2 = C(0.5) * k2;
+  const C hk = C(0.5) * ((ph.Cp * m1.th - k1) + (ph.Cp * m2.th - k2));
+  C FE = FH + hk * (Frho - Fr);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const C Fb = muscl<C>(m0.rho * m0.u[AX] * m0.u[b] + (AX == b ? p0 : C(0)),
+                          m1.rho * m1.u[AX] * m1.u[b] + (AX == b ? p1 : C(0)),
+                          m2.rho * m2.u[AX] * m2.u[b] + (AX == b ? p2 : C(0)),
+                          m3.rho * m3.u[AX] * m3.u[b] + (AX == b ? p3 : C(0)), u1, u2);
+    const C ub = C(0.5) * (m1.u[b] + m2.u[b]);
+    FE = FE + ub * (Fm[b] - Fb);
+  }
+  FE = FE - ph.lam * (m2.th - m1.th);
+  return FE;
+}
+
+}  // namespace lbmib

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in include/lbmib.h (argument marshalling
+only: every step of the method runs in the CUDA library).
+
+Host arrays are numpy; device arrays may be torch CUDA tensors (their
+data_ptr is passed through).  The library must be built first
+(``python -m paper_2607_07432_b300.build``); importing this module without
+it raises ImportError rather than falling back to anything else.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "liblbmib.so")
+
+D2Q9, D3Q19 = 0, 1
+FP64, FP32, FP16DEV, BF16DEV = 0, 1, 2, 3
+DIBM, FODIBM, FODIBM_R = 0, 1, 2
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD = 0, 1, 2, 3
+TAU_THETA, TAU_LITERAL = 0, 1
+SHAPE_SPHERE, SHAPE_ELLIPSE, SHAPE_POLYGON, SHAPE_MASK = 0, 1, 2, 3
+STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EGEOM",
+          5: "LBM_ENAN", 6: "LBM_ETIMEOUT", 7: "LBM_ESTATE", 8: "LBM_EUNSUPPORTED"}
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
+
+EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", "ib_set_geometry",
+           "lbm_step", "lbm_check", "lbm_get_fields", "lbm_get_state", "lbm_set_state", "lbm_set_fields",
+           "lbm_get_wall_loads", "lbm_get_constants", "ib_get_sizes", "ib_get_setup", "lbm_profile",
+           "lbm_get_profile", "lbm_launch_count"]
+
+
+class Config(ct.Structure):
+    _fields_ = [("struct_size", ct.c_size_t), ("lattice", ct.c_int), ("precision", ct.c_int),
+                ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("mach", ct.c_double),
+                ("reynolds", ct.c_double), ("ref_length", ct.c_double), ("prandtl", ct.c_double),
+                ("gamma", ct.c_double), ("theta_inf", ct.c_double), ("inflow_dir", ct.c_double * 3),
+                ("sigma_hrr", ct.c_double), ("d_n", ct.c_double), ("method", ct.c_int),
+                ("bc", ct.c_int * 6), ("tau_mode", ct.c_int), ("use_ac", ct.c_int), ("device", ct.c_int),
+                ("stream", ct.c_void_p)]
+
+
+class Geometry(ct.Structure):
+    _fields_ = [("struct_size", ct.c_size_t), ("n_points", ct.c_int), ("X", ct.c_void_p),
+                ("normals", ct.c_void_p), ("tbc", ct.c_void_p), ("u_target", ct.c_void_p),
+                ("t_value", ct.c_void_p), ("shape", ct.c_int), ("center", ct.c_double * 3),
+                ("radius", ct.c_double), ("radii", ct.c_double * 2), ("cos_a", ct.c_double),
+                ("sin_a", ct.c_double), ("n_poly", ct.c_int), ("poly", ct.c_void_p), ("mask", ct.c_void_p)]
+
+
+def load():
+    if not os.path.exists(LIBPATH):
+        raise ImportError("liblbmib.so is not built; run python -m paper_2607_07432_b300.build")
+    lib = ct.CDLL(LIBPATH)
+    lib.lbm_last_error.restype = ct.c_char_p
+    lib.lbm_launch_count.restype = ct.c_longlong
+    lib.lbm_create.argtypes = [ct.POINTER(Config), ct.POINTER(ct.c_void_p)]
+    for name in ("lbm_step",):
+        getattr(lib, name).argtypes = [ct.c_void_p, ct.c_int]
+    for name in ("lbm_destroy", "lbm_check", "lbm_last_error", "lbm_launch_count"):
+        getattr(lib, name).argtypes = [ct.c_void_p]
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ct.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ct.c_void_p)
+
+
+class Solver:
+    """One case on one GPU (lbm_create ... lbm_destroy)."""
+
+    def __init__(self, lattice="D2Q9", precision="fp32", shape=(64, 64), mach=0.1, reynolds=100.0,
+                 ref_length=10.0, prandtl=0.71, gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0),
+                 sigma=0.98, d_n=1.5, method=FODIBM_R, bc=None, tau_mode=TAU_THETA, use_ac=True,
+                 device=0, stream=None):
+        L = lib()
+        cfg = Config()
+        L.lbm_config_default(ct.byref(cfg))
+        self.D = 2 if lattice in ("D2Q9", D2Q9) else 3
+        self.Q = 9 if self.D == 2 else 19
+        cfg.lattice = D2Q9 if self.D == 2 else D3Q19
+        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg.nx, cfg.ny = int(shape[0]), int(shape[1])
+        cfg.nz = int(shape[2]) if self.D == 3 else 1
+        cfg.mach, cfg.reynolds, cfg.ref_length = mach, reynolds, ref_length
+        cfg.prandtl, cfg.gamma, cfg.theta_inf = prandtl, gamma, theta_inf
+        for a in range(3):
+            cfg.inflow_dir[a] = float(inflow_dir[a]) if a < len(inflow_dir) else 0.0
+        cfg.sigma_hrr, cfg.d_n, cfg.method = sigma, d_n, int(method)
+        bc = list(bc) if bc is not None else [BC_PERIODIC] * (2 * self.D)
+        for k in range(6):
+            cfg.bc[k] = int(bc[k]) if k < len(bc) else BC_PERIODIC
+        cfg.tau_mode, cfg.use_ac, cfg.device = int(tau_mode), int(bool(use_ac)), int(device)
+        cfg.stream = ct.c_void_p(stream) if stream else None
+        self.cfg = cfg
+        self.shape = tuple(int(s) for s in shape)
+        self.N = int(np.prod(self.shape))
+        self.zyx = tuple(reversed(self.shape))
+        h = ct.c_void_p()
+        st = L.lbm_create(ct.byref(cfg), ct.byref(h))
+        if st:
+            raise LBMError(st, "lbm_create failed")
+        self.h = h
+        self.NL = 0
+
+    def _check(self, st):
+        if st:
+            raise LBMError(st, lib().lbm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- geometry ----------------------------------------------------------
+    def set_geometry(self, geo):
+        D = self.D
+        X = np.ascontiguousarray(geo["X"], dtype=np.float64).reshape(-1, D)
+        N = np.ascontiguousarray(geo["normals"], dtype=np.float64).reshape(-1, D)
+        NL = X.shape[0]
+        tbc = np.ascontiguousarray(geo.get("tbc", np.zeros(NL)), dtype=np.int32)
+        ut = np.ascontiguousarray(geo.get("u_target", np.zeros((NL, D))), dtype=np.float64).reshape(NL, D)
+        tv = np.ascontiguousarray(geo["t_value"], dtype=np.float64).reshape(NL)
+        g = Geometry()
+        g.struct_size = ct.sizeof(Geometry)
+        g.n_points = NL
+        g.X, g.normals, g.tbc, g.u_target, g.t_value = _ptr(X), _ptr(N), _ptr(tbc), _ptr(ut), _ptr(tv)
+        sh = geo["shape"]
+        keep = [X, N, tbc, ut, tv]
+        kind = sh["kind"]
+        if kind in ("circle", "sphere"):
+            g.shape = SHAPE_SPHERE
+            for a in range(D):
+                g.center[a] = float(sh["center"][a])
+            g.radius = float(sh["radius"])
+        elif kind == "ellipse":
+            g.shape = SHAPE_ELLIPSE
+            g.center[0], g.center[1] = float(sh["center"][0]), float(sh["center"][1])
+            g.radii[0], g.radii[1] = float(sh["radii"][0]), float(sh["radii"][1])
+            g.cos_a, g.sin_a = float(sh["cos"]), float(sh["sin"])
+        elif kind == "polygon":
+            g.shape = SHAPE_POLYGON
+            P = np.ascontiguousarray(sh["poly"], dtype=np.float64)
+            keep.append(P)
+            g.n_poly, g.poly = P.shape[0], _ptr(P)
+        elif kind == "mask":
+            g.shape = SHAPE_MASK
+            M = np.ascontiguousarray(sh["mask"], dtype=np.uint8)
+            keep.append(M)
+            g.mask = _ptr(M)
+        else:
+            raise ValueError(kind)
+        self._check(lib().ib_set_geometry(self.h, ct.byref(g)))
+        self.NL = NL
+
+    # -- time stepping -----------------------------------------------------
+    def step(self, n=1):
+        self._check(lib().lbm_step(self.h, int(n)))
+
+    def check(self):
+        self._check(lib().lbm_check(self.h))
+
+    # -- data --------------------------------------------------------------
+    def fields(self):
+        N, D = self.N, self.D
+        rho, u, T, p = np.empty(N), np.empty(D * N), np.empty(N), np.empty(N)
+        self._check(lib().lbm_get_fields(self.h, 0, _ptr(rho), _ptr(u), _ptr(T), _ptr(p)))
+        z = self.zyx
+        return rho.reshape(z), u.reshape((D,) + z), T.reshape(z), p.reshape(z)
+
+    def fields_device(self, rho, u, T, p):
+        self._check(lib().lbm_get_fields(self.h, 1, _ptr(rho), _ptr(u), _ptr(T), _ptr(p)))
+
+    def state(self):
+        f = np.empty(self.Q * self.N)
+        E = np.empty(self.N)
+        self._check(lib().lbm_get_state(self.h, 0, _ptr(f), _ptr(E)))
+        return f.reshape((self.Q,) + self.zyx), E.reshape(self.zyx)
+
+    def set_state(self, f, E):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        self._check(lib().lbm_set_state(self.h, 0, _ptr(f), _ptr(E)))
+
+    def set_fields(self, rho, u, T, device=False):
+        if device:
+            self._check(lib().lbm_set_fields(self.h, 1, _ptr(rho), _ptr(u), _ptr(T)))
+            return
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        self._check(lib().lbm_set_fields(self.h, 0, _ptr(rho), _ptr(u), _ptr(T)))
+
+    def wall_loads(self, per_point=False):
+        force = (ct.c_double * 3)()
+        heat, work = ct.c_double(), ct.c_double()
+        pp = np.empty(self.NL * (self.D + 2)) if per_point else None
+        self._check(lib().lbm_get_wall_loads(self.h, force, ct.byref(heat), ct.byref(work), _ptr(pp)))
+        out = dict(force=np.array(force[:self.D]), heat=heat.value, work=work.value)
+        if per_point:
+            pp = pp.reshape(self.NL, self.D + 2)
+            out.update(F=pp[:, :self.D].copy(), W=pp[:, self.D].copy(), Q=pp[:, self.D + 1].copy())
+        return out
+
+    def constants(self):
+        out = (ct.c_double * 8)()
+        self._check(lib().lbm_get_constants(self.h, out))
+        keys = ["u_mag", "mu", "lam", "theta_inf", "Cv", "Cp", "rho_inf", "gamma"]
+        return dict(zip(keys, list(out)))
+
+    def ib_setup(self):
+        nr, nnz, nl = ct.c_int(), ct.c_int(), ct.c_int()
+        self._check(lib().ib_get_sizes(self.h, ct.byref(nr), ct.byref(nnz), ct.byref(nl)))
+        nr, nnz, nl = nr.value, nnz.value, nl.value
+        D = self.D
+        out = dict(phi=np.empty(nl), W=np.empty(nl), Xstar=np.empty(nl * D), dBV=np.empty(nl),
+                   inside=np.empty(self.N, dtype=np.uint8), row_ptr=np.empty(nr + 1, dtype=np.int32),
+                   cell_id=np.empty(nr, dtype=np.int32), col=np.empty(nnz, dtype=np.int32), wt=np.empty(nnz))
+        self._check(lib().ib_get_setup(self.h, *[_ptr(out[k]) for k in
+                                                 ("phi", "W", "Xstar", "dBV", "inside", "row_ptr", "cell_id",
+                                                  "col", "wt")]))
+        out["Xstar"] = out["Xstar"].reshape(nl, D)
+        out["inside"] = out["inside"].reshape(self.zyx).astype(bool)
+        return out
+
+    def profile(self, enable=True, reset=True):
+        self._check(lib().lbm_profile(self.h, int(enable), int(reset)))
+
+    def get_profile(self):
+        ms = (ct.c_double * 5)()
+        n = (ct.c_longlong * 5)()
+        self._check(lib().lbm_get_profile(self.h, ms, n))
+        names = ["step", "ib_force", "ib_spread", "bc", "other"]
+        return {k: (ms[i], n[i]) for i, k in enumerate(names)}
+
+    def launch_count(self):
+        return int(lib().lbm_launch_count(self.h))
