@@ -1,0 +1,252 @@
+"""Benchmark: MLUPS of the full time step (IB on) of the 3D sphere case.
+
+Workload (the 3D case the headline metric is quoted on): D3Q19 hybrid LBM,
+grid 256x192x192, sphere D = 48 at (64, 96, 96), 7292 Lagrangian points
+(geodesic icosphere, frequency 27), Ma 0.3, Re 300, isothermal wall at
+1.1 T_inf, FODIBM-R, inlet / outlet in x, far field elsewhere, FP32.
+A step is one pass of the whole hot path (IB interpolation + forcing,
+spreading, collision, streaming, energy update, boundaries).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas of
+the case, one per rank (the single case is not partitioned), weak scaling.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS with IBM on (% of HBM roofline); time-to-steady at 0.1% drag vs plain FP32"
+UNIT = "MLUPS"
+SHAPE = (256, 192, 192)
+CASE = dict(lattice="D3Q19", shape=SHAPE, mach=0.3, reynolds=300.0, ref_length=48.0,
+            center=(64.0, 96.0, 96.0), diameter=48.0, frequency=27)
+# algorithmic bytes per lattice update of the FP32 D3Q19 step: populations
+# read and written once (2 * 19 * 4) plus the state the method carries between
+# steps, read and written once: rho E, rho(1-theta) of the previous step and
+# the deviator of a^F of the previous step (5 components), 7 * 2 * 4.
+BYTES_PER_LU = {("D3Q19", "fp32"): 2 * 19 * 4 + 2 * 7 * 4, ("D3Q19", "fp16"): 2 * 19 * 2 + 2 * 7 * 4,
+                ("D3Q19", "bf16"): 2 * 19 * 2 + 2 * 7 * 4, ("D3Q19", "fp64"): 2 * 19 * 8 + 2 * 7 * 8,
+                ("D2Q9", "fp32"): 2 * 9 * 4 + 2 * 4 * 4, ("D2Q9", "fp64"): 2 * 9 * 8 + 2 * 4 * 8}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_case(lbmib, inputs, precision):
+    c = CASE
+    s = lbmib.Solver(c["lattice"], precision, c["shape"], mach=c["mach"], reynolds=c["reynolds"],
+                     ref_length=c["ref_length"],
+                     bc=[lbmib.BC_INLET, lbmib.BC_OUTLET] + [lbmib.BC_FARFIELD] * 4)
+    th = s.constants()["theta_inf"]
+    geo = inputs.icosphere(c["center"], c["diameter"], c["frequency"], tbc=0, t_value=1.1 * th)
+    s.set_geometry(geo)
+    return s, geo
+
+
+def oracle_sample(steps_budget_s=15.0, max_steps=None):
+    """The oracle on a 64x48x48 downscale of the same case (D = 12, 492
+    points); returns MLUPS, steps and nodes."""
+    from oracle import lbm
+    from paper_2607_07432_b300 import inputs
+    prm = lbm.Params("D3Q19", (64, 48, 48), mach=CASE["mach"], reynolds=CASE["reynolds"], ref_length=12.0,
+                     bc=[1, 2, 3, 3, 3, 3])
+    geo = inputs.icosphere((16.0, 24.0, 24.0), 12.0, 7, tbc=0, t_value=1.1 * prm.theta_inf)
+    sim = lbm.Sim(prm, geo)
+    sim.step()  # warm-up
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        sim.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if el > steps_budget_s or (max_steps and n >= max_steps):
+            break
+    nodes = 64 * 48 * 48
+    return nodes * n / el / 1e6, n, nodes, el
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    mlups, n, nodes, el = oracle_sample(steps_budget_s=max(5.0, 10.0 * args.steps / 20.0))
+    line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "3D sphere D3Q19 256x192x192 (oracle on its 64x48x48 downscale)",
+                       "precision": "fp64", "method": "FODIBM-R"},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d steps of the 64x48x48 downscale (D=12, 492 points), %.1f s" % (n, el)},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    args.warmup = max(args.warmup, 3)
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2607_07432_b300 import inputs, lbmib
+    s, geo = build_case(lbmib, inputs, args.precision)
+    N = int(np.prod(SHAPE))
+    s.step(args.warmup)
+    s.check()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-timed region: K steps, inputs resident in HBM (state 1.5 GB,
+    # larger than L2, so no flush is needed between steps)
+    clocks = ClockSampler(local)
+    l0 = s.launch_count()
+    s.profile(True, True)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(args.steps)
+    e1.record()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = s.get_profile()
+    s.profile(False, True)
+    launches = s.launch_count() - l0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * N * args.steps / (ms / 1e3) / 1e6
+    s.check()
+
+    # end-to-end through the public API with host buffers: the job uploads
+    # its initial fields from pinned host memory, steps, and reads the wall
+    # loads back every step; all copies are inside the timed region
+    c = s.constants()
+    rho0 = torch.full((N,), 1.0, dtype=torch.float64).pin_memory()
+    u0 = torch.zeros((3 * N,), dtype=torch.float64)
+    u0[:N] = c["u_mag"]
+    u0 = u0.pin_memory()
+    T0 = torch.full((N,), c["theta_inf"], dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    s.set_fields(rho0.numpy(), u0.numpy(), T0.numpy())
+    for _ in range(args.steps):
+        s.step(1)
+        s.wall_loads()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(N * 5 * 8 / args.steps), "d2h_bytes_per_step": 5 * 8}
+
+    if rank != 0:
+        return
+    peak, peak_kind = peaks()
+    bpl = BYTES_PER_LU[(CASE["lattice"], args.precision)]
+    step_ms, step_n = prof["step"]
+    other_ms, other_n = prof["other"]
+    # dominant kernel class: the LBM step (collision + streaming + energy;
+    # the separate macroscopic pass of the unfused form counts with it)
+    kern_ms = (step_ms + other_ms) / args.steps
+    achieved = bpl * N / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind, "bytes_per_lu": bpl,
+            "kernel_ms_per_step": kern_ms,
+            "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        mlups, n, nodes, el = oracle_sample(15.0)
+        cpu = {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d steps of the 64x48x48 downscale (D=12, 492 points), %.1f s" % (n, el)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": "3D sphere D3Q19 256x192x192, D=48, 7292 points, Ma 0.3, Re 300, "
+                                   "isothermal wall, FODIBM-R",
+                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state 1.5 GB > L2, no flush"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
+if __name__ == "__main__":
+    main()

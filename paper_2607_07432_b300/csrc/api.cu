@@ -4,7 +4,9 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <cub/cub.cuh>
 #include <string>
 #include <vector>
@@ -50,7 +52,7 @@ double theta_rule(double mach, double gamma, double re, double L, double pr, int
 void free_ib(lbm_handle* h) {
   void* ptrs[] = {h->inside, h->X, h->nrm, h->uB, h->tB, h->tbc, h->sten_node, h->psten_node, h->sten_w,
                   h->sten_x, h->psten_w, h->phi, h->W, h->Xstar, h->dBV, h->row_ptr, h->cell_id, h->col,
-                  h->slot_of_entry, h->wt, h->row_of_node, h->G, h->FU, h->WQ, h->loads};
+                  h->slot_of_entry, h->wt, h->row_of_node, h->forced, h->G, h->FU, h->WQ, h->loads};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->inside = nullptr;
@@ -61,6 +63,7 @@ void free_ib(lbm_handle* h) {
   h->row_ptr = h->cell_id = h->col = h->slot_of_entry = nullptr;
   h->wt = nullptr;
   h->row_of_node = nullptr;
+  h->forced = nullptr;
   h->G = h->FU = h->WQ = h->loads = nullptr;
   h->has_ib = false;
   h->NL = h->n_rows = h->nnz = 0;
@@ -160,8 +163,19 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
       s = fail(h, LBM_ENOMEM, "device allocation failed");
     }
   };
+  {
+    const char* env = std::getenv("LBMIB_UNFUSED");
+    h->use_fused = (env && env[0] == '1') ? 0 : 1;
+    const char* zc = std::getenv("LBMIB_ZCHUNK");
+    if (zc) h->zchunk = std::max(1, std::atoi(zc));
+  }
   alloc(&h->f, N * h->Q * h->ssize);
-  alloc(&h->fcol, N * h->Q * (h->use_fused ? h->ssize : h->csize));
+  if (h->use_fused) {
+    alloc(&h->f2, N * h->Q * h->ssize);
+    alloc(&h->M2, N * (D + 2) * h->csize);
+  } else {
+    alloc(&h->fcol, N * h->Q * h->csize);
+  }
   alloc(&h->M, N * (D + 3) * h->csize);
   alloc(&h->E, N * h->csize);
   for (int k2 = 0; k2 < 2; ++k2) {
@@ -184,7 +198,7 @@ void lbm_destroy(lbm_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   free_ib(h);
-  void* ptrs[] = {h->f, h->fcol, h->M, h->E, h->P[0], h->P[1], h->A[0], h->A[1], h->feq_inf, h->d_bad};
+  void* ptrs[] = {h->f, h->f2, h->fcol, h->M, h->M2, h->E, h->P[0], h->P[1], h->A[0], h->A[1], h->feq_inf, h->d_bad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : h->ev_pool) cudaEventDestroy(e);
@@ -251,6 +265,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
   alloc((void**)&h->G, NL * (D + 2) * 8);
   alloc((void**)&h->loads, 8 * 8);
   alloc((void**)&h->row_of_node, N * 4);
+  alloc((void**)&h->forced, N);
   alloc((void**)&derr, 4);
   alloc((void**)&keys, (size_t)NL * KS * 8);
   alloc((void**)&keys_sorted, (size_t)NL * KS * 8);
@@ -290,6 +305,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     CK(cudaMemsetAsync(derr, 0, 4, h->st));
     CK(cudaMemsetAsync(count, 0, 4, h->st));
     CK(cudaMemsetAsync(h->row_of_node, 0xff, N * 4, h->st));
+    CK(cudaMemsetAsync(h->forced, 0, N, h->st));
     if ((s = launch(h, kProfOther, [&] { k_classify<<<nblk(N, 256), 256, 0, h->st>>>(h->g, D, sd, h->inside); })))
       goto done;
     IBSetupDev sdv;
@@ -383,7 +399,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
          })))
       goto done;
     if ((s = launch(h, kProfOther, [&] {
-           k_row_map<<<nblk(nrows, 256), 256, 0, h->st>>>(nrows, h->cell_id, h->row_of_node);
+           k_row_map<<<nblk(nrows, 256), 256, 0, h->st>>>(nrows, h->cell_id, h->row_of_node, h->forced);
          })))
       goto done;
     CK(cudaMemsetAsync(h->G, 0, NL * (D + 2) * 8, h->st));

@@ -77,6 +77,7 @@ struct Engine {
                                                              dev ? u : du, dev ? T : dT, C(h->Cv));
     });
     if (!s) s = reset_aux(h);
+    if (!s) s = refresh_moments(h);
     if (!dev) {
       cudaStreamSynchronize(h->st);
       cudaFree(dr);
@@ -107,16 +108,22 @@ struct Engine {
     s.tB = h->tB;
     s.G = h->G;
     lbm_status st = launch(h, kProfIBForce, [&] {
-      k_ib_force<L, S, C><<<nblk((long long)h->NL * 32, 128), 128, 0, h->st>>>(h->g, s, (const S*)h->f,
-                                                                             (const C*)h->E);
+      k_ib_force<L, S, C><<<nblk((long long)h->NL * 32, 128), 128, 0, h->st>>>(
+          h->g, s, (const S*)h->f, (const C*)h->E, h->use_fused ? (const C*)h->M : nullptr);
     });
     if (st) return st;
-    return launch(h, kProfIBSpread, [&] {
+    st = launch(h, kProfIBSpread, [&] {
       k_ib_spread<<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->n_rows, h->row_ptr, h->col, h->wt, h->G,
                                                           h->FU, h->WQ);
     });
+    if (st || !h->use_fused) return st;
+    return launch(h, kProfIBSpread, [&] {
+      k_apply_forcing<C><<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->g.N, h->n_rows, h->cell_id, h->FU,
+                                                                  h->WQ, (C*)h->M);
+    });
   }
   static lbm_status bc(lbm_handle* h) {
+    if (h->use_fused) return bc_fused(h);
     for (int face = 0; face < 2 * L::D; ++face) {
       if (h->cfg.bc[face] != LBM_BC_OUTLET) continue;
       FacePlane fp{face / 2, face % 2};
@@ -135,6 +142,42 @@ struct Engine {
       });
       if (s) return s;
     }
+    return LBM_OK;
+  }
+  static lbm_status bc_fused(lbm_handle* h) {
+    for (int face = 0; face < 2 * L::D; ++face) {
+      if (h->cfg.bc[face] != LBM_BC_OUTLET) continue;
+      FacePlane fp{face / 2, face % 2};
+      lbm_status s = launch(h, kProfBC, [&] {
+        k_bc_outlet_m<L, S, C><<<nblk(fp.count(h->g), 128), 128, 0, h->st>>>(h->g, (S*)h->f, (C*)h->M, fp.axis,
+                                                                            fp.side);
+      });
+      if (s) return s;
+    }
+    for (int face = 0; face < 2 * L::D; ++face) {
+      const int t = h->cfg.bc[face];
+      if (t != LBM_BC_INLET && t != LBM_BC_FARFIELD) continue;
+      FacePlane fp{face / 2, face % 2};
+      lbm_status s = launch(h, kProfBC, [&] {
+        k_bc_equilibrium_m<L, S, C><<<nblk(fp.count(h->g), 128), 128, 0, h->st>>>(
+            h->g, (S*)h->f, (C*)h->M, fp.axis, fp.side, (const C*)h->feq_inf, C(h->E_inf));
+      });
+      if (s) return s;
+    }
+    return LBM_OK;
+  }
+  // fused form: predicted moments from the populations and rho E
+  static lbm_status refresh_moments(lbm_handle* h) {
+    if (!h->use_fused) return LBM_OK;
+    return launch(h, kProfOther, [&] {
+      k_moments<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, (const S*)h->f, (const C*)h->E, (C*)h->M);
+    });
+  }
+  // fused form: rho E lives in the moment buffer; copy it out for readback
+  static lbm_status sync_energy(lbm_handle* h) {
+    if (!h->use_fused) return LBM_OK;
+    CK(cudaMemcpyAsync(h->E, (const C*)h->M + (size_t)(L::D + 1) * h->g.N, h->g.N * sizeof(C),
+                       cudaMemcpyDeviceToDevice, h->st));
     return LBM_OK;
   }
   static lbm_status step(lbm_handle* h) {
@@ -159,12 +202,14 @@ struct Engine {
   }
   static lbm_status fused_step(lbm_handle* h, const Phys<C>& ph);
   static lbm_status fields(lbm_handle* h, double* rho, double* u, double* T, double* p) {
+    if (lbm_status s0 = sync_energy(h)) return s0;
     return launch(h, kProfOther, [&] {
       k_fields<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, (const S*)h->f, (const C*)h->E, C(h->Cv),
                                                               C(h->R), rho, u, T, p);
     });
   }
   static lbm_status get_state(lbm_handle* h, double* f, double* E) {
+    if (lbm_status s0 = sync_energy(h)) return s0;
     return launch(h, kProfOther, [&] {
       k_get_state<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, (const S*)h->f, (const C*)h->E, f, E);
     });
@@ -175,9 +220,12 @@ struct Engine {
     });
     if (s) return s;
     h->sticky = LBM_OK;
-    return reset_aux(h);
+    s = reset_aux(h);
+    if (!s) s = refresh_moments(h);
+    return s;
   }
   static lbm_status health(lbm_handle* h, unsigned long long* bad) {
+    if (lbm_status s0 = sync_energy(h)) return s0;
     return launch(h, kProfOther, [&] {
       k_health<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, (const S*)h->f, (const C*)h->E, C(h->Cv),
                                                               bad);
@@ -193,20 +241,21 @@ template <class L, class S, class C>
 inline lbm_status Engine<L, S, C>::fused_step(lbm_handle* h, const Phys<C>& ph) {
   FusedArgs<S, C> a;
   a.f_in = (const S*)h->f;
-  a.f_out = (S*)h->fcol;  // the fused path ping-pongs populations through fcol
-  a.E_in = (const C*)h->E;
-  a.E_out = (C*)h->M;
+  a.f_out = (S*)h->f2;
+  a.M_in = (const C*)h->M;
+  a.M_out = (C*)h->M2;
   a.Pp = (const C*)h->P[h->cur];
   a.Pn = (C*)h->P[1 - h->cur];
   a.Ap = (const C*)h->A[h->cur];
   a.An = (C*)h->A[1 - h->cur];
-  a.row_of_node = h->has_ib ? h->row_of_node : nullptr;
+  a.forced = h->has_ib ? h->forced : nullptr;
+  a.cell_id = h->cell_id;
+  a.n_rows = h->n_rows;
   a.FU = h->FU;
-  a.WQ = h->WQ;
-  lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st); });
+  lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st, h->zchunk); });
   if (s) return s;
-  std::swap(h->f, h->fcol);
-  std::swap(h->E, h->M);
+  std::swap(h->f, h->f2);
+  std::swap(h->M, h->M2);
   return LBM_OK;
 }
 

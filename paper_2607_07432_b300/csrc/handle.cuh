@@ -37,7 +37,10 @@ struct lbm_handle {
   void* A[2] = {nullptr, nullptr};
   void* feq_inf = nullptr;
   int cur = 0;
-  int use_fused = 0;
+  int use_fused = 1;         // fused shared-memory step (0: unfused global-memory form)
+  int zchunk = 48;           // planes per CTA along z in the fused step
+  void* f2 = nullptr;        // second population buffer (fused form)
+  void* M2 = nullptr;        // second predicted-moment buffer (fused form)
   unsigned long long* d_bad = nullptr;
   // immersed boundary
   bool has_ib = false;
@@ -51,6 +54,7 @@ struct lbm_handle {
   int *row_ptr = nullptr, *cell_id = nullptr, *col = nullptr, *slot_of_entry = nullptr;
   double* wt = nullptr;
   int* row_of_node = nullptr;
+  unsigned char* forced = nullptr;
   double *G = nullptr, *FU = nullptr, *WQ = nullptr, *loads = nullptr;
   // bookkeeping
   std::string err;

@@ -360,10 +360,11 @@ static __global__ void k_csr_weights(int nnz, const int* col, const int* slot_of
   wt[e] = phi[l] * W[l] * sten_w[slot_of_entry[e]];
 }
 
-static __global__ void k_row_map(int n_rows, const int* cell_id, int* row_of_node) {
+static __global__ void k_row_map(int n_rows, const int* cell_id, int* row_of_node, unsigned char* forced) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
   row_of_node[cell_id[r]] = r;
+  forced[cell_id[r]] = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -390,20 +391,30 @@ static __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// predicted moments of one node from the post-stream populations (Sec. 2.2)
+// predicted moments of one node (Sec. 2.2): from the stored moments
+// rho, rho u, rho E when M is given, else from the post-stream populations
 template <class L, class S, class C>
-__device__ __forceinline__ void node_pred(const S* f, const C* E, long long N, long long n, double& rho,
-                                          double* j, double* u, double& T, double Cv) {
+__device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, long long N, long long n,
+                                          double& rho, double* j, double* u, double& T, double Cv) {
   constexpr int D = L::D;
-  rho = 0.0;
-  for (int a = 0; a < 3; ++a) j[a] = 0.0;
+  double En;
+  if (M) {
+    rho = double(M[n]);
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    const double v = double(load_pop<L, S, C>(f, i, N, n));
-    rho += v;
+    for (int a = 0; a < D; ++a) j[a] = double(M[(1 + a) * N + n]);
+    En = double(M[(1 + D) * N + n]);
+  } else {
+    rho = 0.0;
+    for (int a = 0; a < 3; ++a) j[a] = 0.0;
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-      if (L::c(i, a) != 0) j[a] += double(L::c(i, a)) * v;
+    for (int i = 0; i < L::Q; ++i) {
+      const double v = double(load_pop<L, S, C>(f, i, N, n));
+      rho += v;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (L::c(i, a) != 0) j[a] += double(L::c(i, a)) * v;
+    }
+    En = double(E[n]);
   }
   double uu = 0.0;
 #pragma unroll
@@ -411,11 +422,11 @@ __device__ __forceinline__ void node_pred(const S* f, const C* E, long long N, l
     u[a] = j[a] / rho;
     uu += u[a] * u[a];
   }
-  T = (double(E[n]) / rho - 0.5 * uu) / Cv;
+  T = (En / rho - 0.5 * uu) / Cv;
 }
 
 template <class L, class S, class C>
-static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E) {
+static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E, const C* M) {
   constexpr int D = L::D;
   constexpr int KS = D == 2 ? 16 : 64;
   constexpr int KP = D == 2 ? 4 : 8;
@@ -438,7 +449,7 @@ static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, co
       if (n >= 0) {
         const double w = s.sten_w[l * KS + k];
         double rho, j[3], u[3], T;
-        node_pred<L, S, C>(f, E, g.N, n, rho, j, u, T, s.Cv);
+        node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, s.Cv);
         v[rep][0] = rho * w;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -457,7 +468,7 @@ static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, co
     if (n >= 0) {
       const double w = s.psten_w[l * KP + lane];
       double rho, j[3], u[3], T;
-      node_pred<L, S, C>(f, E, g.N, n, rho, j, u, T, s.Cv);
+      node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, s.Cv);
 #pragma unroll
       for (int a = 0; a < D; ++a) pv[a] = u[a] * w;
       pv[D] = T * w;

@@ -1,4 +1,22 @@
-// Fused collide + stream + energy kernel (shared-memory tiles); see below.
+// Fused time step: collision, pull streaming and the total-energy update in
+// one pass over HBM (arXiv 2607.07432, Eq. LB, Eq. energy, Sec. 2.5 step 5).
+//
+// Each CTA owns a TX x TY column of the (x, y) plane and marches along z
+// (2.5D blocking).  Shared memory holds two rings of planes:
+//   * corrected macroscopic fields (rho, u, theta, rho E') of five planes
+//     z-2..z+2 with a halo of two nodes in x and y (MUSCL stencils and the
+//     velocity gradients of halo nodes), and
+//   * post-collision populations of three planes z-1..z+1 with a halo of one
+//     node (pull streaming and the face-crossing flux tables).
+// Per plane: load the macros of plane z+2, collide plane z+1 (halo included),
+// then stream, form the energy face fluxes and update rho E of plane z.
+//
+// Between steps the state carries, besides the populations, the predicted
+// moments rho, rho u (sums of the streamed populations) and rho E of every
+// node, so halo nodes cost D+2 values instead of Q populations.  The IB
+// spreading kernel adds f_u/2 and w + q to those moments in place before
+// this kernel runs; forced nodes then look up f_u for the force populations.
+// In 2D the same kernel runs with a single plane.
 #pragma once
 #include "grid.cuh"
 #include "physics.cuh"
@@ -7,20 +25,316 @@ namespace lbmib {
 
 template <class S, class C>
 struct FusedArgs {
-  const S* f_in;
-  S* f_out;
-  const C* E_in;
-  C* E_out;
-  const C* Pp;
-  C* Pn;
-  const C* Ap;
-  C* An;
-  const int* row_of_node;
-  const double* FU;
-  const double* WQ;
+  const S* f_in;       // Q*N populations of step n
+  S* f_out;            // Q*N populations of step n+1
+  const C* M_in;       // (D+2)*N: rho, rho u (+ f_u/2 on forced nodes), rho E (+ w + q)
+  C* M_out;            // (D+2)*N: predicted moments of step n+1
+  const C* Pp;         // N
+  C* Pn;               // N
+  const C* Ap;         // NDEV*N
+  C* An;               // NDEV*N
+  const unsigned char* forced;  // N flags (nullptr: no body)
+  const int* cell_id;  // n_rows, ascending
+  int n_rows;
+  const double* FU;    // n_rows*D
+};
+
+template <class C>
+struct FusedTile;
+template <>
+struct FusedTile<float> {
+  static constexpr int TX = 32, TY = 8;
+};
+template <>
+struct FusedTile<double> {
+  static constexpr int TX = 16, TY = 8;
+};
+
+__device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int node) {
+  int lo = 0, hi = n_rows - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int v = __ldg(cell_id + mid);
+    if (v == node) return mid;
+    if (v < node) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+template <class L, class C>
+struct FusedLayout {
+  static constexpr int D = L::D;
+  static constexpr int TX = FusedTile<C>::TX, TY = FusedTile<C>::TY;
+  static constexpr int HX2 = TX + 4, HY2 = TY + 4, NH2 = HX2 * HY2;
+  static constexpr int HX1 = TX + 2, HY1 = TY + 2, NH1 = HX1 * HY1;
+  static constexpr int RM = D == 3 ? 5 : 1;   // macro planes
+  static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
+  static constexpr int NMF = D + 3;           // rho, u (D), theta, E'
+  static constexpr size_t bytes = sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1);
 };
 
 template <class L, class S, class C>
-void launch_fused(const Grid&, const FusedArgs<S, C>&, const Phys<C>&, cudaStream_t) {}
+__global__ void __launch_bounds__(FusedTile<C>::TX * FusedTile<C>::TY)
+    k_fused(Grid g, FusedArgs<S, C> a, Phys<C> ph, int zchunk) {
+  using Lay = FusedLayout<L, C>;
+  constexpr int D = L::D, Q = L::Q;
+  constexpr int TX = Lay::TX, TY = Lay::TY, NT = TX * TY;
+  constexpr int HX2 = Lay::HX2, NH2 = Lay::NH2, HX1 = Lay::HX1, NH1 = Lay::NH1;
+  constexpr int RM = Lay::RM, RF = Lay::RF, NMF = Lay::NMF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* mr = reinterpret_cast<C*>(smem_raw);        // [RM][NMF][NH2]
+  C* fr = mr + (size_t)RM * NMF * NH2;           // [RF][Q][NH1]
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int nz = g.n[2];
+  const int z0 = D == 3 ? blockIdx.z * zchunk : 0;
+  const int z1 = D == 3 ? min(nz, z0 + zchunk) : 1;
+  const long long N = g.N;
+
+  auto mslot = [&](int z) { return D == 3 ? ((z % RM) + RM) % RM : 0; };
+  auto fslot = [&](int z) { return D == 3 ? ((z % RF) + RF) % RF : 0; };
+
+  // corrected macros of plane z over the halo-2 region
+  auto load_macros = [&](int z) {
+    C* dst = mr + (size_t)mslot(z) * NMF * NH2;
+    const int gz = g.wrap(2, z);
+    for (int k = t; k < NH2; k += NT) {
+      const int hx = k % HX2, hy = k / HX2;
+      const long long n = g.lin(g.wrap(0, x0 + hx - 2), g.wrap(1, y0 + hy - 2), gz);
+      const C rho = a.M_in[n];
+      C u[3], uu = C(0);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        u[d] = a.M_in[(1 + d) * N + n] / rho;
+        uu += u[d] * u[d];
+      }
+      const C E = a.M_in[(1 + D) * N + n];
+      const C th = (E / rho - C(0.5) * uu) / ph.Cv;
+      dst[0 * NH2 + k] = rho;
+#pragma unroll
+      for (int d = 0; d < D; ++d) dst[(1 + d) * NH2 + k] = u[d];
+      dst[(1 + D) * NH2 + k] = th;
+      dst[(2 + D) * NH2 + k] = E;
+    }
+  };
+  auto macro_at = [&](int z, int hx, int hy) {
+    const C* src = mr + (size_t)mslot(z) * NMF * NH2;
+    const int k = hy * HX2 + hx;
+    Macro<C> m;
+    m.rho = src[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) m.u[d] = d < D ? src[(1 + d) * NH2 + k] : C(0);
+    m.th = src[(1 + D) * NH2 + k];
+    m.E = src[(2 + D) * NH2 + k];
+    return m;
+  };
+  // collision of plane z over the halo-1 region
+  auto collide_plane = [&](int z) {
+    C* dst = fr + (size_t)fslot(z) * Q * NH1;
+    const int gz = g.wrap(2, z);
+    const bool own_z = z >= z0 && z < z1;
+    for (int k = t; k < NH1; k += NT) {
+      const int cx = k % HX1, cy = k / HX1;
+      const int gx = x0 + cx - 1, gy = y0 + cy - 1;
+      const long long n = g.lin(g.wrap(0, gx), g.wrap(1, gy), gz);
+      const int hx = cx + 1, hy = cy + 1;
+      auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
+      C du[3][3], aC[3][3];
+      gradients<L, C>(MA, du, aC, ph.use_ac);
+      const Macro<C> m = macro_at(z, hx, hy);
+      C fbar[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
+      C fu[3] = {C(0), C(0), C(0)};
+      if (a.forced && a.forced[n]) {
+        const int r = find_row_dev(a.cell_id, a.n_rows, (int)n);
+#pragma unroll
+        for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
+      }
+      C dAFp[L::NDEV];
+#pragma unroll
+      for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
+      C fcol[Q], Pn, dAFn[L::NDEV];
+      collide<L, C>(fbar, m, du, aC, a.Pp[n], dAFp, fu, ph, fcol, Pn, dAFn);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) dst[i * NH1 + k] = fcol[i];
+      const bool own = own_z && cx >= 1 && cx <= TX && cy >= 1 && cy <= TY && gx < g.n[0] && gy < g.n[1];
+      if (own) {
+        a.Pn[n] = Pn;
+#pragma unroll
+        for (int q = 0; q < L::NDEV; ++q) a.An[q * N + n] = dAFn[q];
+      }
+    }
+  };
+  auto fcol_at = [&](int i, int z, int cx, int cy) { return fr[((size_t)fslot(z) * Q + i) * NH1 + cy * HX1 + cx]; };
+
+  // prologue
+  if (D == 3) {
+    for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z);
+    __syncthreads();
+    collide_plane(z0 - 1);
+    collide_plane(z0);
+    __syncthreads();
+  }
+  const int tx = t % TX, ty = t / TX;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool active = gx < g.n[0] && gy < g.n[1];
+  for (int z = z0; z < z1; ++z) {
+    if (D == 3) {
+      load_macros(z + 2);
+      __syncthreads();
+      collide_plane(z + 1);
+      __syncthreads();
+    } else {
+      load_macros(0);
+      __syncthreads();
+      collide_plane(0);
+      __syncthreads();
+    }
+    if (active) {
+      const long long n = g.lin(gx, gy, z);
+      const int cx = tx + 1, cy = ty + 1;  // halo-1 coordinates
+      const int hx = tx + 2, hy = ty + 2;  // halo-2 coordinates
+      // Eq. LB pull streaming and the predicted moments of step n+1
+      C rho = C(0), j[3] = {C(0), C(0), C(0)};
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const C v = fcol_at(i, z - L::c(i, 2), cx - L::c(i, 0), cy - L::c(i, 1));
+        store_pop<L, S, C>(a.f_out, i, N, n, v);
+        rho += v;
+        sfor<0, D>([&](auto A) {
+          constexpr int d = decltype(A)::value;
+          if constexpr (L::c(i, d) != 0) j[d] += C(L::c(i, d)) * v;
+        });
+      });
+      // Eq. energy: rho E^{n+1} = rho E' - sum_a (F_{+a/2}(x) - F_{+a/2}(x - e_a))
+      C E = macro_at(z, hx, hy).E;
+      auto face = [&](auto AXc, int bx, int by, int bz) {
+        constexpr int AX = decltype(AXc)::value;
+        auto MAl = [&](int k) {
+          return macro_at(bz + (AX == 2 ? k : 0), hx + bx + (AX == 0 ? k : 0), hy + by + (AX == 1 ? k : 0));
+        };
+        auto FCl = [&](int i, int dx, int dy, int dz) { return fcol_at(i, bz + dz, cx + bx + dx, cy + by + dy); };
+        return energy_face_flux<L, C, AX>(MAl, FCl, ph);
+      };
+      {
+        const C Fp = face(std::integral_constant<int, 0>{}, 0, 0, z);
+        const C Fm = face(std::integral_constant<int, 0>{}, -1, 0, z);
+        E = E - (Fp - Fm);
+      }
+      {
+        const C Fp = face(std::integral_constant<int, 1>{}, 0, 0, z);
+        const C Fm = face(std::integral_constant<int, 1>{}, 0, -1, z);
+        E = E - (Fp - Fm);
+      }
+      if constexpr (D == 3) {
+        const C Fp = face(std::integral_constant<int, 2>{}, 0, 0, z);
+        const C Fm = face(std::integral_constant<int, 2>{}, 0, 0, z - 1);
+        E = E - (Fp - Fm);
+      }
+      a.M_out[n] = rho;
+#pragma unroll
+      for (int d = 0; d < D; ++d) a.M_out[(1 + d) * N + n] = j[d];
+      a.M_out[(1 + D) * N + n] = E;
+    }
+    __syncthreads();
+  }
+}
+
+// zchunk: planes per CTA along z (3D)
+template <class L, class S, class C>
+inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
+                         int zchunk) {
+  using Lay = FusedLayout<L, C>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fused<L, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+    attr = true;
+  }
+  dim3 grid((g.n[0] + Lay::TX - 1) / Lay::TX, (g.n[1] + Lay::TY - 1) / Lay::TY,
+            L::D == 3 ? (g.n[2] + zchunk - 1) / zchunk : 1);
+  k_fused<L, S, C><<<grid, Lay::TX * Lay::TY, Lay::bytes, st>>>(g, a, ph, zchunk);
+}
+
+// IB spreading applied to the predicted moments in place: rho u += f_u / 2,
+// rho E += w + q on the forced nodes (Sec. 2.2, reading Q15)
+template <class C>
+__global__ void k_apply_forcing(int D, long long N, int n_rows, const int* cell_id, const double* FU,
+                                const double* WQ, C* M) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const long long n = cell_id[r];
+  for (int d = 0; d < D; ++d) M[(1 + d) * N + n] = M[(1 + d) * N + n] + C(0.5) * C(FU[(long long)r * D + d]);
+  M[(1 + D) * N + n] = M[(1 + D) * N + n] + C(WQ[r]);
+}
+
+// predicted moments rho, rho u, rho E of every node from populations and E
+template <class L, class S, class C>
+__global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
+  constexpr int D = L::D;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  C r = C(0), j[3] = {C(0), C(0), C(0)};
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const C v = load_pop<L, S, C>(f, i, g.N, n);
+    r += v;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
+  }
+  M[n] = r;
+#pragma unroll
+  for (int a = 0; a < D; ++a) M[(1 + a) * g.N + n] = j[a];
+  M[(1 + D) * g.N + n] = E[n];
+}
+
+// boundary faces also refresh the predicted moments of the nodes they set
+template <class L, class S, class C>
+__global__ void k_bc_outlet_m(Grid g, S* f, C* M, int axis, int side) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  if (t >= g.n[a1] * g.n[a2]) return;
+  int c[3];
+  c[a1] = t % g.n[a1];
+  c[a2] = t / g.n[a1];
+  const int nax = g.n[axis];
+  c[axis] = side ? nax - 1 : 0;
+  const long long dst = g.lin(c[0], c[1], c[2]);
+  c[axis] = side ? nax - 2 : 1;
+  const long long src = g.lin(c[0], c[1], c[2]);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) f[(long long)i * g.N + dst] = f[(long long)i * g.N + src];
+#pragma unroll
+  for (int k = 0; k < L::D + 2; ++k) M[k * g.N + dst] = M[k * g.N + src];
+}
+
+template <class L, class S, class C>
+__global__ void k_bc_equilibrium_m(Grid g, S* f, C* M, int axis, int side, const C* feq_inf, C E_inf) {
+  constexpr int D = L::D;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  if (t >= g.n[a1] * g.n[a2]) return;
+  int c[3];
+  c[a1] = t % g.n[a1];
+  c[a2] = t / g.n[a1];
+  c[axis] = side ? g.n[axis] - 1 : 0;
+  const long long dst = g.lin(c[0], c[1], c[2]);
+  C r = C(0), j[3] = {C(0), C(0), C(0)};
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i]);
+    const C v = load_pop<L, S, C>(f, i, g.N, dst);
+    r += v;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
+  }
+  M[dst] = r;
+#pragma unroll
+  for (int a = 0; a < D; ++a) M[(1 + a) * g.N + dst] = j[a];
+  M[(1 + D) * g.N + dst] = E_inf;
+}
 
 }  // namespace lbmib
