@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "handle.cuh"
 #include "ib.cuh"
 #include "physics.cuh"
@@ -145,26 +147,20 @@ struct Engine {
     return LBM_OK;
   }
   static lbm_status bc_fused(lbm_handle* h) {
-    for (int face = 0; face < 2 * L::D; ++face) {
-      if (h->cfg.bc[face] != LBM_BC_OUTLET) continue;
-      FacePlane fp{face / 2, face % 2};
-      lbm_status s = launch(h, kProfBC, [&] {
-        k_bc_outlet_m<L, S, C><<<nblk(fp.count(h->g), 128), 128, 0, h->st>>>(h->g, (S*)h->f, (C*)h->M, fp.axis,
-                                                                            fp.side);
-      });
-      if (s) return s;
+    BCFaces bf;
+    int maxplane = 0;
+    for (int face = 0; face < 6; ++face) {
+      bf.type[face] = face < 2 * L::D ? h->cfg.bc[face] : 0;
+      if (face < 2 * L::D && bf.type[face]) {
+        FacePlane fp{face / 2, face % 2};
+        maxplane = std::max(maxplane, fp.count(h->g));
+      }
     }
-    for (int face = 0; face < 2 * L::D; ++face) {
-      const int t = h->cfg.bc[face];
-      if (t != LBM_BC_INLET && t != LBM_BC_FARFIELD) continue;
-      FacePlane fp{face / 2, face % 2};
-      lbm_status s = launch(h, kProfBC, [&] {
-        k_bc_equilibrium_m<L, S, C><<<nblk(fp.count(h->g), 128), 128, 0, h->st>>>(
-            h->g, (S*)h->f, (C*)h->M, fp.axis, fp.side, (const C*)h->feq_inf, C(h->E_inf));
-      });
-      if (s) return s;
-    }
-    return LBM_OK;
+    if (!maxplane) return LBM_OK;
+    return launch(h, kProfBC, [&] {
+      k_bc_all_m<L, S, C><<<dim3(nblk(maxplane, 128), 2 * L::D), 128, 0, h->st>>>(
+          h->g, (S*)h->f, (C*)h->M, bf, (const C*)h->feq_inf, C(h->E_inf));
+    });
   }
   // fused form: predicted moments from the populations and rho E
   static lbm_status refresh_moments(lbm_handle* h) {

@@ -62,6 +62,12 @@ __device__ __forceinline__ C load_pop(const S* f, int i, long long N, long long 
   const C v = C(Store<S>::load(f[(long long)i * N + n]));
   return Store<S>::dev ? v + C(L::w(i)) : v;
 }
+// the value a population takes after a store and a reload
+template <class L, class S, class C>
+__device__ __forceinline__ C roundtrip_pop(int i, C v) {
+  if (Store<S>::dev) return C(Store<S>::load(Store<S>::save(v - C(L::w(i))))) + C(L::w(i));
+  return C(Store<S>::load(Store<S>::save(v)));
+}
 template <class L, class S, class C>
 __device__ __forceinline__ void store_pop(S* f, int i, long long N, long long n, C v) {
   f[(long long)i * N + n] = Store<S>::save(Store<S>::dev ? v - C(L::w(i)) : v);

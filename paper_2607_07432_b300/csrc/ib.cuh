@@ -392,37 +392,46 @@ static __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // predicted moments of one node (Sec. 2.2): from the stored moments
-// rho, rho u, rho E when M is given, else from the post-stream populations
+// rho, rho u, rho E when M is given, else from the post-stream populations.
+// Evaluated in the compute type C (the precision of the stored state) and
+// widened to FP64 for the Lagrangian sums.
 template <class L, class S, class C>
 __device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, long long N, long long n,
-                                          double& rho, double* j, double* u, double& T, double Cv) {
+                                          double& rho_o, double* j_o, double* u_o, double& T_o, C Cv) {
   constexpr int D = L::D;
-  double En;
+  C rho, j[3], En;
   if (M) {
-    rho = double(M[n]);
+    rho = M[n];
 #pragma unroll
-    for (int a = 0; a < D; ++a) j[a] = double(M[(1 + a) * N + n]);
-    En = double(M[(1 + D) * N + n]);
+    for (int a = 0; a < D; ++a) j[a] = M[(1 + a) * N + n];
+    En = M[(1 + D) * N + n];
   } else {
-    rho = 0.0;
-    for (int a = 0; a < 3; ++a) j[a] = 0.0;
+    rho = C(0);
+    for (int a = 0; a < 3; ++a) j[a] = C(0);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      const double v = double(load_pop<L, S, C>(f, i, N, n));
+      const C v = load_pop<L, S, C>(f, i, N, n);
       rho += v;
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        if (L::c(i, a) != 0) j[a] += double(L::c(i, a)) * v;
+        if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
     }
-    En = double(E[n]);
+    En = E[n];
   }
-  double uu = 0.0;
+  C uu = C(0), u[3];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     u[a] = j[a] / rho;
     uu += u[a] * u[a];
   }
-  T = (En / rho - 0.5 * uu) / Cv;
+  const C T = (En / rho - C(0.5) * uu) / Cv;
+  rho_o = double(rho);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    j_o[a] = double(j[a]);
+    u_o[a] = double(u[a]);
+  }
+  T_o = double(T);
 }
 
 template <class L, class S, class C>
@@ -449,7 +458,7 @@ static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, co
       if (n >= 0) {
         const double w = s.sten_w[l * KS + k];
         double rho, j[3], u[3], T;
-        node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, s.Cv);
+        node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
         v[rep][0] = rho * w;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -468,26 +477,40 @@ static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, co
     if (n >= 0) {
       const double w = s.psten_w[l * KP + lane];
       double rho, j[3], u[3], T;
-      node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, s.Cv);
+      node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
 #pragma unroll
       for (int a = 0; a < D; ++a) pv[a] = u[a] * w;
       pv[D] = T * w;
     }
   }
-  double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  // stage the slot values in shared memory; lane k < NV then adds quantity k
+  // over the slots in order (one FP64 add per slot instead of one per lane)
+  __shared__ double stage[4][64 + 8][NV];
+  const int wib = threadIdx.x >> 5;
 #pragma unroll
   for (int rep = 0; rep < (KS + 31) / 32; ++rep)
-    for (int src = 0; src < 32; ++src)
 #pragma unroll
-      for (int k = 0; k < NV; ++k) acc[k] = acc[k] + __shfl_sync(0xffffffffu, v[rep][k], src);
+    for (int k = 0; k < NV; ++k) stage[wib][lane + 32 * rep][k] = v[rep][k];
+  if (lane < KP)
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k) stage[wib][64 + lane][k] = pv[k];
+  __syncwarp();
+  double acc[NV];
   double pacc[D + 1];
+  if (lane < NV) {
+    double a_ = 0.0;
+    for (int k = 0; k < KS; ++k) a_ = a_ + stage[wib][k][lane];
+    stage[wib][0][lane] = a_;
+  } else if (lane >= 16 && lane < 16 + D + 1) {
+    double a_ = 0.0;
+    for (int k = 0; k < KP; ++k) a_ = a_ + stage[wib][64 + k][lane - 16];
+    stage[wib][64][lane - 16] = a_;
+  }
+  __syncwarp();
 #pragma unroll
-  for (int k = 0; k < D + 1; ++k) pacc[k] = 0.0;
-  for (int src = 0; src < KP; ++src)
+  for (int k = 0; k < NV; ++k) acc[k] = stage[wib][0][k];
 #pragma unroll
-    for (int k = 0; k < D + 1; ++k) pacc[k] = pacc[k] + __shfl_sync(0xffffffffu, pv[k], src);
+  for (int k = 0; k < D + 1; ++k) pacc[k] = stage[wib][64][k];
   if (lane != 0) return;
   const double ph = s.phi[l];
   const double rho_s = ph * acc[0];

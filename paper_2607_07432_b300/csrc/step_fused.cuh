@@ -39,15 +39,28 @@ struct FusedArgs {
   const double* FU;    // n_rows*D
 };
 
-template <class C>
-struct FusedTile;
-template <>
-struct FusedTile<float> {
-  static constexpr int TX = 32, TY = 8;
+// Tile: one thread per node of the halo-1 region HX1 x HY1 (the collision
+// region), interior TX x TY = (HX1-2) x (HY1-2).  The D3Q19 FP32 tile uses
+// 512 threads and about 190 KB of shared memory.
+template <class L, class C>
+struct FusedTile {
+  static constexpr int HX1 = sizeof(C) == 8 ? 16 : 32;
+  static constexpr int HY1 = sizeof(C) == 8 ? 8 : (L::D == 3 ? 16 : 8);
+  static constexpr int TX = HX1 - 2, TY = HY1 - 2;
 };
-template <>
-struct FusedTile<double> {
-  static constexpr int TX = 16, TY = 8;
+
+template <class L, class C>
+struct FusedLayout {
+  static constexpr int D = L::D;
+  static constexpr int TX = FusedTile<L, C>::TX, TY = FusedTile<L, C>::TY;
+  static constexpr int HX1 = TX + 2, HY1 = TY + 2, NH1 = HX1 * HY1;
+  static constexpr int HX2 = TX + 4, HY2 = TY + 4, NH2 = HX2 * HY2;
+  static constexpr int NT = NH1;
+  static constexpr int RM = D == 3 ? 5 : 1;   // macro planes
+  static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
+  static constexpr int NMF = D + 3;           // rho, u (D), theta, E'
+  static constexpr size_t bytes =
+      sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1 + 2 * (size_t)NH1);
 };
 
 __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int node) {
@@ -62,35 +75,36 @@ __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int 
   return -1;
 }
 
-template <class L, class C>
-struct FusedLayout {
-  static constexpr int D = L::D;
-  static constexpr int TX = FusedTile<C>::TX, TY = FusedTile<C>::TY;
-  static constexpr int HX2 = TX + 4, HY2 = TY + 4, NH2 = HX2 * HY2;
-  static constexpr int HX1 = TX + 2, HY1 = TY + 2, NH1 = HX1 * HY1;
-  static constexpr int RM = D == 3 ? 5 : 1;   // macro planes
-  static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
-  static constexpr int NMF = D + 3;           // rho, u (D), theta, E'
-  static constexpr size_t bytes = sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1);
-};
+template <class C>
+__device__ __forceinline__ C recip(C x) {
+  return C(1) / x;
+}
 
 template <class L, class S, class C>
-__global__ void __launch_bounds__(FusedTile<C>::TX * FusedTile<C>::TY)
+__global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
     k_fused(Grid g, FusedArgs<S, C> a, Phys<C> ph, int zchunk) {
   using Lay = FusedLayout<L, C>;
   constexpr int D = L::D, Q = L::Q;
-  constexpr int TX = Lay::TX, TY = Lay::TY, NT = TX * TY;
+  constexpr int TX = Lay::TX, TY = Lay::TY, NT = Lay::NT;
   constexpr int HX2 = Lay::HX2, NH2 = Lay::NH2, HX1 = Lay::HX1, NH1 = Lay::NH1;
   constexpr int RM = Lay::RM, RF = Lay::RF, NMF = Lay::NMF;
+  constexpr bool exact = std::is_same<C, double>::value;  // FP64: operations as in the oracle
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* mr = reinterpret_cast<C*>(smem_raw);        // [RM][NMF][NH2]
   C* fr = mr + (size_t)RM * NMF * NH2;           // [RF][Q][NH1]
+  C* Fx = fr + (size_t)RF * Q * NH1;             // [NH1] +x face fluxes
+  C* Fy = Fx + NH1;                              // [NH1] +y face fluxes
   const int t = threadIdx.x;
+  const int cx = t % HX1, cy = t / HX1;          // halo-1 coordinates of this thread's node
+  const int hx = cx + 1, hy = cy + 1;            // halo-2 coordinates
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + cx - 1, gy = y0 + cy - 1;
   const int nz = g.n[2];
   const int z0 = D == 3 ? blockIdx.z * zchunk : 0;
   const int z1 = D == 3 ? min(nz, z0 + zchunk) : 1;
   const long long N = g.N;
+  const bool interior = cx >= 1 && cx <= TX && cy >= 1 && cy <= TY && gx < g.n[0] && gy < g.n[1];
+  const int wx = g.wrap(0, gx), wy = g.wrap(1, gy);
 
   auto mslot = [&](int z) { return D == 3 ? ((z % RM) + RM) % RM : 0; };
   auto fslot = [&](int z) { return D == 3 ? ((z % RF) + RF) % RF : 0; };
@@ -100,17 +114,28 @@ __global__ void __launch_bounds__(FusedTile<C>::TX * FusedTile<C>::TY)
     C* dst = mr + (size_t)mslot(z) * NMF * NH2;
     const int gz = g.wrap(2, z);
     for (int k = t; k < NH2; k += NT) {
-      const int hx = k % HX2, hy = k / HX2;
-      const long long n = g.lin(g.wrap(0, x0 + hx - 2), g.wrap(1, y0 + hy - 2), gz);
+      const int kx = k % HX2, ky = k / HX2;
+      const long long n = g.lin(g.wrap(0, x0 + kx - 2), g.wrap(1, y0 + ky - 2), gz);
       const C rho = a.M_in[n];
       C u[3], uu = C(0);
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        u[d] = a.M_in[(1 + d) * N + n] / rho;
-        uu += u[d] * u[d];
-      }
       const C E = a.M_in[(1 + D) * N + n];
-      const C th = (E / rho - C(0.5) * uu) / ph.Cv;
+      C th;
+      if constexpr (exact) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          u[d] = a.M_in[(1 + d) * N + n] / rho;
+          uu += u[d] * u[d];
+        }
+        th = (E / rho - C(0.5) * uu) / ph.Cv;
+      } else {
+        const C ir = recip(rho);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          u[d] = a.M_in[(1 + d) * N + n] * ir;
+          uu += u[d] * u[d];
+        }
+        th = (E * ir - C(0.5) * uu) * (C(1) / ph.Cv);
+      }
       dst[0 * NH2 + k] = rho;
 #pragma unroll
       for (int d = 0; d < D; ++d) dst[(1 + d) * NH2 + k] = u[d];
@@ -118,9 +143,9 @@ __global__ void __launch_bounds__(FusedTile<C>::TX * FusedTile<C>::TY)
       dst[(2 + D) * NH2 + k] = E;
     }
   };
-  auto macro_at = [&](int z, int hx, int hy) {
+  auto macro_at = [&](int z, int kx, int ky) {
     const C* src = mr + (size_t)mslot(z) * NMF * NH2;
-    const int k = hy * HX2 + hx;
+    const int k = ky * HX2 + kx;
     Macro<C> m;
     m.rho = src[k];
 #pragma unroll
@@ -129,75 +154,82 @@ __global__ void __launch_bounds__(FusedTile<C>::TX * FusedTile<C>::TY)
     m.E = src[(2 + D) * NH2 + k];
     return m;
   };
-  // collision of plane z over the halo-1 region
+  // collision of this thread's node of plane z (halo-1 region, one node per thread)
   auto collide_plane = [&](int z) {
     C* dst = fr + (size_t)fslot(z) * Q * NH1;
-    const int gz = g.wrap(2, z);
-    const bool own_z = z >= z0 && z < z1;
-    for (int k = t; k < NH1; k += NT) {
-      const int cx = k % HX1, cy = k / HX1;
-      const int gx = x0 + cx - 1, gy = y0 + cy - 1;
-      const long long n = g.lin(g.wrap(0, gx), g.wrap(1, gy), gz);
-      const int hx = cx + 1, hy = cy + 1;
-      auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
-      C du[3][3], aC[3][3];
-      gradients<L, C>(MA, du, aC, ph.use_ac);
-      const Macro<C> m = macro_at(z, hx, hy);
-      C fbar[Q];
+    const long long n = g.lin(wx, wy, g.wrap(2, z));
+    auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
+    C du[3][3], aC[3][3];
+    gradients<L, C>(MA, du, aC, ph.use_ac);
+    const Macro<C> m = macro_at(z, hx, hy);
+    C fbar[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
-      C fu[3] = {C(0), C(0), C(0)};
-      if (a.forced && a.forced[n]) {
-        const int r = find_row_dev(a.cell_id, a.n_rows, (int)n);
+    for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
+    C fu[3] = {C(0), C(0), C(0)};
+    if (a.forced && a.forced[n]) {
+      const int r = find_row_dev(a.cell_id, a.n_rows, (int)n);
 #pragma unroll
-        for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
-      }
-      C dAFp[L::NDEV];
+      for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
+    }
+    C dAFp[L::NDEV];
 #pragma unroll
-      for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
-      C fcol[Q], Pn, dAFn[L::NDEV];
+    for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
+    C fcol[Q], Pn, dAFn[L::NDEV];
+    if constexpr (exact) {
       collide<L, C>(fbar, m, du, aC, a.Pp[n], dAFp, fu, ph, fcol, Pn, dAFn);
+    } else {
+      collide_fast<L, C>(fbar, m, du, aC, a.Pp[n], dAFp, fu, ph, fcol, Pn, dAFn);
+    }
 #pragma unroll
-      for (int i = 0; i < Q; ++i) dst[i * NH1 + k] = fcol[i];
-      const bool own = own_z && cx >= 1 && cx <= TX && cy >= 1 && cy <= TY && gx < g.n[0] && gy < g.n[1];
-      if (own) {
-        a.Pn[n] = Pn;
+    for (int i = 0; i < Q; ++i) dst[i * NH1 + t] = fcol[i];
+    if (interior && z >= z0 && z < z1) {
+      a.Pn[n] = Pn;
 #pragma unroll
-        for (int q = 0; q < L::NDEV; ++q) a.An[q * N + n] = dAFn[q];
-      }
+      for (int q = 0; q < L::NDEV; ++q) a.An[q * N + n] = dAFn[q];
     }
   };
-  auto fcol_at = [&](int i, int z, int cx, int cy) { return fr[((size_t)fslot(z) * Q + i) * NH1 + cy * HX1 + cx]; };
+  auto fcol_at = [&](int i, int z, int kx, int ky) { return fr[((size_t)fslot(z) * Q + i) * NH1 + ky * HX1 + kx]; };
+  // energy flux through the + face (axis AX) of the node at (cx+bx, cy+by, bz)
+  auto face = [&](auto AXc, int bz) {
+    constexpr int AX = decltype(AXc)::value;
+    auto MAl = [&](int k) {
+      return macro_at(bz + (AX == 2 ? k : 0), hx + (AX == 0 ? k : 0), hy + (AX == 1 ? k : 0));
+    };
+    auto FCl = [&](int i, int dx, int dy, int dz) { return fcol_at(i, bz + dz, cx + dx, cy + dy); };
+    return energy_face_flux<L, C, AX>(MAl, FCl, ph);
+  };
 
   // prologue
-  if (D == 3) {
+  if constexpr (D == 3) {
     for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z);
     __syncthreads();
     collide_plane(z0 - 1);
     collide_plane(z0);
     __syncthreads();
   }
-  const int tx = t % TX, ty = t / TX;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool active = gx < g.n[0] && gy < g.n[1];
+  // the -z face of plane z is the +z face of plane z-1: carried in a register
+  C Fz_prev = C(0);
+  if constexpr (D == 3) {
+    if (interior) Fz_prev = face(std::integral_constant<int, 2>{}, z0 - 1);
+  }
+  const bool xface = cx <= TX && cy >= 1 && cy <= TY;  // +x faces of nodes cx = 0..TX
+  const bool yface = cy <= TY && cx >= 1 && cx <= TX;  // +y faces of nodes cy = 0..TY
   for (int z = z0; z < z1; ++z) {
-    if (D == 3) {
+    if constexpr (D == 3) {
       load_macros(z + 2);
       __syncthreads();
       collide_plane(z + 1);
-      __syncthreads();
     } else {
       load_macros(0);
       __syncthreads();
       collide_plane(0);
-      __syncthreads();
     }
-    if (active) {
-      const long long n = g.lin(gx, gy, z);
-      const int cx = tx + 1, cy = ty + 1;  // halo-1 coordinates
-      const int hx = tx + 2, hy = ty + 2;  // halo-2 coordinates
+    __syncthreads();
+    C rho = C(0), j[3] = {C(0), C(0), C(0)};
+    long long n = 0;
+    if (interior) {
+      n = g.lin(gx, gy, z);
       // Eq. LB pull streaming and the predicted moments of step n+1
-      C rho = C(0), j[3] = {C(0), C(0), C(0)};
       sfor<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const C v = fcol_at(i, z - L::c(i, 2), cx - L::c(i, 0), cy - L::c(i, 1));
@@ -208,30 +240,23 @@ __global__ void __launch_bounds__(FusedTile<C>::TX * FusedTile<C>::TY)
           if constexpr (L::c(i, d) != 0) j[d] += C(L::c(i, d)) * v;
         });
       });
-      // Eq. energy: rho E^{n+1} = rho E' - sum_a (F_{+a/2}(x) - F_{+a/2}(x - e_a))
+    }
+    // Eq. energy face fluxes, each face once
+    if (xface) Fx[t] = face(std::integral_constant<int, 0>{}, z);
+    if (yface) Fy[t] = face(std::integral_constant<int, 1>{}, z);
+    C Fzp = C(0);
+    if constexpr (D == 3) {
+      if (interior) Fzp = face(std::integral_constant<int, 2>{}, z);
+    }
+    __syncthreads();
+    if (interior) {
+      // rho E^{n+1} = rho E' - sum_a (F_{+a/2}(x) - F_{+a/2}(x - e_a))
       C E = macro_at(z, hx, hy).E;
-      auto face = [&](auto AXc, int bx, int by, int bz) {
-        constexpr int AX = decltype(AXc)::value;
-        auto MAl = [&](int k) {
-          return macro_at(bz + (AX == 2 ? k : 0), hx + bx + (AX == 0 ? k : 0), hy + by + (AX == 1 ? k : 0));
-        };
-        auto FCl = [&](int i, int dx, int dy, int dz) { return fcol_at(i, bz + dz, cx + bx + dx, cy + by + dy); };
-        return energy_face_flux<L, C, AX>(MAl, FCl, ph);
-      };
-      {
-        const C Fp = face(std::integral_constant<int, 0>{}, 0, 0, z);
-        const C Fm = face(std::integral_constant<int, 0>{}, -1, 0, z);
-        E = E - (Fp - Fm);
-      }
-      {
-        const C Fp = face(std::integral_constant<int, 1>{}, 0, 0, z);
-        const C Fm = face(std::integral_constant<int, 1>{}, 0, -1, z);
-        E = E - (Fp - Fm);
-      }
+      E = E - (Fx[t] - Fx[t - 1]);
+      E = E - (Fy[t] - Fy[t - HX1]);
       if constexpr (D == 3) {
-        const C Fp = face(std::integral_constant<int, 2>{}, 0, 0, z);
-        const C Fm = face(std::integral_constant<int, 2>{}, 0, 0, z - 1);
-        E = E - (Fp - Fm);
+        E = E - (Fzp - Fz_prev);
+        Fz_prev = Fzp;
       }
       a.M_out[n] = rho;
 #pragma unroll
@@ -254,7 +279,7 @@ inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>&
   }
   dim3 grid((g.n[0] + Lay::TX - 1) / Lay::TX, (g.n[1] + Lay::TY - 1) / Lay::TY,
             L::D == 3 ? (g.n[2] + zchunk - 1) / zchunk : 1);
-  k_fused<L, S, C><<<grid, Lay::TX * Lay::TY, Lay::bytes, st>>>(g, a, ph, zchunk);
+  k_fused<L, S, C><<<grid, Lay::NT, Lay::bytes, st>>>(g, a, ph, zchunk);
 }
 
 // IB spreading applied to the predicted moments in place: rho u += f_u / 2,
@@ -335,6 +360,65 @@ __global__ void k_bc_equilibrium_m(Grid g, S* f, C* M, int axis, int side, const
 #pragma unroll
   for (int a = 0; a < D; ++a) M[(1 + a) * g.N + dst] = j[a];
   M[(1 + D) * g.N + dst] = E_inf;
+}
+
+// all domain faces in one launch (reading Q24): a node on an inlet or far-field
+// face takes the free-stream equilibrium; a node on an outlet face and on no
+// equilibrium face copies its inner neighbour along the outlet axis.  This is
+// the outlet-copy-then-equilibrium order with the edges resolved up front.
+struct BCFaces {
+  int type[6];  // LBM_BC_* per face: 0 periodic, 1 inlet, 2 outlet, 3 far field
+};
+
+template <class L, class S, class C>
+__global__ void k_bc_all_m(Grid g, S* f, C* M, BCFaces bf, const C* feq_inf, C E_inf) {
+  constexpr int D = L::D;
+  const int face = blockIdx.y;
+  const int axis = face / 2, side = face % 2;
+  const int ft = bf.type[face];
+  if (ft == 0) return;
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.n[a1] * g.n[a2]) return;
+  int c[3];
+  c[a1] = t % g.n[a1];
+  c[a2] = t / g.n[a1];
+  c[axis] = side ? g.n[axis] - 1 : 0;
+  auto on_eq_face = [&](int b) {
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int t2 = bf.type[2 * b + s2];
+      if ((t2 == 1 || t2 == 3) && c[b] == (s2 ? g.n[b] - 1 : 0)) return true;
+    }
+    return false;
+  };
+  bool eq = false;
+  for (int b = 0; b < D; ++b) eq = eq || on_eq_face(b);
+  const long long dst = g.lin(c[0], c[1], c[2]);
+  if (eq) {
+    if (ft != 1 && ft != 3) return;  // written by the equilibrium face's own thread
+    C r = C(0), j[3] = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i]);
+      const C v = roundtrip_pop<L, S, C>(i, feq_inf[i]);
+      r += v;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
+    }
+    M[dst] = r;
+#pragma unroll
+    for (int a = 0; a < D; ++a) M[(1 + a) * g.N + dst] = j[a];
+    M[(1 + D) * g.N + dst] = E_inf;
+    return;
+  }
+  if (ft != 2) return;
+  c[axis] = side ? g.n[axis] - 2 : 1;
+  const long long src = g.lin(c[0], c[1], c[2]);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) f[(long long)i * g.N + dst] = f[(long long)i * g.N + src];
+#pragma unroll
+  for (int k = 0; k < L::D + 2; ++k) M[k * g.N + dst] = M[k * g.N + src];
 }
 
 }  // namespace lbmib
