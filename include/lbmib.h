@@ -163,6 +163,23 @@ lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho,
 lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, double* work,
                               double* per_point);
 
+/* Wall loads as lbm_get_wall_loads, for callers that cannot allocate device
+ * memory when they ask for them (a process whose device memory is fully
+ * reserved by another framework's caching pool, or an embedding that forbids
+ * cudaMalloc / cudaFree after start-up).  The paper has no counterpart: this
+ * is a service of the library.  It allocates nothing: the reduction scratch
+ * is a fixed static device array of 257 x 8 doubles, present on every device
+ * that loads the library until the process exits, which limits the body to
+ * at most 65536 Lagrangian points (LBM_EINVAL beyond).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * must come before any stream capture.  Every call reuses the same array
+ * and overwrites every entry it reads, so nothing needs clearing; calls
+ * that overlap on the GPU (two handles on different streams of one device)
+ * race on it.  The sums are FP64 in a fixed order (per-block trees, then
+ * blocks in order), deterministic, equal to lbm_get_wall_loads up to
+ * rounding. */
+lbm_status lbm_get_wall_loads_noalloc(lbm_handle* h, double force[3], double* heat, double* work);
+
 /* Derived constants: out[0..7] = u_inf magnitude, mu, lambda, theta_inf,
  * C_v, C_p, rho_inf, gamma. */
 lbm_status lbm_get_constants(const lbm_handle* h, double out[8]);

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
 EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", "ib_set_geometry",
            "lbm_step", "lbm_check", "lbm_get_fields", "lbm_get_state", "lbm_set_state", "lbm_set_fields",
            "lbm_get_wall_loads", "lbm_get_constants", "ib_get_sizes", "ib_get_setup", "lbm_profile",
-           "lbm_get_profile", "lbm_launch_count"]
+           "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc"]
 
 
 class Config(ct.Structure):
@@ -227,6 +227,14 @@ class Solver:
             pp = pp.reshape(self.NL, self.D + 2)
             out.update(F=pp[:, :self.D].copy(), W=pp[:, self.D].copy(), Q=pp[:, self.D + 1].copy())
         return out
+
+    def wall_loads_noalloc(self):
+        """lbm_get_wall_loads_noalloc: the same loads with no device allocation
+        (static scratch, at most 65536 points)."""
+        force = (ct.c_double * 3)()
+        heat, work = ct.c_double(), ct.c_double()
+        self._check(lib().lbm_get_wall_loads_noalloc(self.h, force, ct.byref(heat), ct.byref(work)))
+        return dict(force=np.array(force[:self.D]), heat=heat.value, work=work.value)
 
     def constants(self):
         out = (ct.c_double * 8)()
