@@ -168,6 +168,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     h->use_fused = (env && env[0] == '1') ? 0 : 1;
     const char* zc = std::getenv("LBMIB_ZCHUNK");
     if (zc) h->zchunk = std::max(1, std::atoi(zc));
+    const char* tr = std::getenv("LBMIB_TILE_ROWS");
+    if (tr) h->tile_rows = std::atoi(tr);
   }
   alloc(&h->f, N * h->Q * h->ssize);
   if (h->use_fused) {

@@ -248,7 +248,7 @@ inline lbm_status Engine<L, S, C>::fused_step(lbm_handle* h, const Phys<C>& ph) 
   a.cell_id = h->cell_id;
   a.n_rows = h->n_rows;
   a.FU = h->FU;
-  lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st, h->zchunk); });
+  lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st, h->zchunk, h->tile_rows); });
   if (s) return s;
   std::swap(h->f, h->f2);
   std::swap(h->M, h->M2);

@@ -38,7 +38,8 @@ struct lbm_handle {
   void* feq_inf = nullptr;
   int cur = 0;
   int use_fused = 1;         // fused shared-memory step (0: unfused global-memory form)
-  int zchunk = 48;           // planes per CTA along z in the fused step
+  int zchunk = 16;           // planes per CTA along z in the fused step
+  int tile_rows = 0;         // tile height of the 3D FP32 fused step (0 = default)
   void* f2 = nullptr;        // second population buffer (fused form)
   void* M2 = nullptr;        // second predicted-moment buffer (fused form)
   unsigned long long* d_bad = nullptr;

@@ -42,25 +42,33 @@ struct FusedArgs {
 // Tile: one thread per node of the halo-1 region HX1 x HY1 (the collision
 // region), interior TX x TY = (HX1-2) x (HY1-2).  The D3Q19 FP32 tile uses
 // 512 threads and about 190 KB of shared memory.
-template <class L, class C>
+template <class L, class C, int HY = 0>
 struct FusedTile {
   static constexpr int HX1 = sizeof(C) == 8 ? 16 : 32;
-  static constexpr int HY1 = sizeof(C) == 8 ? 8 : (L::D == 3 ? 16 : 8);
+  static constexpr int HY1 = HY ? HY : (sizeof(C) == 8 ? 8 : (L::D == 3 ? 16 : 8));
   static constexpr int TX = HX1 - 2, TY = HY1 - 2;
 };
 
-template <class L, class C>
+template <class L, class S, class C, int HY = 0>
 struct FusedLayout {
   static constexpr int D = L::D;
-  static constexpr int TX = FusedTile<L, C>::TX, TY = FusedTile<L, C>::TY;
+  static constexpr int TX = FusedTile<L, C, HY>::TX, TY = FusedTile<L, C, HY>::TY;
   static constexpr int HX1 = TX + 2, HY1 = TY + 2, NH1 = HX1 * HY1;
   static constexpr int HX2 = TX + 4, HY2 = TY + 4, NH2 = HX2 * HY2;
   static constexpr int NT = NH1;
   static constexpr int RM = D == 3 ? 5 : 1;   // macro planes
   static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
   static constexpr int NMF = D + 3;           // rho, u (D), theta, E'
-  static constexpr size_t bytes =
+  // 3D FP32: the next plane's inputs are staged in shared memory with
+  // asynchronous copies while the current plane is finished
+  static constexpr bool stage = D == 3 && sizeof(S) == 4 && sizeof(C) == 4 && HY1 == 12;
+  // resident CTAs per SM the tile is sized for
+  static constexpr int min_blocks = (D == 3 && sizeof(C) == 4 && HY1 <= 8) ? 2 : 1;
+  static constexpr size_t ring_bytes =
       sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1 + 2 * (size_t)NH1);
+  static constexpr size_t stage_bytes =
+      stage ? 4 * ((size_t)(D + 2) * NH2 + (size_t)(L::Q + 1 + L::NDEV) * NH1) : 0;
+  static constexpr size_t bytes = ring_bytes + stage_bytes;
 };
 
 __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int node) {
@@ -80,20 +88,32 @@ __device__ __forceinline__ C recip(C x) {
   return C(1) / x;
 }
 
-template <class L, class S, class C>
-__global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
+// 4-byte asynchronous global -> shared copy (sm_80+ LDGSTS) and its fences
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class L, class S, class C, int HY>
+__global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S, C, HY>::min_blocks)
     k_fused(Grid g, FusedArgs<S, C> a, Phys<C> ph, int zchunk) {
-  using Lay = FusedLayout<L, C>;
+  using Lay = FusedLayout<L, S, C, HY>;
   constexpr int D = L::D, Q = L::Q;
   constexpr int TX = Lay::TX, TY = Lay::TY, NT = Lay::NT;
   constexpr int HX2 = Lay::HX2, NH2 = Lay::NH2, HX1 = Lay::HX1, NH1 = Lay::NH1;
   constexpr int RM = Lay::RM, RF = Lay::RF, NMF = Lay::NMF;
+  constexpr bool STG = Lay::stage;
   constexpr bool exact = std::is_same<C, double>::value;  // FP64: operations as in the oracle
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* mr = reinterpret_cast<C*>(smem_raw);        // [RM][NMF][NH2]
   C* fr = mr + (size_t)RM * NMF * NH2;           // [RF][Q][NH1]
   C* Fx = fr + (size_t)RF * Q * NH1;             // [NH1] +x face fluxes
   C* Fy = Fx + NH1;                              // [NH1] +y face fluxes
+  C* stM = Fy + NH1;                             // staged moments [(D+2)][NH2]
+  S* stF = reinterpret_cast<S*>(stM + (size_t)(D + 2) * NH2);  // staged populations [Q][NH1]
+  C* stA = reinterpret_cast<C*>(stF + (size_t)Q * NH1);        // staged P_prev, dAF [1+NDEV][NH1]
   const int t = threadIdx.x;
   const int cx = t % HX1, cy = t / HX1;          // halo-1 coordinates of this thread's node
   const int hx = cx + 1, hy = cy + 1;            // halo-2 coordinates
@@ -108,22 +128,36 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
 
   auto mslot = [&](int z) { return D == 3 ? ((z % RM) + RM) % RM : 0; };
   auto fslot = [&](int z) { return D == 3 ? ((z % RF) + RF) % RF : 0; };
+  auto halo2_node = [&](int k, int gz) {
+    const int kx = k % HX2, ky = k / HX2;
+    return g.lin(g.wrap(0, x0 + kx - 2), g.wrap(1, y0 + ky - 2), gz);
+  };
 
-  // corrected macros of plane z over the halo-2 region
-  auto load_macros = [&](int z) {
+  // corrected macros (rho, u, theta, rho E') of plane z over the halo-2 region,
+  // from the moments rho, rho u, rho E (staged copy or global memory)
+  auto load_macros = [&](int z, bool staged) {
     C* dst = mr + (size_t)mslot(z) * NMF * NH2;
     const int gz = g.wrap(2, z);
     for (int k = t; k < NH2; k += NT) {
-      const int kx = k % HX2, ky = k / HX2;
-      const long long n = g.lin(g.wrap(0, x0 + kx - 2), g.wrap(1, y0 + ky - 2), gz);
-      const C rho = a.M_in[n];
+      C rho, jm[3], E;
+      if (STG && staged) {
+        rho = stM[k];
+#pragma unroll
+        for (int d = 0; d < D; ++d) jm[d] = stM[(1 + d) * NH2 + k];
+        E = stM[(1 + D) * NH2 + k];
+      } else {
+        const long long n = halo2_node(k, gz);
+        rho = a.M_in[n];
+#pragma unroll
+        for (int d = 0; d < D; ++d) jm[d] = a.M_in[(1 + d) * N + n];
+        E = a.M_in[(1 + D) * N + n];
+      }
       C u[3], uu = C(0);
-      const C E = a.M_in[(1 + D) * N + n];
       C th;
       if constexpr (exact) {
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          u[d] = a.M_in[(1 + d) * N + n] / rho;
+          u[d] = jm[d] / rho;
           uu += u[d] * u[d];
         }
         th = (E / rho - C(0.5) * uu) / ph.Cv;
@@ -131,7 +165,7 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
         const C ir = recip(rho);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          u[d] = a.M_in[(1 + d) * N + n] * ir;
+          u[d] = jm[d] * ir;
           uu += u[d] * u[d];
         }
         th = (E * ir - C(0.5) * uu) * (C(1) / ph.Cv);
@@ -141,6 +175,25 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
       for (int d = 0; d < D; ++d) dst[(1 + d) * NH2 + k] = u[d];
       dst[(1 + D) * NH2 + k] = th;
       dst[(2 + D) * NH2 + k] = E;
+    }
+  };
+  // asynchronous copies of the inputs of plane zm (moments, halo 2) and of
+  // this thread's node of plane zf (populations, previous-step auxiliaries)
+  auto prefetch = [&](int zm, int zf) {
+    if constexpr (STG) {
+      const int gzm = g.wrap(2, zm);
+      for (int k = t; k < NH2; k += NT) {
+        const long long n = halo2_node(k, gzm);
+#pragma unroll
+        for (int q = 0; q < D + 2; ++q) cp_async4(&stM[q * NH2 + k], &a.M_in[q * N + n]);
+      }
+      const long long nf = g.lin(wx, wy, g.wrap(2, zf));
+#pragma unroll
+      for (int i = 0; i < Q; ++i) cp_async4(&stF[i * NH1 + t], &a.f_in[(long long)i * N + nf]);
+      cp_async4(&stA[t], &a.Pp[nf]);
+#pragma unroll
+      for (int q = 0; q < L::NDEV; ++q) cp_async4(&stA[(1 + q) * NH1 + t], &a.Ap[q * N + nf]);
+      cp_async_commit();
     }
   };
   auto macro_at = [&](int z, int kx, int ky) {
@@ -155,7 +208,7 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
     return m;
   };
   // collision of this thread's node of plane z (halo-1 region, one node per thread)
-  auto collide_plane = [&](int z) {
+  auto collide_plane = [&](int z, bool staged) {
     C* dst = fr + (size_t)fslot(z) * Q * NH1;
     const long long n = g.lin(wx, wy, g.wrap(2, z));
     auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
@@ -163,22 +216,35 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
     gradients<L, C>(MA, du, aC, ph.use_ac);
     const Macro<C> m = macro_at(z, hx, hy);
     C fbar[Q];
+    C dAFp[L::NDEV];
+    C Pp;
+    if (STG && staged) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
+      for (int i = 0; i < Q; ++i) {
+        const C v = C(Store<S>::load(stF[i * NH1 + t]));
+        fbar[i] = Store<S>::dev ? v + C(L::w(i)) : v;
+      }
+      Pp = stA[t];
+#pragma unroll
+      for (int q = 0; q < L::NDEV; ++q) dAFp[q] = stA[(1 + q) * NH1 + t];
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
+      Pp = a.Pp[n];
+#pragma unroll
+      for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
+    }
     C fu[3] = {C(0), C(0), C(0)};
     if (a.forced && a.forced[n]) {
       const int r = find_row_dev(a.cell_id, a.n_rows, (int)n);
 #pragma unroll
       for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
     }
-    C dAFp[L::NDEV];
-#pragma unroll
-    for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
     C fcol[Q], Pn, dAFn[L::NDEV];
     if constexpr (exact) {
-      collide<L, C>(fbar, m, du, aC, a.Pp[n], dAFp, fu, ph, fcol, Pn, dAFn);
+      collide<L, C>(fbar, m, du, aC, Pp, dAFp, fu, ph, fcol, Pn, dAFn);
     } else {
-      collide_fast<L, C>(fbar, m, du, aC, a.Pp[n], dAFp, fu, ph, fcol, Pn, dAFn);
+      collide_fast<L, C>(fbar, m, du, aC, Pp, dAFp, fu, ph, fcol, Pn, dAFn);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[i * NH1 + t] = fcol[i];
@@ -189,7 +255,7 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
     }
   };
   auto fcol_at = [&](int i, int z, int kx, int ky) { return fr[((size_t)fslot(z) * Q + i) * NH1 + ky * HX1 + kx]; };
-  // energy flux through the + face (axis AX) of the node at (cx+bx, cy+by, bz)
+  // energy flux through the + face (axis AX) of this thread's node of plane bz
   auto face = [&](auto AXc, int bz) {
     constexpr int AX = decltype(AXc)::value;
     auto MAl = [&](int k) {
@@ -199,12 +265,13 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
     return energy_face_flux<L, C, AX>(MAl, FCl, ph);
   };
 
-  // prologue
+  // prologue: macros of planes z0-2..z0+1, collisions of planes z0-1 and z0
   if constexpr (D == 3) {
-    for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z);
+    for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z, false);
     __syncthreads();
-    collide_plane(z0 - 1);
-    collide_plane(z0);
+    collide_plane(z0 - 1, false);
+    collide_plane(z0, false);
+    prefetch(z0 + 2, z0 + 1);
     __syncthreads();
   }
   // the -z face of plane z is the +z face of plane z-1: carried in a register
@@ -215,16 +282,20 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
   const bool xface = cx <= TX && cy >= 1 && cy <= TY;  // +x faces of nodes cx = 0..TX
   const bool yface = cy <= TY && cx >= 1 && cx <= TX;  // +y faces of nodes cy = 0..TY
   for (int z = z0; z < z1; ++z) {
-    if constexpr (D == 3) {
-      load_macros(z + 2);
-      __syncthreads();
-      collide_plane(z + 1);
-    } else {
-      load_macros(0);
-      __syncthreads();
-      collide_plane(0);
-    }
+    if constexpr (STG) cp_async_wait_all();
     __syncthreads();
+    if constexpr (D == 3) {
+      load_macros(z + 2, true);
+      __syncthreads();
+      collide_plane(z + 1, true);
+      __syncthreads();
+      prefetch(z + 3, z + 2);
+    } else {
+      load_macros(0, false);
+      __syncthreads();
+      collide_plane(0, false);
+      __syncthreads();
+    }
     C rho = C(0), j[3] = {C(0), C(0), C(0)};
     long long n = 0;
     if (interior) {
@@ -263,23 +334,35 @@ __global__ void __launch_bounds__(FusedLayout<L, C>::NT, 1)
       for (int d = 0; d < D; ++d) a.M_out[(1 + d) * N + n] = j[d];
       a.M_out[(1 + D) * N + n] = E;
     }
-    __syncthreads();
   }
+  if constexpr (STG) cp_async_wait_all();
 }
 
-// zchunk: planes per CTA along z (3D)
-template <class L, class S, class C>
-inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
-                         int zchunk) {
-  using Lay = FusedLayout<L, C>;
+template <class L, class S, class C, int HY>
+inline void launch_fused_tile(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
+                              int zchunk) {
+  using Lay = FusedLayout<L, S, C, HY>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fused<L, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
+    cudaFuncSetAttribute(k_fused<L, S, C, HY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
     attr = true;
   }
   dim3 grid((g.n[0] + Lay::TX - 1) / Lay::TX, (g.n[1] + Lay::TY - 1) / Lay::TY,
             L::D == 3 ? (g.n[2] + zchunk - 1) / zchunk : 1);
-  k_fused<L, S, C><<<grid, Lay::NT, Lay::bytes, st>>>(g, a, ph, zchunk);
+  k_fused<L, S, C, HY><<<grid, Lay::NT, Lay::bytes, st>>>(g, a, ph, zchunk);
+}
+
+// zchunk: planes per CTA along z (3D); tile_rows selects the halo-1 tile
+// height of the 3D FP32 kernel (8: two CTAs per SM, 12: staged inputs,
+// 16: one CTA per SM), 0 = default
+template <class L, class S, class C>
+inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
+                         int zchunk, int tile_rows) {
+  if constexpr (L::D == 3 && sizeof(C) == 4) {
+    if (tile_rows == 8) return launch_fused_tile<L, S, C, 8>(g, a, ph, st, zchunk);
+    if (tile_rows == 12) return launch_fused_tile<L, S, C, 12>(g, a, ph, st, zchunk);
+  }
+  launch_fused_tile<L, S, C, 0>(g, a, ph, st, zchunk);
 }
 
 // IB spreading applied to the predicted moments in place: rho u += f_u / 2,
