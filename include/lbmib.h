@@ -58,7 +58,9 @@ enum { IB_DIBM = 0, IB_FODIBM = 1, IB_FODIBM_R = 2 };
 /* per-face domain boundary: periodic; free-stream equilibrium (inlet or far
  * field); zero-gradient outlet.  Faces: x-, x+, y-, y+, z-, z+. */
 enum { LBM_BC_PERIODIC = 0, LBM_BC_INLET = 1, LBM_BC_OUTLET = 2, LBM_BC_FARFIELD = 3 };
-/* relaxation time: tau_LB = mu/(rho c_s^2 theta) or mu/(rho c_s^2) (Eq. LB) */
+/* relaxation time: tau_LB = mu/(rho c_s^2 theta), or tau_LB = nu/c_s^2 = mu/(rho c_s^2)
+ * as written in Eq. LB (the default; the theta-scaled variant is not stable for
+ * theta < 1 and gives a shear viscosity mu/theta) */
 enum { LBM_TAU_THETA = 0, LBM_TAU_LITERAL = 1 };
 /* temperature condition at a Lagrangian point (velocity is always Dirichlet) */
 enum { IB_T_DIRICHLET = 0, IB_T_NEUMANN = 1 };
@@ -81,7 +83,7 @@ typedef struct {
   double d_n;              /* projection distance d_PB in cells (default 1.5) */
   int method;              /* IB_DIBM / IB_FODIBM / IB_FODIBM_R */
   int bc[6];               /* LBM_BC_* per face */
-  int tau_mode;            /* LBM_TAU_THETA (default) or LBM_TAU_LITERAL */
+  int tau_mode;            /* LBM_TAU_LITERAL (default) or LBM_TAU_THETA */
   int use_ac;              /* 1: include the a^C term of Eq. af2 (default) */
   int device;              /* CUDA device ordinal */
   void* stream;            /* cudaStream_t, or NULL */
@@ -106,7 +108,7 @@ typedef struct {
 } ib_geometry;
 
 /* Fill *cfg with defaults (D2Q9, FP32, Pr 0.71, gamma 1.4, sigma 0.98,
- * d_n 1.5, FODIBM-R, periodic faces, theta-scaled tau, a^C on). */
+ * d_n 1.5, FODIBM-R, periodic faces, tau_LB = nu/c_s^2, a^C on). */
 lbm_status lbm_config_default(lbm_config* cfg);
 
 /* Create a case (Sec. 2.2): validates *cfg, derives u_inf, mu, lambda,

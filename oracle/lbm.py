@@ -20,21 +20,25 @@ design notes of the repository):
       N_k = sum_i w_i H3r_k,i^2 (2 c_s^6 for the '+' and 6 c_s^6 for the '-'
       D3Q19 combinations) in place of the printed single 1/(6 c_s^6).
   Q4  the trace projection in Eq. pi2 uses delta/D (delta/3 in 3D as printed).
-  Q6  a^C (Eq. af2, only cited): with m = rho (1 - theta) u,
-      a^C_ab = c_s^2 [d_b m_a + d_a m_b - (2/D) d_ab div m] - d_ab d_a(rho u_a^3),
-      the divergence of the defect of the equilibrium third moment with
-      respect to the Maxwellian at temperature theta, less the trace that the
-      explicit delta_ab terms of Eq. af2 already carry.  PARITY UNPINNED
-      against the paper; pinned by physics tests (shear viscosity equals mu
-      at theta != 1 and in a moving frame).
+  Q6  a^C (Eq. af2, only cited as the lattice-dependent component) =
+      -delta_ab d_a(rho u_a^3): the divergence of the diagonal third-order
+      equilibrium moment that D2Q9/D3Q19 cannot represent.  With the literal
+      tau_LB = nu/c_s^2 the lattice already gives the shear stress
+      -tau rho c_s^2 (grad u + grad u^T), and the explicit delta_ab terms of
+      Eq. af2 make the trace exactly the zero-bulk-viscosity one (linearized
+      Chapman-Enskog), so no theta correction is left for a^C.  PARITY
+      UNPINNED against the paper; pinned by physics tests (shear viscosity
+      equals mu at theta != 1 and in a moving frame; linear stability).
   Q7  spatial derivatives are 2nd-order central; time derivative of
       rho(1-theta) is the backward difference with the stored previous value.
   Q8  the F_i(t - dt) term of Eq. pi2 enters through its traceless second
       moment, the stored deviator of a^F of the previous step.
-  Q9  tau_LB = mu / (rho c_s^2 theta) ("theta-scaled", default) or
-      mu / (rho c_s^2) ("literal", Eq. LB); the finite-difference part of
-      Eq. pi2 uses rho c_s^2 theta^m tau-bar with the same m, so that it is
-      the Chapman-Enskog estimate -tau-bar p S of the f-bar stress.
+  Q9  tau_LB = nu / c_s^2 with nu = mu / rho (Eq. LB, default); a theta-scaled
+      variant mu / (rho c_s^2 theta) is kept as an option, with the
+      finite-difference part of Eq. pi2 scaled the same way.  The
+      theta-scaled variant needs a theta correction in a^C that is an
+      explicit anti-diffusion and is unstable for theta < 1; it is not the
+      paper's scheme.
   Q12 face values of h, k and u_beta in the energy flux are the arithmetic
       mean of the two cells sharing the face.
   Q14 no limiter; sign(0) = 0; u_alpha ~ = 0 takes the '+' branch; the
@@ -59,18 +63,19 @@ TAU_THETA, TAU_LITERAL = 0, 1
 def theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, dim):
     """Q11: T_ref is free (App. A: it sets the CFL number); theta_inf = T_inf/T_ref
     is the largest value <= 1 that keeps (a) u_inf = Ma sqrt(gamma c_s^2 theta)
-    <= 0.35 and (b) the explicit conduction number kappa = lambda/(rho C_v)
+    <= U_MAX and (b) the explicit conduction number kappa = lambda/(rho C_v)
     = mu gamma / Pr <= KAPPA_MAX[dim] (mu = u_inf L / Re scales with sqrt(theta))."""
     u1 = mach * np.sqrt(gamma * CS2)
     k1 = (u1 * ref_length / reynolds) * gamma / prandtl
     th = 1.0
-    if u1 > 0.35:
-        th = min(th, (0.35 / u1) ** 2)
+    if u1 > U_MAX:
+        th = min(th, (U_MAX / u1) ** 2)
     if k1 > KAPPA_MAX[dim]:
         th = min(th, (KAPPA_MAX[dim] / k1) ** 2)
     return th
 
 
+U_MAX = 0.15
 KAPPA_MAX = {2: 0.10, 3: 0.0667}
 
 
@@ -83,7 +88,7 @@ class Params:
 
     def __init__(self, lattice, shape, mach, reynolds, ref_length, prandtl=0.71,
                  gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98,
-                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_THETA, use_ac=True, mu=None):
+                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=True, mu=None):
         self.lat = L.get(lattice)
         D = self.lat.D
         self.shape = tuple(int(s) for s in shape)  # (nx, ny[, nz])
@@ -234,23 +239,17 @@ def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
     div = sum(du[a][a] for a in range(D))
     P = rho * (1.0 - theta)
     dPdt = P - P_prev
-    # a^C (reading Q6): deviatoric divergence of the theta-defect of the
-    # equilibrium third moment plus the diagonal u^3 defect of the lattice
+    # a^C (reading Q6): the lattice-dependent part of the force moment, the
+    # divergence of the diagonal third-order moment the lattice cannot carry
+    # (sum f^eq c_a^3 = rho u_a instead of rho u_a^3 + 3 rho c_s^2 theta u_a;
+    # with tau_LB = nu / c_s^2 the theta part of the defect is already
+    # absorbed by the explicit trace terms of Eq. af2)
+    aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
     if prm.use_ac:
         def cdiff(g, b):
             return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
-        m = [rho * (1.0 - theta) * u[a] for a in range(D)]
-        dm = [[cdiff(m[a], b) for b in range(D)] for a in range(D)]
-        divm = sum(dm[g][g] for g in range(D))
-        aC = [[None] * D for _ in range(D)]
         for a in range(D):
-            for b in range(D):
-                v = CS2 * (dm[a][b] + dm[b][a])
-                if a == b:
-                    v = v - CS2 * (2.0 / D) * divm - cdiff(rho * (u[a] * u[a] * u[a]), a)
-                aC[a][b] = v
-    else:
-        aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
+            aC[a][a] = -cdiff(rho * (u[a] * u[a] * u[a]), a)
     # Eq. af2
     aF = [[None] * D for _ in range(D)]
     for a in range(D):

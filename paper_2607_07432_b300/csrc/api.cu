@@ -38,13 +38,15 @@ const Ops* pick_ops(int lattice, int precision) {
   return nullptr;
 }
 
-// reading Q11: largest theta_inf <= 1 with u_inf <= 0.35 and kappa <= kappa_max
+// reading Q11: largest theta_inf <= 1 with u_inf <= 0.15 (lattice units) and
+// an explicit conduction number kappa = mu gamma / Pr <= kappa_max
 double theta_rule(double mach, double gamma, double re, double L, double pr, int D) {
+  const double umax = 0.15;
   const double u1 = mach * std::sqrt(gamma * (1.0 / 3.0));
   const double k1 = (u1 * L / re) * gamma / pr;
   const double kmax = D == 2 ? 0.10 : 0.0667;
   double th = 1.0;
-  if (u1 > 0.35) th = std::fmin(th, (0.35 / u1) * (0.35 / u1));
+  if (u1 > umax) th = std::fmin(th, (umax / u1) * (umax / u1));
   if (k1 > kmax) th = std::fmin(th, (kmax / k1) * (kmax / k1));
   return th;
 }
@@ -92,7 +94,7 @@ lbm_status lbm_config_default(lbm_config* c) {
   c->sigma_hrr = 0.98;
   c->d_n = 1.5;
   c->method = IB_FODIBM_R;
-  c->tau_mode = LBM_TAU_THETA;
+  c->tau_mode = LBM_TAU_LITERAL;
   c->use_ac = 1;
   return LBM_OK;
 }

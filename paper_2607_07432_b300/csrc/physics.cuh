@@ -65,15 +65,14 @@ __device__ __forceinline__ C feq_i(C rho, const C* u, C th) {
   return C(wi) * (rho + tth + t1 + t2 + t3);
 }
 
-// Velocity gradient du[a][b] = d u_a / d x_b and a^C (reading of the term
-// of Eq. af2 that the paper only cites): with m = rho (1-theta) u,
-// a^C_ab = c_s^2 [d_b m_a + d_a m_b - (2/D) d_ab div m] - d_ab d_a(rho u_a^3).
-// Central differences; MacroAt(dx,dy,dz) returns the neighbour's Macro.
+// Velocity gradient du[a][b] = d u_a / d x_b and a^C, the lattice-dependent
+// part of Eq. af2 (only cited by the paper): a^C_ab = -d_ab d_a(rho u_a^3),
+// the divergence of the diagonal third-order equilibrium moment that the
+// lattice cannot carry.  Central differences; MacroAt(dx,dy,dz) returns the
+// neighbour's Macro.
 template <class L, class C, class MacroAt>
 __device__ __forceinline__ void gradients(const MacroAt& M, C du[3][3], C aC[3][3], int use_ac) {
   constexpr int D = L::D;
-  C dm[3][3];
-  C dcube[3];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     const Macro<C> p = M(b == 0 ? 1 : 0, b == 1 ? 1 : 0, b == 2 ? 1 : 0);
@@ -81,31 +80,11 @@ __device__ __forceinline__ void gradients(const MacroAt& M, C du[3][3], C aC[3][
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       du[a][b] = (p.u[a] - m.u[a]) * C(0.5);
-      const C mp = p.rho * (C(1) - p.th) * p.u[a];
-      const C mm = m.rho * (C(1) - m.th) * m.u[a];
-      dm[a][b] = (mp - mm) * C(0.5);
+      aC[a][b] = C(0);
     }
-    dcube[b] = (p.rho * (p.u[b] * p.u[b] * p.u[b]) - m.rho * (m.u[b] * m.u[b] * m.u[b])) * C(0.5);
+    if (use_ac)
+      aC[b][b] = -((p.rho * (p.u[b] * p.u[b] * p.u[b]) - m.rho * (m.u[b] * m.u[b] * m.u[b])) * C(0.5));
   }
-  if (!use_ac) {
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = 0; b < D; ++b) aC[a][b] = C(0);
-    return;
-  }
-  C divm = C(0);
-#pragma unroll
-  for (int g = 0; g < D; ++g) divm += dm[g][g];
-  const C cs2 = C(kCs2);
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      C v = cs2 * (dm[a][b] + dm[b][a]);
-      if (a == b) v = v - cs2 * (C(2) / C(D)) * divm - dcube[a];
-      aC[a][b] = v;
-    }
 }
 
 // expand stored deviator slots to a full symmetric traceless tensor

@@ -91,7 +91,7 @@ class Solver:
 
     def __init__(self, lattice="D2Q9", precision="fp32", shape=(64, 64), mach=0.1, reynolds=100.0,
                  ref_length=10.0, prandtl=0.71, gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0),
-                 sigma=0.98, d_n=1.5, method=FODIBM_R, bc=None, tau_mode=TAU_THETA, use_ac=True,
+                 sigma=0.98, d_n=1.5, method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=True,
                  device=0, stream=None):
         L = lib()
         cfg = Config()
