@@ -39,6 +39,22 @@ BYTES_PER_LU = {("D3Q19", "fp32"): 2 * 19 * 4 + 2 * 7 * 4, ("D3Q19", "fp16"): 2 
                 ("D2Q9", "fp32"): 2 * 9 * 4 + 2 * 4 * 4, ("D2Q9", "fp64"): 2 * 9 * 8 + 2 * 4 * 8}
 
 
+def kernel_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    capture, if the kernel sources are unchanged since that capture."""
+    import glob
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "fused_step_sphere256_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2607_07432_b300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return float(d["dram_bytes_per_launch"]) if h.hexdigest() == d["src_sha256"] else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -60,7 +76,7 @@ class ClockSampler:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -222,12 +238,12 @@ def main():
     bpl = BYTES_PER_LU[(CASE["lattice"], args.precision)]
     step_ms, step_n = prof["step"]
     other_ms, other_n = prof["other"]
-    # dominant kernel class: the LBM step (collision + streaming + energy;
-    # the separate macroscopic pass of the unfused form counts with it)
+    # dominant kernel: the fused collide-stream-energy step kernel
     kern_ms = (step_ms + other_ms) / args.steps
     achieved = bpl * N / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_kind": peak_kind, "bytes_per_lu": bpl,
+            "traffic": kernel_traffic() if args.precision == "fp32" else None, "peak_kind": peak_kind,
+            "bytes_per_lu": bpl,
             "kernel_ms_per_step": kern_ms,
             "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
     cpu = None
