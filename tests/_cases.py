@@ -23,6 +23,14 @@ def small_cylinder_periodic(method=2):
                 geo=lambda th: inputs.cylinder((15.3, 16.4), 10.0, 32, tbc=0, t_value=1.05 * th))
 
 
+def ellipse_case(method=2):
+    """Rotated ellipse (aspect 2.5) on a 96x64 grid: exercises the ellipse
+    classification predicate."""
+    return dict(lattice="D2Q9", shape=(96, 64), mach=0.3, reynolds=60.0, ref_length=30.0,
+                bc=[BC_IN, BC_OUT, BC_FF, BC_FF], method=method,
+                geo=lambda th: inputs.ellipse((40.3, 31.7), 15.0, 6.0, 0.6, 80, tbc=0, t_value=1.05 * th))
+
+
 def small_sphere(method=2, bc=None):
     return dict(lattice="D3Q19", shape=(24, 20, 20), mach=0.2, reynolds=20.0, ref_length=8.0,
                 bc=bc or [BC_IN, BC_OUT, BC_FF, BC_FF, BC_FF, BC_FF], method=method,

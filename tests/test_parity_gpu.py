@@ -20,7 +20,8 @@ def _rel_l2(a, b):
 
 
 @pytest.mark.parametrize("case_fn", [C.cylinder_c1, C.small_cylinder_periodic, C.small_sphere,
-                                     C.naca_downscale])
+                                     C.naca_downscale, lambda: C.small_cylinder_periodic(method=0),
+                                     C.ellipse_case])
 def test_ib_setup_parity(case_fn):
     """Classification, spreading CSR, phi, W, X*, d_BV and CSR weights
     bit-exact."""
@@ -43,12 +44,15 @@ def test_ib_setup_parity(case_fn):
     g.close()
 
 
-@pytest.mark.parametrize("case_fn,steps", [(C.small_cylinder_periodic, 1), (C.small_cylinder_periodic, 30),
-                                           (C.small_sphere, 1), (C.small_sphere, 10)])
-def test_fp64_step_parity_perturbed(case_fn, steps):
-    """FP64 path vs oracle from a seeded perturbed state, with the body:
-    max relative error of populations and rho E <= 1e-12."""
-    case = case_fn()
+@pytest.mark.parametrize("case_fn,steps,method", [(C.small_cylinder_periodic, 1, 2), (C.small_cylinder_periodic, 30, 2),
+                                                  (C.small_cylinder_periodic, 30, 1), (C.small_cylinder_periodic, 30, 0),
+                                                  (C.small_sphere, 1, 2), (C.small_sphere, 10, 2),
+                                                  (C.small_sphere, 10, 0)])
+def test_fp64_step_parity_perturbed(case_fn, steps, method):
+    """FP64 path vs oracle from a seeded perturbed state, with the body, for
+    FODIBM-R (2), FODIBM (1) and DIBM (0): max relative error of populations
+    and rho E <= 1e-12."""
+    case = case_fn(method=method)
     sim, geo = C.make_oracle(case)
     C.perturb(sim, seed=11)
     g = C.make_gpu(case, "fp64", geo)
