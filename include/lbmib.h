@@ -208,6 +208,38 @@ lbm_status lbm_get_profile(lbm_handle* h, double ms[5], long long launches[5]);
 /* Number of kernels this handle has launched since creation. */
 long long lbm_launch_count(const lbm_handle* h);
 
+/* ---- several cases advanced together ------------------------------------
+ * A batch owns n cases (same lattice, precision and device; grids, bodies
+ * and flow parameters may differ) on one stream of its own.  A batched step
+ * runs each case's immersed-boundary and boundary kernels around one fused
+ * launch that covers the tiles of every case in a schedule order; two steps
+ * are captured once as a CUDA graph and replayed.  Results are bit-identical
+ * to stepping each case on its own. */
+typedef struct lbm_batch lbm_batch;
+
+/* Create n cases from cfgs[0..n-1] (their stream fields are ignored). */
+lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_batch** out);
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+/* Borrow case i's handle (geometry, fields, loads); owned by the batch. */
+lbm_status lbm_batch_case(lbm_batch* b, int i, lbm_handle** h);
+/* Advance every case n_steps steps with batched launches (graph replay). */
+lbm_status lbm_batch_step(lbm_batch* b, int n_steps);
+/* Advance every case n_steps steps one case after another with per-case
+ * launches (the unbatched form, for comparison). */
+lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps);
+/* Wait for the batch stream. */
+lbm_status lbm_batch_sync(lbm_batch* b);
+/* Fused-launch plan: tile_rows 0 (default tile) or 16 (2D FP32 only), and
+ * schedule 0 = case-major, 1 = round-robin over cases, 2 = largest first. */
+lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule);
+lbm_status lbm_batch_get_plan(const lbm_batch* b, int* tile_rows, int* schedule);
+/* Autotuner: times each plan over `steps` batched steps on the batch itself
+ * (state saved before and restored after) and keeps the fastest; with
+ * cache_path, results are read from / appended to that text file keyed by
+ * the case set.  *best_ms (optional) receives the best time per step. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, double* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -411,6 +411,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     CK(cudaMemsetAsync(h->WQ, 0, (size_t)nrows * 8, h->st));
     CK(cudaStreamSynchronize(h->st));
     h->has_ib = true;
+    h->geom_version++;
   }
 done:
   cudaStreamSynchronize(h->st);

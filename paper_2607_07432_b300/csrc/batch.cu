@@ -1,0 +1,309 @@
+// Batched stepping of several cases (lbm_batch_*): the per-case immersed
+// boundary and boundary kernels surround one fused launch that covers the
+// tiles of every case, from a schedule table; two consecutive steps (both
+// buffer parities) are captured once as a CUDA graph and replayed.  The
+// autotuner times the tile heights and schedules on the batch and keeps the
+// fastest; it restores the state it advanced.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+
+using namespace lbmib_host;
+
+struct lbm_batch {
+  BatchPlan plan;
+  cudaStream_t st = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_ok = false;
+  const Ops* ops = nullptr;
+  std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+
+void drop_graph(lbm_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->graph_ok = false;
+}
+
+// the plan matches the handles when every case is at the parity it was
+// built for and no geometry changed since
+bool plan_current(lbm_batch* b) {
+  BatchPlan& p = b->plan;
+  if (!p.built) return false;
+  for (size_t k = 0; k < p.cases.size(); ++k)
+    if (p.cases[k]->f != p.built_f[k] || p.cases[k]->geom_version != p.built_geom[k]) return false;
+  return true;
+}
+
+lbm_status rebuild(lbm_batch* b) {
+  drop_graph(b);
+  BatchPlan& p = b->plan;
+  lbm_status s = b->ops->batch_build(&p);
+  if (s) return bfail(b, s, p.err.empty() ? "batch plan" : p.err);
+  p.built_f.clear();
+  p.built_geom.clear();
+  for (lbm_handle* h : p.cases) {
+    p.built_f.push_back(h->f);
+    p.built_geom.push_back(h->geom_version);
+  }
+  p.built = true;
+  return LBM_OK;
+}
+
+// one step of every case, eager (also used while capturing)
+lbm_status one_step(lbm_batch* b, int parity) {
+  BatchPlan& p = b->plan;
+  for (lbm_handle* h : p.cases) {
+    if (h->sticky) return (lbm_status)h->sticky;
+    lbm_status s = b->ops->ib_part(h);
+    if (s) return bfail(b, s, h->err);
+  }
+  lbm_status s = b->ops->batch_fused(&p, parity);
+  if (s) return bfail(b, s, p.err);
+  for (lbm_handle* h : p.cases) {
+    std::swap(h->f, h->f2);
+    std::swap(h->M, h->M2);
+    h->cur = 1 - h->cur;
+    lbm_status s2 = b->ops->bc_part(h);
+    if (s2) return bfail(b, s2, h->err);
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_batch** out) {
+  if (n <= 0 || !cfgs || !out) return LBM_EINVAL;
+  *out = nullptr;
+  for (int k = 1; k < n; ++k)
+    if (cfgs[k].lattice != cfgs[0].lattice || cfgs[k].precision != cfgs[0].precision ||
+        cfgs[k].device != cfgs[0].device)
+      return LBM_EINVAL;
+  lbm_batch* b = new lbm_batch();
+  if (cudaSetDevice(cfgs[0].device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return LBM_ECUDA;
+  }
+  b->plan.st = b->st;
+  for (int k = 0; k < n; ++k) {
+    lbm_config c = cfgs[k];
+    c.stream = b->st;
+    lbm_handle* h = nullptr;
+    lbm_status s = lbm_create(&c, &h);
+    if (s) {
+      lbm_batch_destroy(b);
+      return s;
+    }
+    b->plan.cases.push_back(h);
+  }
+  b->ops = b->plan.cases[0]->ops;
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  drop_graph(b);
+  for (lbm_handle* h : b->plan.cases) lbm_destroy(h);
+  for (int p = 0; p < 2; ++p)
+    if (b->plan.descs[p]) cudaFree(b->plan.descs[p]);
+  if (b->plan.work) cudaFree(b->plan.work);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+lbm_status lbm_batch_case(lbm_batch* b, int i, lbm_handle** h) {
+  if (!b || !h || i < 0 || i >= (int)b->plan.cases.size()) return LBM_EINVAL;
+  *h = b->plan.cases[i];
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule) {
+  if (!b || (tile_rows != 0 && tile_rows != 16) || schedule < 0 || schedule > 2) return LBM_EINVAL;
+  b->plan.tile_rows = tile_rows;
+  b->plan.schedule = schedule;
+  b->plan.built = false;
+  drop_graph(b);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_plan(const lbm_batch* b, int* tile_rows, int* schedule) {
+  if (!b) return LBM_EINVAL;
+  if (tile_rows) *tile_rows = b->plan.tile_rows;
+  if (schedule) *schedule = b->plan.schedule;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
+  if (!b || n_steps < 0) return LBM_EINVAL;
+  int done = 0;
+  while (done < n_steps) {
+    if (!plan_current(b)) {
+      // the cases are at the other parity (odd number of eager steps) or a
+      // geometry changed: rebuild the plan for the current state
+      lbm_status s = rebuild(b);
+      if (s) return s;
+    }
+    if (n_steps - done >= 2) {
+      if (!b->graph_ok) {
+        cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        lbm_status s = one_step(b, 0);
+        lbm_status s2 = s ? s : one_step(b, 1);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->st, &g);
+        if (s2 || e != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          return s2 ? s2 : bfail(b, LBM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        b->graph = g;
+        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+          drop_graph(b);
+          return bfail(b, LBM_ECUDA, "graph instantiate");
+        }
+        b->graph_ok = true;
+      }
+      if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return bfail(b, LBM_ECUDA, "graph launch");
+      done += 2;
+    } else {
+      lbm_status s = one_step(b, 0);
+      if (s) return s;
+      done += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps) {
+  if (!b || n_steps < 0) return LBM_EINVAL;
+  for (lbm_handle* h : b->plan.cases) {
+    lbm_status s = lbm_step(h, n_steps);
+    if (s) return bfail(b, s, h->err);
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+  if (!b) return LBM_EINVAL;
+  return cudaStreamSynchronize(b->st) == cudaSuccess ? LBM_OK : bfail(b, LBM_ECUDA, "sync");
+}
+
+// Time every (tile rows, schedule) candidate over `steps` batched steps and
+// keep the fastest.  The state each trial advances is saved before and
+// restored after.  With cache_path, a result for the same case set is read
+// from / appended to that text file ("key tile_rows schedule" lines).
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, double* best_ms) {
+  if (!b || steps <= 0) return LBM_EINVAL;
+  BatchPlan& p = b->plan;
+  std::ostringstream key;
+  key << p.cases.size() << ":" << p.cases[0]->cfg.lattice << ":" << p.cases[0]->cfg.precision;
+  for (lbm_handle* h : p.cases) key << ":" << h->g.n[0] << "x" << h->g.n[1] << "x" << h->g.n[2] << "/" << h->NL;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string k;
+    int tr, sc;
+    while (in >> k >> tr >> sc)
+      if (k == key.str()) return lbm_batch_set_plan(b, tr, sc);
+  }
+  // save the state
+  struct Saved {
+    std::vector<std::pair<void*, size_t>> bufs;
+    std::vector<void*> copies;
+  } sv;
+  for (lbm_handle* h : p.cases) {
+    const size_t N = (size_t)h->g.N;
+    sv.bufs.push_back({h->f, N * h->Q * h->ssize});
+    sv.bufs.push_back({h->M, N * (h->D + 2) * h->csize});
+    sv.bufs.push_back({h->P[h->cur], N * h->csize});
+    sv.bufs.push_back({h->A[h->cur], N * h->NDEV * h->csize});
+  }
+  for (auto& bf : sv.bufs) {
+    void* c = nullptr;
+    if (cudaMalloc(&c, bf.second) != cudaSuccess) {
+      for (void* q : sv.copies) cudaFree(q);
+      return bfail(b, LBM_ENOMEM, "autotune snapshot");
+    }
+    cudaMemcpyAsync(c, bf.first, bf.second, cudaMemcpyDeviceToDevice, b->st);
+    sv.copies.push_back(c);
+  }
+  std::vector<void*> f0, M0;
+  std::vector<int> cur0;
+  for (lbm_handle* h : p.cases) {
+    f0.push_back(h->f);
+    M0.push_back(h->M);
+    cur0.push_back(h->cur);
+  }
+  auto restore = [&]() {
+    for (size_t k = 0; k < p.cases.size(); ++k) {
+      lbm_handle* h = p.cases[k];
+      if (h->f != f0[k]) {
+        std::swap(h->f, h->f2);
+        std::swap(h->M, h->M2);
+      }
+      h->cur = cur0[k];
+    }
+    for (size_t i = 0; i < sv.bufs.size(); ++i)
+      cudaMemcpyAsync(sv.bufs[i].first, sv.copies[i], sv.bufs[i].second, cudaMemcpyDeviceToDevice, b->st);
+  };
+  const int rows[2] = {0, 16};
+  const int nrows = (p.cases[0]->D == 2 && p.cases[0]->csize == 4) ? 2 : 1;
+  double best = 1e300;
+  int best_r = 0, best_s = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  lbm_status st = LBM_OK;
+  for (int ri = 0; ri < nrows && !st; ++ri)
+    for (int sc = 0; sc < 3 && !st; ++sc) {
+      lbm_batch_set_plan(b, rows[ri], sc);
+      st = lbm_batch_step(b, 2);  // warm-up and capture
+      if (st) break;
+      cudaEventRecord(e0, b->st);
+      st = lbm_batch_step(b, 2 * ((steps + 1) / 2));
+      cudaEventRecord(e1, b->st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_r = rows[ri];
+        best_s = sc;
+      }
+      restore();
+    }
+  cudaStreamSynchronize(b->st);
+  for (void* q : sv.copies) cudaFree(q);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  lbm_batch_set_plan(b, best_r, best_s);
+  if (best_ms) *best_ms = best / (2 * ((steps + 1) / 2));
+  if (cache_path) {
+    std::ofstream o(cache_path, std::ios::app);
+    o << key.str() << " " << best_r << " " << best_s << "\n";
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"

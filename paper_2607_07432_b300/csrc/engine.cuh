@@ -176,6 +176,128 @@ struct Engine {
                        cudaMemcpyDeviceToDevice, h->st));
     return LBM_OK;
   }
+  static lbm_status ib_part(lbm_handle* h) { return h->has_ib ? ib_force(h) : LBM_OK; }
+  static lbm_status bc_part(lbm_handle* h) { return bc(h); }
+  static FusedArgs<S, C> fused_args(lbm_handle* h, int parity) {
+    // parity 0: the handle's current buffers; parity 1: the swapped ones
+    FusedArgs<S, C> a;
+    const bool sw = parity != 0;
+    a.f_in = (const S*)(sw ? h->f2 : h->f);
+    a.f_out = (S*)(sw ? h->f : h->f2);
+    a.M_in = (const C*)(sw ? h->M2 : h->M);
+    a.M_out = (C*)(sw ? h->M : h->M2);
+    const int c0 = sw ? 1 - h->cur : h->cur;
+    a.Pp = (const C*)h->P[c0];
+    a.Pn = (C*)h->P[1 - c0];
+    a.Ap = (const C*)h->A[c0];
+    a.An = (C*)h->A[1 - c0];
+    a.forced = h->has_ib ? h->forced : nullptr;
+    a.cell_id = h->cell_id;
+    a.n_rows = h->n_rows;
+    a.FU = h->FU;
+    return a;
+  }
+  template <int HY>
+  static void batch_tiles(lbm_handle* h, int& tx, int& ty, int& tz) {
+    using Lay = FusedLayout<L, S, C, HY>;
+    tx = (h->g.n[0] + Lay::TX - 1) / Lay::TX;
+    ty = (h->g.n[1] + Lay::TY - 1) / Lay::TY;
+    tz = L::D == 3 ? (h->g.n[2] + h->zchunk - 1) / h->zchunk : 1;
+  }
+  static lbm_status batch_build(BatchPlan* b) {
+    const int n = (int)b->cases.size();
+    std::vector<CaseDesc<S, C>> d0(n), d1(n);
+    std::vector<int> tx(n), ty(n), tz(n);
+    for (int k = 0; k < n; ++k) {
+      lbm_handle* h = b->cases[k];
+      if (!h->use_fused) {
+        b->err = "batched stepping needs the fused step";
+        return LBM_EUNSUPPORTED;
+      }
+      for (int p = 0; p < 2; ++p) {
+        CaseDesc<S, C>& d = p ? d1[k] : d0[k];
+        d.g = h->g;
+        d.a = fused_args(h, p);
+        d.ph = phys(h);
+        d.zchunk = h->zchunk;
+      }
+      bool done = false;
+      if constexpr (L::D == 2 && sizeof(C) == 4) {
+        if (b->tile_rows == 16) {
+          batch_tiles<16>(h, tx[k], ty[k], tz[k]);
+          done = true;
+        }
+      }
+      if (!done) batch_tiles<0>(h, tx[k], ty[k], tz[k]);
+    }
+    // work items in schedule order
+    std::vector<int4> w;
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    if (b->schedule == 2)
+      std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return tx[p] * ty[p] * tz[p] > tx[q] * ty[q] * tz[q]; });
+    if (b->schedule == 1) {
+      std::vector<int> left(n);
+      size_t total = 0;
+      for (int k = 0; k < n; ++k) total += (size_t)tx[k] * ty[k] * tz[k];
+      std::vector<int> pos(n, 0);
+      while (w.size() < total)
+        for (int k = 0; k < n; ++k) {
+          const int cnt = tx[k] * ty[k] * tz[k];
+          if (pos[k] < cnt) {
+            const int i = pos[k]++;
+            w.push_back(make_int4(k, i % tx[k], (i / tx[k]) % ty[k], i / (tx[k] * ty[k])));
+          }
+        }
+    } else {
+      for (int k : order)
+        for (int bz = 0; bz < tz[k]; ++bz)
+          for (int by = 0; by < ty[k]; ++by)
+            for (int bx = 0; bx < tx[k]; ++bx) w.push_back(make_int4(k, bx, by, bz));
+    }
+    for (int p = 0; p < 2; ++p) {
+      if (b->descs[p]) cudaFree(b->descs[p]);
+      if (cudaMalloc(&b->descs[p], sizeof(CaseDesc<S, C>) * n) != cudaSuccess) return LBM_ENOMEM;
+      if (cudaMemcpy(b->descs[p], p ? d1.data() : d0.data(), sizeof(CaseDesc<S, C>) * n, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+        return LBM_ECUDA;
+    }
+    if (b->work) cudaFree(b->work);
+    if (cudaMalloc(&b->work, sizeof(int4) * w.size()) != cudaSuccess) return LBM_ENOMEM;
+    if (cudaMemcpy(b->work, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return LBM_ECUDA;
+    b->n_work = (int)w.size();
+    return LBM_OK;
+  }
+  template <int HY>
+  static void batch_launch(BatchPlan* b, int parity) {
+    using Lay = FusedLayout<L, S, C, HY>;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_fused_batched<L, S, C, HY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Lay::bytes);
+      attr = true;
+    }
+    k_fused_batched<L, S, C, HY><<<b->n_work, Lay::NT, Lay::bytes, b->st>>>(
+        (const CaseDesc<S, C>*)b->descs[parity], (const int4*)b->work);
+  }
+  static lbm_status batch_fused(BatchPlan* b, int parity) {
+    bool done = false;
+    if constexpr (L::D == 2 && sizeof(C) == 4) {
+      if (b->tile_rows == 16) {
+        batch_launch<16>(b, parity);
+        done = true;
+      }
+    }
+    if (!done) batch_launch<0>(b, parity);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      b->err = std::string("batched launch: ") + cudaGetErrorString(e);
+      return LBM_ECUDA;
+    }
+    for (lbm_handle* h : b->cases) h->launches++;
+    return LBM_OK;
+  }
   static lbm_status step(lbm_handle* h) {
     lbm_status s;
     if (h->has_ib && (s = ib_force(h))) return s;
@@ -228,7 +350,8 @@ struct Engine {
     });
   }
   static const Ops* ops() {
-    static const Ops o = {&init, &step, &fields, &get_state, &set_state, &set_fields_api, &health};
+    static const Ops o = {&init,   &step,        &fields,      &get_state, &set_state, &set_fields_api,
+                          &health, &batch_build, &batch_fused, &ib_part,   &bc_part};
     return &o;
   }
 };

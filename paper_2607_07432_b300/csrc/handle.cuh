@@ -61,6 +61,7 @@ struct lbm_handle {
   std::string err;
   long long launches = 0;
   int sticky = LBM_OK;
+  int geom_version = 0;
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
@@ -115,6 +116,7 @@ inline lbm_status launch(lbm_handle* h, int cls, F&& fn) {
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+struct BatchPlan;
 struct Ops {
   lbm_status (*init)(lbm_handle*);
   lbm_status (*step)(lbm_handle*);
@@ -123,6 +125,29 @@ struct Ops {
   lbm_status (*set_state)(lbm_handle*, const double*, const double*);
   lbm_status (*set_fields)(lbm_handle*, const double*, const double*, const double*);
   lbm_status (*health)(lbm_handle*, unsigned long long*);
+  // batched step support: build the case descriptors and the work schedule
+  // of a plan, and launch one batched fused step of the given parity
+  lbm_status (*batch_build)(BatchPlan*);
+  lbm_status (*batch_fused)(BatchPlan*, int parity);
+  // per-case parts of a step around the fused kernel
+  lbm_status (*ib_part)(lbm_handle*);
+  lbm_status (*bc_part)(lbm_handle*);
+};
+
+// A set of cases advanced together (lbm_batch_*): one fused launch covers
+// every case; the per-case IB and boundary kernels surround it.
+struct BatchPlan {
+  std::vector<lbm_handle*> cases;
+  cudaStream_t st = nullptr;
+  int tile_rows = 0;   // 0: the default tile of the lattice / precision
+  int schedule = 0;    // 0 case-major, 1 round-robin over cases, 2 largest case first
+  void* descs[2] = {nullptr, nullptr};   // device CaseDesc arrays, parity 0 / 1
+  void* work = nullptr;                  // device int4 work items
+  int n_work = 0;
+  std::vector<void*> built_f;            // per case h->f at build time (parity 0)
+  std::vector<int> built_geom;           // per case geometry version at build time
+  bool built = false;
+  std::string err;
 };
 
 

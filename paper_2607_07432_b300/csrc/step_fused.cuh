@@ -96,9 +96,10 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// body of the fused step for the tile (bx, by) and z-chunk bz of one case
 template <class L, class S, class C, int HY>
-__global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S, C, HY>::min_blocks)
-    k_fused(Grid g, FusedArgs<S, C> a, Phys<C> ph, int zchunk) {
+__device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, int zchunk,
+                                           int bx, int by, int bz) {
   using Lay = FusedLayout<L, S, C, HY>;
   constexpr int D = L::D, Q = L::Q;
   constexpr int TX = Lay::TX, TY = Lay::TY, NT = Lay::NT;
@@ -117,10 +118,10 @@ __global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S
   const int t = threadIdx.x;
   const int cx = t % HX1, cy = t / HX1;          // halo-1 coordinates of this thread's node
   const int hx = cx + 1, hy = cy + 1;            // halo-2 coordinates
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = bx * TX, y0 = by * TY;
   const int gx = x0 + cx - 1, gy = y0 + cy - 1;
   const int nz = g.n[2];
-  const int z0 = D == 3 ? blockIdx.z * zchunk : 0;
+  const int z0 = D == 3 ? bz * zchunk : 0;
   const int z1 = D == 3 ? min(nz, z0 + zchunk) : 1;
   const long long N = g.N;
   const bool interior = cx >= 1 && cx <= TX && cy >= 1 && cy <= TY && gx < g.n[0] && gy < g.n[1];
@@ -336,6 +337,30 @@ __global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S
     }
   }
   if constexpr (STG) cp_async_wait_all();
+}
+
+template <class L, class S, class C, int HY>
+__global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S, C, HY>::min_blocks)
+    k_fused(Grid g, FusedArgs<S, C> a, Phys<C> ph, int zchunk) {
+  fused_body<L, S, C, HY>(g, a, ph, zchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several cases in one launch: work item k = (case, tile x, tile y, z-chunk)
+// from a schedule table; each block reads its case's descriptor.
+template <class S, class C>
+struct CaseDesc {
+  Grid g;
+  FusedArgs<S, C> a;
+  Phys<C> ph;
+  int zchunk;
+};
+
+template <class L, class S, class C, int HY>
+__global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S, C, HY>::min_blocks)
+    k_fused_batched(const CaseDesc<S, C>* descs, const int4* work) {
+  const int4 w = work[blockIdx.x];
+  const CaseDesc<S, C>& d = descs[w.x];
+  fused_body<L, S, C, HY>(d.g, d.a, d.ph, d.zchunk, w.y, w.z, w.w);
 }
 
 template <class L, class S, class C, int HY>

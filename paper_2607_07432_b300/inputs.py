@@ -116,10 +116,10 @@ def icosphere(center, diameter, frequency, tbc=0, t_value=1.0):
     return _as_geometry(X, U, shape, tbc, t_value)
 
 
-def batch_cases(n_cases, seed):
+def batch_cases(n_cases, seed, mach_range=(0.1, 0.8)):
     """Seeded uneven 2D case set (circles and ellipses, aspect 1-3, diameters
-    10-60, 32-512 points, grids 256x128 .. 1024x512, Ma in [0.1, 0.8],
-    Re in [20, 200])."""
+    10-60, 32-512 points, grids 256x128 .. 1024x512, Ma uniform in
+    mach_range, Re in [20, 200])."""
     rng = np.random.Generator(np.random.PCG64(seed))
     cases = []
     for _ in range(n_cases):
@@ -132,7 +132,7 @@ def batch_cases(n_cases, seed):
         ang = rng.uniform(0.0, np.pi)
         per = np.pi * (3 * (a + b) - np.sqrt((3 * a + b) * (a + 3 * b)))
         nl = int(min(512, max(32, round(per))))
-        ma = rng.uniform(0.1, 0.8)
+        ma = rng.uniform(mach_range[0], mach_range[1])
         re = rng.uniform(20.0, 200.0)
         cases.append(dict(nx=nx, ny=ny, a=a, b=b, angle=ang, n_points=nl, mach=ma, reynolds=re,
                           ellipse=ellipse_, ref_length=dmaj))

@@ -27,7 +27,10 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
 EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", "ib_set_geometry",
            "lbm_step", "lbm_check", "lbm_get_fields", "lbm_get_state", "lbm_set_state", "lbm_set_fields",
            "lbm_get_wall_loads", "lbm_get_constants", "ib_get_sizes", "ib_get_setup", "lbm_profile",
-           "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc"]
+           "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_batch_create",
+           "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_case", "lbm_batch_step",
+           "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
+           "lbm_batch_autotune"]
 
 
 class Config(ct.Structure):
@@ -55,6 +58,13 @@ def load():
     lib.lbm_last_error.restype = ct.c_char_p
     lib.lbm_launch_count.restype = ct.c_longlong
     lib.lbm_create.argtypes = [ct.POINTER(Config), ct.POINTER(ct.c_void_p)]
+    lib.lbm_batch_last_error.restype = ct.c_char_p
+    lib.lbm_batch_last_error.argtypes = [ct.c_void_p]
+    lib.lbm_batch_destroy.argtypes = [ct.c_void_p]
+    lib.lbm_batch_step.argtypes = [ct.c_void_p, ct.c_int]
+    lib.lbm_batch_step_sequential.argtypes = [ct.c_void_p, ct.c_int]
+    lib.lbm_batch_sync.argtypes = [ct.c_void_p]
+    lib.lbm_batch_set_plan.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
     for name in ("lbm_step",):
         getattr(lib, name).argtypes = [ct.c_void_p, ct.c_int]
     for name in ("lbm_destroy", "lbm_check", "lbm_last_error", "lbm_launch_count"):
@@ -269,3 +279,102 @@ class Solver:
 
     def launch_count(self):
         return int(lib().lbm_launch_count(self.h))
+
+
+class CaseView(Solver):
+    """A case owned by a Batch (borrowed handle; not destroyed on close)."""
+
+    def __init__(self, handle, lattice, shape):
+        self.h = handle
+        self.D = 2 if lattice == "D2Q9" else 3
+        self.Q = 9 if self.D == 2 else 19
+        self.shape = tuple(int(v) for v in shape)
+        self.N = int(np.prod(self.shape))
+        self.zyx = tuple(reversed(self.shape))
+        self.NL = 0
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Several cases advanced together (lbm_batch_*)."""
+
+    def __init__(self, lattice, precision, cases, device=0):
+        """cases: list of dicts with shape, mach, reynolds, ref_length and
+        optional bc, method, inflow_dir, theta_inf, prandtl, gamma."""
+        L = lib()
+        n = len(cases)
+        cfgs = (Config * n)()
+        self.lattice = lattice
+        D = 2 if lattice == "D2Q9" else 3
+        for k, c in enumerate(cases):
+            cfg = cfgs[k]
+            L.lbm_config_default(ct.byref(cfg))
+            cfg.lattice = D2Q9 if D == 2 else D3Q19
+            cfg.precision = PRECISIONS[precision]
+            cfg.nx, cfg.ny = int(c["shape"][0]), int(c["shape"][1])
+            cfg.nz = int(c["shape"][2]) if D == 3 else 1
+            cfg.mach, cfg.reynolds, cfg.ref_length = c["mach"], c["reynolds"], c["ref_length"]
+            cfg.theta_inf = c.get("theta_inf", 0.0)
+            cfg.method = int(c.get("method", FODIBM_R))
+            d = c.get("inflow_dir", (1.0, 0.0, 0.0))
+            for a in range(3):
+                cfg.inflow_dir[a] = float(d[a]) if a < len(d) else 0.0
+            bc = c.get("bc", [BC_PERIODIC] * (2 * D))
+            for f in range(6):
+                cfg.bc[f] = int(bc[f]) if f < len(bc) else BC_PERIODIC
+            cfg.device = device
+        h = ct.c_void_p()
+        st = L.lbm_batch_create(n, cfgs, ct.byref(h))
+        if st:
+            raise LBMError(st, "lbm_batch_create failed")
+        self.b = h
+        self.views = []
+        for k, c in enumerate(cases):
+            hk = ct.c_void_p()
+            self._check(L.lbm_batch_case(self.b, k, ct.byref(hk)))
+            self.views.append(CaseView(hk, lattice, c["shape"]))
+
+    def _check(self, st):
+        if st:
+            raise LBMError(st, lib().lbm_batch_last_error(self.b).decode())
+
+    def case(self, k):
+        return self.views[k]
+
+    def step(self, n=1):
+        self._check(lib().lbm_batch_step(self.b, int(n)))
+
+    def step_sequential(self, n=1):
+        self._check(lib().lbm_batch_step_sequential(self.b, int(n)))
+
+    def sync(self):
+        self._check(lib().lbm_batch_sync(self.b))
+
+    def set_plan(self, tile_rows, schedule):
+        self._check(lib().lbm_batch_set_plan(self.b, int(tile_rows), int(schedule)))
+
+    def plan(self):
+        tr, sc = ct.c_int(), ct.c_int()
+        self._check(lib().lbm_batch_get_plan(self.b, ct.byref(tr), ct.byref(sc)))
+        return tr.value, sc.value
+
+    def autotune(self, steps=10, cache_path=None):
+        best = ct.c_double()
+        p = cache_path.encode() if cache_path else None
+        self._check(lib().lbm_batch_autotune(self.b, int(steps), p, ct.byref(best)))
+        return self.plan(), best.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self.views:
+                v.close()
+            lib().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
