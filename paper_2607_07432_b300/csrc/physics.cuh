@@ -350,27 +350,19 @@ __device__ __forceinline__ C third(C x) {
   }
 }
 
-// MUSCL-Hancock face value of Eq. linear at the face between cells 1 and 2
-// along the axis; phi0..phi3 are the values at cells x-1, x, x+1, x+2 and
-// u1, u2 the axial velocities of cells x and x+1.
+// MUSCL-Hancock face value of Eq. linear from the upwind stencil: B is the
+// reconstructing cell (x if u~ >= 0, else x + e), A and Cc its neighbours
+// behind and ahead along the axis, uB its axial velocity; plus selects the
+// x + e/2 face value of cell x (phi_+ branch) or the x - e/2 value of cell
+// x + e (phi_- branch).
 template <class C>
-__device__ __forceinline__ C muscl(C phi0, C phi1, C phi2, C phi3, C u1, C u2) {
-  const C ut = C(0.5) * (u1 + u2);
-  if (ut >= C(0)) {
-    const C sg = u1 > C(0) ? C(1) : (u1 < C(0) ? C(-1) : C(0));
-    const C eta = third<C>(C(2) * u1 - sg);
-    const C delta = C(0.5) * ((C(1) + eta) * (phi1 - phi0) + (C(1) - eta) * (phi2 - phi1));
-    const C pp = phi1 + C(0.5) * delta;
-    const C pm = phi1 - C(0.5) * delta;
-    return pp + C(0.5) * u1 * (pm - pp);
-  } else {
-    const C sg = u2 > C(0) ? C(1) : (u2 < C(0) ? C(-1) : C(0));
-    const C eta = third<C>(C(2) * u2 - sg);
-    const C delta = C(0.5) * ((C(1) + eta) * (phi2 - phi1) + (C(1) - eta) * (phi3 - phi2));
-    const C pp = phi2 + C(0.5) * delta;
-    const C pm = phi2 - C(0.5) * delta;
-    return pm + C(0.5) * u2 * (pm - pp);
-  }
+__device__ __forceinline__ C muscl3(C A, C B, C Cc, C uB, bool plus) {
+  const C sg = uB > C(0) ? C(1) : (uB < C(0) ? C(-1) : C(0));
+  const C eta = third<C>(C(2) * uB - sg);
+  const C delta = C(0.5) * ((C(1) + eta) * (B - A) + (C(1) - eta) * (Cc - B));
+  const C pp = B + C(0.5) * delta;
+  const C pm = B - C(0.5) * delta;
+  return (plus ? pp : pm) + C(0.5) * uB * (pm - pp);
 }
 
 // Total-energy flux F^{rhoE}_{+axis/2} through the face x + e_axis/2
@@ -410,13 +402,17 @@ __device__ __forceinline__ C energy_face_flux(const MacroAlong& MA, const FcolAt
       }
     }
   });
-  const Macro<C> m0 = MA(-1), m1 = MA(0), m2 = MA(1), m3 = MA(2);
-  const C p0 = m0.rho * cs2 * m0.th, p1 = m1.rho * cs2 * m1.th;
-  const C p2 = m2.rho * cs2 * m2.th, p3 = m3.rho * cs2 * m3.th;
-  const C u1 = m1.u[AX], u2 = m2.u[AX];
-  const C FH = muscl<C>((m0.E + p0) * m0.u[AX], (m1.E + p1) * m1.u[AX], (m2.E + p2) * m2.u[AX],
-                        (m3.E + p3) * m3.u[AX], u1, u2);
-  const C Fr = muscl<C>(m0.rho * m0.u[AX], m1.rho * m1.u[AX], m2.rho * m2.u[AX], m3.rho * m3.u[AX], u1, u2);
+  // upwind stencil of the MUSCL reconstruction: only three cells are read
+  const Macro<C> m1 = MA(0), m2 = MA(1);
+  const bool plus = C(0.5) * (m1.u[AX] + m2.u[AX]) >= C(0);
+  const Macro<C> mo = MA(plus ? -1 : 2);
+  const Macro<C>& A = plus ? mo : m1;
+  const Macro<C>& B = plus ? m1 : m2;
+  const Macro<C>& Cc = plus ? m2 : mo;
+  const C pA = A.rho * cs2 * A.th, pB = B.rho * cs2 * B.th, pC = Cc.rho * cs2 * Cc.th;
+  const C uB = B.u[AX];
+  const C FH = muscl3<C>((A.E + pA) * A.u[AX], (B.E + pB) * B.u[AX], (Cc.E + pC) * Cc.u[AX], uB, plus);
+  const C Fr = muscl3<C>(A.rho * A.u[AX], B.rho * B.u[AX], Cc.rho * Cc.u[AX], uB, plus);
   C k1 = C(0), k2 = C(0);
 #pragma unroll
   for (int b = 0; b < D; ++b) {
@@ -429,10 +425,9 @@ __device__ __forceinline__ C energy_face_flux(const MacroAlong& MA, const FcolAt
   C FE = FH + hk * (Frho - Fr);
 #pragma unroll
   for (int b = 0; b < D; ++b) {
-    const C Fb = muscl<C>(m0.rho * m0.u[AX] * m0.u[b] + (AX == b ? p0 : C(0)),
-                          m1.rho * m1.u[AX] * m1.u[b] + (AX == b ? p1 : C(0)),
-                          m2.rho * m2.u[AX] * m2.u[b] + (AX == b ? p2 : C(0)),
-                          m3.rho * m3.u[AX] * m3.u[b] + (AX == b ? p3 : C(0)), u1, u2);
+    const C Fb = muscl3<C>(A.rho * A.u[AX] * A.u[b] + (AX == b ? pA : C(0)),
+                           B.rho * B.u[AX] * B.u[b] + (AX == b ? pB : C(0)),
+                           Cc.rho * Cc.u[AX] * Cc.u[b] + (AX == b ? pC : C(0)), uB, plus);
     const C ub = C(0.5) * (m1.u[b] + m2.u[b]);
     FE = FE + ub * (Fm[b] - Fb);
   }

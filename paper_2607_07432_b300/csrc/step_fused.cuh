@@ -136,8 +136,68 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
 
   // corrected macros (rho, u, theta, rho E') of plane z over the halo-2 region,
   // from the moments rho, rho u, rho E (staged copy or global memory)
-  auto load_macros = [&](int z, bool staged) {
+  constexpr bool RPM = D == 3 && !STG && !exact && NH2 <= 2 * NT;
+  C rm[RPM ? 2 : 1][RPM ? D + 2 : 1];
+  auto prefetch_moments = [&](int z) {
+    if constexpr (RPM) {
+      const int gz = g.wrap(2, z);
+      {
+        const long long n = halo2_node(t, gz);
+#pragma unroll
+        for (int q = 0; q < D + 2; ++q) rm[0][RPM ? q : 0] = a.M_in[q * N + n];
+      }
+      if (t + NT < NH2) {
+        const long long n = halo2_node(t + NT, gz);
+#pragma unroll
+        for (int q = 0; q < D + 2; ++q) rm[RPM ? 1 : 0][RPM ? q : 0] = a.M_in[q * N + n];
+      }
+    }
+  };
+  // convert the moments rho, rho u, rho E of halo-2 node k into the corrected
+  // macros rho, u, theta, rho E' of the ring slot dst
+  auto put_macro = [&](C* dst, int k, C rho, const C* jm, C E) {
+    C u[3], uu = C(0);
+    C th;
+    if constexpr (exact) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        u[d] = jm[d] / rho;
+        uu += u[d] * u[d];
+      }
+      th = (E / rho - C(0.5) * uu) / ph.Cv;
+    } else {
+      const C ir = recip(rho);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        u[d] = jm[d] * ir;
+        uu += u[d] * u[d];
+      }
+      th = (E * ir - C(0.5) * uu) * (C(1) / ph.Cv);
+    }
+    dst[0 * NH2 + k] = rho;
+#pragma unroll
+    for (int d = 0; d < D; ++d) dst[(1 + d) * NH2 + k] = u[d];
+    dst[(1 + D) * NH2 + k] = th;
+    dst[(2 + D) * NH2 + k] = E;
+  };
+  // corrected macros of plane z over the halo-2 region, from the moments in
+  // registers (prefetched), the staged copy, or global memory
+  auto load_macros = [&](int z, bool staged, bool regs = false) {
     C* dst = mr + (size_t)mslot(z) * NMF * NH2;
+    if constexpr (RPM) {
+      if (regs) {
+        C jm[3];
+#pragma unroll
+        for (int d = 0; d < D; ++d) jm[d] = rm[0][RPM ? 1 + d : 0];
+        put_macro(dst, t, rm[0][0], jm, rm[0][RPM ? 1 + D : 0]);
+        if (t + NT < NH2) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) jm[d] = rm[1][RPM ? 1 + d : 0];
+          put_macro(dst, t + NT, rm[1][0], jm, rm[1][RPM ? 1 + D : 0]);
+        }
+        return;
+      }
+    }
     const int gz = g.wrap(2, z);
     for (int k = t; k < NH2; k += NT) {
       C rho, jm[3], E;
@@ -153,29 +213,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         for (int d = 0; d < D; ++d) jm[d] = a.M_in[(1 + d) * N + n];
         E = a.M_in[(1 + D) * N + n];
       }
-      C u[3], uu = C(0);
-      C th;
-      if constexpr (exact) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          u[d] = jm[d] / rho;
-          uu += u[d] * u[d];
-        }
-        th = (E / rho - C(0.5) * uu) / ph.Cv;
-      } else {
-        const C ir = recip(rho);
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          u[d] = jm[d] * ir;
-          uu += u[d] * u[d];
-        }
-        th = (E * ir - C(0.5) * uu) * (C(1) / ph.Cv);
-      }
-      dst[0 * NH2 + k] = rho;
-#pragma unroll
-      for (int d = 0; d < D; ++d) dst[(1 + d) * NH2 + k] = u[d];
-      dst[(1 + D) * NH2 + k] = th;
-      dst[(2 + D) * NH2 + k] = E;
+      put_macro(dst, k, rho, jm, E);
     }
   };
   // asynchronous copies of the inputs of plane zm (moments, halo 2) and of
@@ -208,8 +246,27 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     m.E = src[(2 + D) * NH2 + k];
     return m;
   };
+  // 3D FP32 with the default tile: the populations and auxiliaries of the
+  // next collision plane are loaded into registers one plane ahead, so their
+  // latency overlaps the streaming and energy stage of the current plane
+  constexpr bool RP = D == 3 && !STG && !exact && sizeof(S) == 4;
+  S rf[RP ? Q : 1];
+  C rP = C(0);
+  C rA[RP ? L::NDEV : 1];
+  unsigned char rfl = 0;
+  auto prefetch_regs = [&](int z) {
+    if constexpr (RP) {
+      const long long n = g.lin(wx, wy, g.wrap(2, z));
+#pragma unroll
+      for (int i = 0; i < Q; ++i) rf[i] = a.f_in[(long long)i * N + n];
+      rP = a.Pp[n];
+#pragma unroll
+      for (int q = 0; q < L::NDEV; ++q) rA[q] = a.Ap[q * N + n];
+      rfl = a.forced ? a.forced[n] : 0;
+    }
+  };
   // collision of this thread's node of plane z (halo-1 region, one node per thread)
-  auto collide_plane = [&](int z, bool staged) {
+  auto collide_plane = [&](int z, bool staged, bool regs) {
     C* dst = fr + (size_t)fslot(z) * Q * NH1;
     const long long n = g.lin(wx, wy, g.wrap(2, z));
     auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
@@ -219,7 +276,18 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     C fbar[Q];
     C dAFp[L::NDEV];
     C Pp;
-    if (STG && staged) {
+    bool is_forced;
+    if (RP && regs) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const C v = C(Store<S>::load(rf[RP ? i : 0]));
+        fbar[i] = Store<S>::dev ? v + C(L::w(i)) : v;
+      }
+      Pp = rP;
+#pragma unroll
+      for (int q = 0; q < L::NDEV; ++q) dAFp[q] = rA[RP ? q : 0];
+      is_forced = rfl != 0;
+    } else if (STG && staged) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const C v = C(Store<S>::load(stF[i * NH1 + t]));
@@ -228,15 +296,17 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       Pp = stA[t];
 #pragma unroll
       for (int q = 0; q < L::NDEV; ++q) dAFp[q] = stA[(1 + q) * NH1 + t];
+      is_forced = a.forced && a.forced[n];
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
       Pp = a.Pp[n];
 #pragma unroll
       for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
+      is_forced = a.forced && a.forced[n];
     }
     C fu[3] = {C(0), C(0), C(0)};
-    if (a.forced && a.forced[n]) {
+    if (is_forced) {
       const int r = find_row_dev(a.cell_id, a.n_rows, (int)n);
 #pragma unroll
       for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
@@ -270,9 +340,11 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   if constexpr (D == 3) {
     for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z, false);
     __syncthreads();
-    collide_plane(z0 - 1, false);
-    collide_plane(z0, false);
+    collide_plane(z0 - 1, false, false);
+    collide_plane(z0, false, false);
     prefetch(z0 + 2, z0 + 1);
+    prefetch_regs(z0 + 1);
+    prefetch_moments(z0 + 2);
     __syncthreads();
   }
   // the -z face of plane z is the +z face of plane z-1: carried in a register
@@ -286,15 +358,17 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     if constexpr (STG) cp_async_wait_all();
     __syncthreads();
     if constexpr (D == 3) {
-      load_macros(z + 2, true);
+      load_macros(z + 2, true, true);
       __syncthreads();
-      collide_plane(z + 1, true);
+      collide_plane(z + 1, true, true);
       __syncthreads();
       prefetch(z + 3, z + 2);
+      prefetch_regs(z + 2);
+      prefetch_moments(z + 3);
     } else {
       load_macros(0, false);
       __syncthreads();
-      collide_plane(0, false);
+      collide_plane(0, false, false);
       __syncthreads();
     }
     C rho = C(0), j[3] = {C(0), C(0), C(0)};
