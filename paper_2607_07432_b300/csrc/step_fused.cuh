@@ -65,7 +65,7 @@ struct FusedLayout {
   // resident CTAs per SM the tile is sized for
   static constexpr int min_blocks = (D == 3 && sizeof(C) == 4 && HY1 <= 8) ? 2 : 1;
   static constexpr size_t ring_bytes =
-      sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1 + 2 * (size_t)NH1);
+      sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1 + 4 * (size_t)NH1);
   static constexpr size_t stage_bytes =
       stage ? 4 * ((size_t)(D + 2) * NH2 + (size_t)(L::Q + 1 + L::NDEV) * NH1) : 0;
   static constexpr size_t bytes = ring_bytes + stage_bytes;
@@ -110,9 +110,9 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* mr = reinterpret_cast<C*>(smem_raw);        // [RM][NMF][NH2]
   C* fr = mr + (size_t)RM * NMF * NH2;           // [RF][Q][NH1]
-  C* Fx = fr + (size_t)RF * Q * NH1;             // [NH1] +x face fluxes
-  C* Fy = Fx + NH1;                              // [NH1] +y face fluxes
-  C* stM = Fy + NH1;                             // staged moments [(D+2)][NH2]
+  C* Fx = fr + (size_t)RF * Q * NH1;             // [2][NH1] +x face fluxes (plane parity)
+  C* Fy = Fx + 2 * NH1;                          // [2][NH1] +y face fluxes
+  C* stM = Fy + 2 * NH1;                         // staged moments [(D+2)][NH2]
   S* stF = reinterpret_cast<S*>(stM + (size_t)(D + 2) * NH2);  // staged populations [Q][NH1]
   C* stA = reinterpret_cast<C*>(stF + (size_t)Q * NH1);        // staged P_prev, dAF [1+NDEV][NH1]
   const int t = threadIdx.x;
@@ -354,9 +354,28 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   }
   const bool xface = cx <= TX && cy >= 1 && cy <= TY;  // +x faces of nodes cx = 0..TX
   const bool yface = cy <= TY && cx >= 1 && cx <= TX;  // +y faces of nodes cy = 0..TY
+  // energy update of plane zp, one iteration late (after the barrier that
+  // makes its face fluxes visible):
+  // rho E^{n+1} = rho E' - sum_a (F_{+a/2}(x) - F_{+a/2}(x - e_a))
+  C Fz_pend = C(0);
+  auto finish = [&](int zp) {
+    if (interior) {
+      const C* fx = Fx + (zp & 1) * NH1;
+      const C* fy = Fy + (zp & 1) * NH1;
+      C E = macro_at(zp, hx, hy).E;
+      E = E - (fx[t] - fx[t - 1]);
+      E = E - (fy[t] - fy[t - HX1]);
+      if constexpr (D == 3) {
+        E = E - (Fz_pend - Fz_prev);
+        Fz_prev = Fz_pend;
+      }
+      a.M_out[(1 + D) * N + g.lin(gx, gy, zp)] = E;
+    }
+  };
   for (int z = z0; z < z1; ++z) {
     if constexpr (STG) cp_async_wait_all();
     __syncthreads();
+    if (z > z0) finish(z - 1);
     if constexpr (D == 3) {
       load_macros(z + 2, true, true);
       __syncthreads();
@@ -387,29 +406,20 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         });
       });
     }
-    // Eq. energy face fluxes, each face once
-    if (xface) Fx[t] = face(std::integral_constant<int, 0>{}, z);
-    if (yface) Fy[t] = face(std::integral_constant<int, 1>{}, z);
-    C Fzp = C(0);
-    if constexpr (D == 3) {
-      if (interior) Fzp = face(std::integral_constant<int, 2>{}, z);
-    }
-    __syncthreads();
     if (interior) {
-      // rho E^{n+1} = rho E' - sum_a (F_{+a/2}(x) - F_{+a/2}(x - e_a))
-      C E = macro_at(z, hx, hy).E;
-      E = E - (Fx[t] - Fx[t - 1]);
-      E = E - (Fy[t] - Fy[t - HX1]);
-      if constexpr (D == 3) {
-        E = E - (Fzp - Fz_prev);
-        Fz_prev = Fzp;
-      }
       a.M_out[n] = rho;
 #pragma unroll
       for (int d = 0; d < D; ++d) a.M_out[(1 + d) * N + n] = j[d];
-      a.M_out[(1 + D) * N + n] = E;
+    }
+    // Eq. energy face fluxes, each face once
+    if (xface) Fx[(z & 1) * NH1 + t] = face(std::integral_constant<int, 0>{}, z);
+    if (yface) Fy[(z & 1) * NH1 + t] = face(std::integral_constant<int, 1>{}, z);
+    if constexpr (D == 3) {
+      if (interior) Fz_pend = face(std::integral_constant<int, 2>{}, z);
     }
   }
+  __syncthreads();
+  finish(z1 - 1);
   if constexpr (STG) cp_async_wait_all();
 }
 
