@@ -209,6 +209,48 @@ def run_batch(args):
     b.close()
 
 
+def run_warmstart(args):
+    """Learned warm start on 512x256 two-body cases (a circle and an
+    ellipse, diameters 10-40 cells, Ma 0.1-0.3, Re 20-45 so that every case
+    has a steady state): generate the training fields with the batched
+    solver, train the network on the GPU, then report steps and wall-clock
+    to the 0.1% drag band of the uniform-start answer, warm vs uniform, on
+    held-out cases.  Not a per-step throughput line: the metric is
+    time-to-steady."""
+    import torch
+    from paper_2607_07432_b300 import inputs, warmstart as ws
+    shape = (512, 256)
+    kw = dict(shape=shape, d_range=(10.0, 40.0), mach_range=(0.1, 0.3), re_range=(20.0, 45.0))
+    n_train, gen_steps, train_steps, n_test, run_steps = args.ws_cases, args.ws_gen_steps, args.ws_train_steps, 8, 40000
+    train_cases = inputs.warmstart_cases(n_train, 20260002, **kw)
+    test_cases = inputs.warmstart_cases(n_test, 20260003, **kw)
+    t0 = time.perf_counter()
+    X, Y = ws.generate(train_cases, gen_steps)
+    t_gen = time.perf_counter() - t0
+    net = ws.new_network(shape, max_batch=8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ws.train(net, X, Y, train_steps, 8, 1e-3, lr_final=1e-4)
+    t_train = time.perf_counter() - t0
+    res = [ws.compare(net, c, run_steps, 100) for c in test_cases]
+    net.close()
+    ok = [r for r in res if r["steps_uniform"] and r["steps_warm"]]
+    su = float(np.mean([r["steps_uniform"] for r in ok])) if ok else None
+    sw = float(np.mean([r["steps_warm"] for r in ok])) if ok else None
+    mu = float(np.mean([r["ms_uniform"] for r in ok])) if ok else None
+    mw = float(np.mean([r["ms_warm"] for r in ok])) if ok else None
+    line = {"metric": "steps to the 0.1% drag band, warm start vs uniform start (mean over held-out cases)",
+            "value": sw, "unit": "steps", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 solver, bf16 x bf16 -> f32 network", "data": "synthetic",
+            "config": {"workload": "2D two-body cases 512x256 (circle + ellipse, D 10-40, Ma 0.1-0.3, Re 20-45)",
+                       "train_cases": n_train, "gen_steps": gen_steps, "train_steps": train_steps, "batch": 8,
+                       "held_out": n_test},
+            "uniform_steps": su, "warm_ms": mw, "uniform_ms": mu, "step_ratio": (sw / su) if ok else None,
+            "gen_s": t_gen, "train_s": t_train, "final_loss": float(losses[-50:].mean()),
+            "cases": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,7 +259,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart"])
+    ap.add_argument("--ws-cases", type=int, default=256)
+    ap.add_argument("--ws-gen-steps", type=int, default=24000)
+    ap.add_argument("--ws-train-steps", type=int, default=2000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,6 +271,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     args.warmup = max(args.warmup, 3)
     import torch
     torch.cuda.set_device(local)

@@ -1,0 +1,492 @@
+// C ABI of the warm-start neural operator (include/nop.h): network buffers,
+// forward pass, reverse pass, Adam training step and the hand-off of a
+// predicted field to a 2D solver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nop.h"
+#include "handle.cuh"
+#include "nop_kernels.cuh"
+
+using namespace lbmib::nop;
+
+namespace {
+
+// one activation tensor: level (resolution H >> level) and channel count
+struct Tensor {
+  int level, C;
+  float* act = nullptr;   // [max_batch][H_l][W_l][C]
+  float* grad = nullptr;  // same shape
+};
+
+enum OpKind { kConv, kPool, kUp, kAdd };
+
+struct Op {
+  OpKind kind;
+  int in, in2, out;  // tensor indices (in2: second summand of kAdd)
+  int layer;         // conv layer index
+  int relu;
+};
+
+struct Layer {
+  int cin, cout;       // real channel counts
+  int cinp, coutp;     // padded to multiples of 16
+  long long offset;    // of W in the flat parameter vector (b follows W)
+  __nv_bfloat16* Wt = nullptr;
+  __nv_bfloat16* Wf = nullptr;
+  float* bias = nullptr;
+  float* dW = nullptr;  // padded weight gradient [coutp][9][cinp]
+  float* db = nullptr;  // padded bias gradient [coutp]
+  long long size() const { return (long long)cout * 9 * cin + cout; }
+};
+
+int pad16(int c) { return (c + 15) / 16 * 16; }
+
+}  // namespace
+
+struct nop_net {
+  nop_config cfg;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  std::vector<Tensor> T;
+  std::vector<Op> ops;
+  std::vector<Layer> L;
+  int x_t = 0, y_t = 0;   // input and output tensors
+  long long n_params = 0;
+  float* master = nullptr;
+  float* grad = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* part = nullptr;  // weight-gradient chunk partials
+  long long part_len = 0;
+  double* loss_part = nullptr;
+  int loss_blocks = 0;
+  double* loss_dev = nullptr;
+  double* fields = nullptr;  // rho, u (2 planes), T for nop_infer_into
+  long long adam_t = 0;
+  bool prepared = false;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+lbm_status fail(nop_net* n, lbm_status s, const std::string& what) {
+  n->err = what;
+  return s;
+}
+
+#define NCK(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(net, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+long long pixels(const nop_net* net, int level, int batch) {
+  return (long long)batch * (net->cfg.height >> level) * (net->cfg.width >> level);
+}
+
+unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+int add_tensor(nop_net* net, int level, int C) {
+  Tensor t;
+  t.level = level;
+  t.C = C;
+  net->T.push_back(t);
+  return (int)net->T.size() - 1;
+}
+
+int add_conv(nop_net* net, int in, int cin, int cout, int relu) {
+  Layer l;
+  l.cin = cin;
+  l.cout = cout;
+  l.cinp = pad16(cin);
+  l.coutp = pad16(cout);
+  l.offset = net->n_params;
+  net->n_params += l.size();
+  net->L.push_back(l);
+  const int out = add_tensor(net, net->T[in].level, l.coutp);
+  net->ops.push_back(Op{kConv, in, -1, out, (int)net->L.size() - 1, relu});
+  return out;
+}
+
+// The U-Net of include/nop.h, recorded as a list of operations.
+void build_graph(nop_net* net) {
+  const int* c = net->cfg.channels;
+  net->x_t = add_tensor(net, 0, pad16(net->cfg.in_channels));
+  int e[4];
+  int in = net->x_t, cin = net->cfg.in_channels;
+  for (int l = 0; l < 4; ++l) {
+    if (l > 0) {
+      const int p = add_tensor(net, l, net->T[e[l - 1]].C);
+      net->ops.push_back(Op{kPool, e[l - 1], -1, p, -1, 0});
+      in = p;
+      cin = c[l - 1];
+    }
+    const int a = add_conv(net, in, cin, c[l], 1);
+    e[l] = add_conv(net, a, c[l], c[l], 1);
+  }
+  int g = e[3];
+  for (int l = 2; l >= 0; --l) {
+    const int u = add_tensor(net, l, net->T[g].C);
+    net->ops.push_back(Op{kUp, g, -1, u, -1, 0});
+    const int s = add_conv(net, u, c[l + 1], c[l], 1);
+    const int t = add_tensor(net, l, c[l]);
+    net->ops.push_back(Op{kAdd, s, e[l], t, -1, 0});
+    g = add_conv(net, t, c[l], c[l], 1);
+  }
+  net->y_t = add_conv(net, g, c[0], net->cfg.out_channels, 0);
+}
+
+template <class T>
+lbm_status dalloc(nop_net* net, T** p, long long count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, (size_t)count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(net, LBM_ENOMEM, "device allocation of the network buffers failed");
+  }
+  net->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return LBM_OK;
+}
+
+lbm_status launch_check(nop_net* net, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(net, LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// BF16 copies of the master weights (after every change of the masters)
+lbm_status prepare(nop_net* net) {
+  if (net->prepared) return LBM_OK;
+  for (Layer& l : net->L) {
+    const long long n = (long long)l.coutp * 9 * l.cinp;
+    k_prep_layer<<<blocks(n), 256, 0, net->st>>>(net->master + l.offset, l.cin, l.cout, l.cinp, l.coutp, l.Wt,
+                                                 l.Wf, l.bias);
+  }
+  net->prepared = true;
+  return launch_check(net, "k_prep_layer");
+}
+
+lbm_status forward(nop_net* net, int B) {
+  lbm_status s = prepare(net);
+  if (s) return s;
+  const int H = net->cfg.height, W = net->cfg.width;
+  for (const Op& op : net->ops) {
+    const Tensor& ti = net->T[op.in];
+    const Tensor& to = net->T[op.out];
+    const int Ho = H >> to.level, Wo = W >> to.level;
+    const long long n_out = pixels(net, to.level, B) * to.C;
+    switch (op.kind) {
+      case kConv: {
+        const Layer& l = net->L[op.layer];
+        const long long P = pixels(net, to.level, B);
+        dim3 grid((unsigned)((P + kTM - 1) / kTM), (unsigned)((l.coutp + kTN - 1) / kTN));
+        k_conv3x3<<<grid, 128, 0, net->st>>>(ti.act, l.Wt, l.bias, to.act, P, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
+        break;
+      }
+      case kPool:
+        k_pool2<<<blocks(n_out), 256, 0, net->st>>>(ti.act, to.act, n_out, Ho, Wo, to.C);
+        break;
+      case kUp:
+        k_up2<<<blocks(n_out), 256, 0, net->st>>>(ti.act, to.act, n_out, Ho, Wo, to.C);
+        break;
+      case kAdd:
+        k_add<<<blocks(n_out), 256, 0, net->st>>>(ti.act, net->T[op.in2].act, to.act, n_out);
+        break;
+    }
+  }
+  return launch_check(net, "forward");
+}
+
+// Reverse pass from the (padded) output gradient already in T[y_t].grad:
+// fills every layer's dW / db and, when want_dx, T[x_t].grad.
+lbm_status backward(nop_net* net, int B, bool want_dx) {
+  const int H = net->cfg.height, W = net->cfg.width;
+  for (size_t k = 0; k < net->T.size(); ++k) {
+    if ((int)k == net->y_t) continue;
+    const Tensor& t = net->T[k];
+    NCK(cudaMemsetAsync(t.grad, 0, (size_t)pixels(net, t.level, B) * t.C * sizeof(float), net->st));
+  }
+  for (int i = (int)net->ops.size() - 1; i >= 0; --i) {
+    const Op& op = net->ops[i];
+    const Tensor& ti = net->T[op.in];
+    const Tensor& to = net->T[op.out];
+    const int Hi = H >> ti.level, Wi = W >> ti.level;
+    const long long n_in = pixels(net, ti.level, B) * ti.C;
+    switch (op.kind) {
+      case kConv: {
+        const Layer& l = net->L[op.layer];
+        const long long P = pixels(net, to.level, B);
+        if (op.relu) k_relu_mask<<<blocks(P * to.C), 256, 0, net->st>>>(to.act, to.grad, P * to.C);
+        const int nchunk = (int)((P + kWChunk - 1) / kWChunk);
+        dim3 wg((unsigned)nchunk, (unsigned)((l.coutp + 31) / 32), (unsigned)(9 * ((l.cinp + 31) / 32)));
+        k_conv3x3_wgrad<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, P, Hi, Wi, l.cinp, l.coutp);
+        const long long len = (long long)l.coutp * 9 * l.cinp;
+        k_sum_chunks<<<blocks(len), 256, 0, net->st>>>(net->part, nchunk, len, l.dW);
+        k_bias_partial<<<nchunk, l.coutp, 0, net->st>>>(to.grad, net->part, P, l.coutp);
+        k_sum_chunks<<<blocks(l.coutp), 256, 0, net->st>>>(net->part, nchunk, l.coutp, l.db);
+        if (op.in != net->x_t || want_dx) {
+          dim3 grid((unsigned)((P + kTM - 1) / kTM), (unsigned)((l.cinp + kTN - 1) / kTN));
+          k_conv3x3<<<grid, 128, 0, net->st>>>(to.grad, l.Wf, nullptr, ti.grad, P, Hi, Wi, l.coutp, l.cinp, 0, 1);
+        }
+        break;
+      }
+      case kPool:
+        k_pool2_bwd<<<blocks(n_in), 256, 0, net->st>>>(to.grad, ti.grad, n_in, Hi, Wi, ti.C);
+        break;
+      case kUp:
+        k_up2_bwd<<<blocks(n_in), 256, 0, net->st>>>(to.grad, ti.grad, n_in, Hi, Wi, ti.C);
+        break;
+      case kAdd: {
+        const long long n = pixels(net, to.level, B) * to.C;
+        k_acc<<<blocks(n), 256, 0, net->st>>>(to.grad, ti.grad, n);
+        k_acc<<<blocks(n), 256, 0, net->st>>>(to.grad, net->T[op.in2].grad, n);
+        break;
+      }
+    }
+  }
+  for (const Layer& l : net->L) {
+    const long long n = (long long)l.cout * 9 * l.cin;
+    k_unpad_grad<<<blocks(n), 256, 0, net->st>>>(l.dW, l.db, l.cin, l.cout, l.cinp, net->grad + l.offset);
+  }
+  return launch_check(net, "backward");
+}
+
+lbm_status check_batch(nop_net* net, int batch) {
+  if (batch < 1 || batch > net->cfg.max_batch) return fail(net, LBM_EINVAL, "batch outside 1..max_batch");
+  return LBM_OK;
+}
+
+lbm_status load_input(nop_net* net, int B, const float* x) {
+  const Tensor& t = net->T[net->x_t];
+  const long long P = pixels(net, 0, B);
+  k_pad_channels<<<blocks(P * t.C), 256, 0, net->st>>>(x, t.act, P, net->cfg.in_channels, t.C);
+  return launch_check(net, "k_pad_channels");
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status nop_config_default(nop_config* cfg) {
+  if (!cfg) return LBM_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->struct_size = sizeof(nop_config);
+  cfg->height = 256;
+  cfg->width = 512;
+  cfg->max_batch = 8;
+  cfg->in_channels = 3;
+  cfg->out_channels = 4;
+  cfg->channels[0] = 32;
+  cfg->channels[1] = 64;
+  cfg->channels[2] = 96;
+  cfg->channels[3] = 128;
+  return LBM_OK;
+}
+
+lbm_status nop_create(const nop_config* cfg, nop_net** out) {
+  if (!cfg || !out || cfg->struct_size != sizeof(nop_config)) return LBM_EINVAL;
+  *out = nullptr;
+  if (cfg->height < 8 || cfg->width < 8 || cfg->height % 8 || cfg->width % 8 || cfg->max_batch < 1 ||
+      cfg->in_channels < 1 || cfg->in_channels > 16 || cfg->out_channels < 1 || cfg->out_channels > 16)
+    return LBM_EINVAL;
+  for (int l = 0; l < 4; ++l)
+    if (cfg->channels[l] < 16 || cfg->channels[l] > 256 || cfg->channels[l] % 16) return LBM_EINVAL;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  nop_net* net = new nop_net();
+  net->cfg = *cfg;
+  if (cfg->stream) {
+    net->st = static_cast<cudaStream_t>(cfg->stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&net->st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete net;
+      return LBM_ECUDA;
+    }
+    net->own_stream = true;
+  }
+  build_graph(net);
+  const int B = cfg->max_batch;
+  lbm_status s = LBM_OK;
+  for (Tensor& t : net->T) {
+    const long long n = pixels(net, t.level, B) * t.C;
+    if (!s) s = dalloc(net, &t.act, n);
+    if (!s) s = dalloc(net, &t.grad, n);
+  }
+  const long long np = net->n_params;
+  if (!s) s = dalloc(net, &net->master, np);
+  if (!s) s = dalloc(net, &net->grad, np);
+  if (!s) s = dalloc(net, &net->adam_m, np);
+  if (!s) s = dalloc(net, &net->adam_v, np);
+  for (const Op& op : net->ops) {
+    if (op.kind != kConv) continue;
+    const Layer& l = net->L[op.layer];
+    const long long nchunk = (pixels(net, net->T[op.out].level, B) + kWChunk - 1) / kWChunk;
+    net->part_len = std::max(net->part_len, nchunk * ((long long)l.coutp * 9 * l.cinp + l.coutp));
+  }
+  for (Layer& l : net->L) {
+    const long long n = (long long)l.coutp * 9 * l.cinp;
+    if (!s) s = dalloc(net, &l.Wt, n);
+    if (!s) s = dalloc(net, &l.Wf, n);
+    if (!s) s = dalloc(net, &l.bias, l.coutp);
+    if (!s) s = dalloc(net, &l.dW, n);
+    if (!s) s = dalloc(net, &l.db, l.coutp);
+  }
+  if (!s) s = dalloc(net, &net->part, net->part_len);
+  net->loss_blocks = (int)blocks(pixels(net, 0, B) * net->T[net->y_t].C);
+  if (!s) s = dalloc(net, &net->loss_part, net->loss_blocks);
+  if (!s) s = dalloc(net, &net->loss_dev, 1);
+  if (!s) s = dalloc(net, &net->fields, 4 * (long long)cfg->height * cfg->width);
+  if (!s && (cudaMemsetAsync(net->master, 0, np * sizeof(float), net->st) != cudaSuccess ||
+             cudaMemsetAsync(net->adam_m, 0, np * sizeof(float), net->st) != cudaSuccess ||
+             cudaMemsetAsync(net->adam_v, 0, np * sizeof(float), net->st) != cudaSuccess ||
+             cudaStreamSynchronize(net->st) != cudaSuccess))
+    s = LBM_ECUDA;
+  if (s) {
+    nop_destroy(net);
+    return s;
+  }
+  *out = net;
+  return LBM_OK;
+}
+
+void nop_destroy(nop_net* net) {
+  if (!net) return;
+  cudaSetDevice(net->cfg.device);
+  if (net->st) cudaStreamSynchronize(net->st);
+  for (void* p : net->allocs) cudaFree(p);
+  if (net->own_stream && net->st) cudaStreamDestroy(net->st);
+  delete net;
+}
+
+const char* nop_last_error(const nop_net* net) { return net ? net->err.c_str() : "null network"; }
+
+long long nop_param_count(const nop_net* net) { return net ? net->n_params : 0; }
+
+lbm_status nop_init_params(nop_net* net, unsigned long long seed) {
+  if (!net) return LBM_EINVAL;
+  NCK(cudaSetDevice(net->cfg.device));
+  for (const Layer& l : net->L)
+    k_init_layer<<<blocks(l.size()), 256, 0, net->st>>>(net->master + l.offset, l.cin, l.cout, seed, l.offset);
+  NCK(cudaMemsetAsync(net->adam_m, 0, net->n_params * sizeof(float), net->st));
+  NCK(cudaMemsetAsync(net->adam_v, 0, net->n_params * sizeof(float), net->st));
+  net->adam_t = 0;
+  net->prepared = false;
+  NCK(cudaStreamSynchronize(net->st));
+  return launch_check(net, "k_init_layer");
+}
+
+lbm_status nop_set_params(nop_net* net, int is_device, const float* params) {
+  if (!net || !params) return LBM_EINVAL;
+  NCK(cudaSetDevice(net->cfg.device));
+  NCK(cudaMemcpyAsync(net->master, params, net->n_params * sizeof(float),
+                      is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, net->st));
+  NCK(cudaMemsetAsync(net->adam_m, 0, net->n_params * sizeof(float), net->st));
+  NCK(cudaMemsetAsync(net->adam_v, 0, net->n_params * sizeof(float), net->st));
+  net->adam_t = 0;
+  net->prepared = false;
+  NCK(cudaStreamSynchronize(net->st));
+  return LBM_OK;
+}
+
+lbm_status nop_get_params(const nop_net* cnet, int is_device, float* params) {
+  nop_net* net = const_cast<nop_net*>(cnet);
+  if (!net || !params) return LBM_EINVAL;
+  NCK(cudaSetDevice(net->cfg.device));
+  NCK(cudaMemcpyAsync(params, net->master, net->n_params * sizeof(float),
+                      is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  return LBM_OK;
+}
+
+lbm_status nop_forward(nop_net* net, int batch, const float* x, float* y) {
+  if (!net || !x || !y) return LBM_EINVAL;
+  lbm_status s = check_batch(net, batch);
+  if (s) return s;
+  NCK(cudaSetDevice(net->cfg.device));
+  if ((s = load_input(net, batch, x)) || (s = forward(net, batch))) return s;
+  const Tensor& t = net->T[net->y_t];
+  const long long P = pixels(net, 0, batch);
+  k_crop_channels<<<blocks(P * net->cfg.out_channels), 256, 0, net->st>>>(t.act, y, P, t.C, net->cfg.out_channels);
+  NCK(cudaStreamSynchronize(net->st));
+  return launch_check(net, "nop_forward");
+}
+
+lbm_status nop_backward(nop_net* net, int batch, const float* x, const float* dy, float* dparams, float* dx) {
+  if (!net || !x || !dy) return LBM_EINVAL;
+  lbm_status s = check_batch(net, batch);
+  if (s) return s;
+  NCK(cudaSetDevice(net->cfg.device));
+  if ((s = load_input(net, batch, x)) || (s = forward(net, batch))) return s;
+  const Tensor& t = net->T[net->y_t];
+  const long long P = pixels(net, 0, batch);
+  k_pad_channels<<<blocks(P * t.C), 256, 0, net->st>>>(dy, t.grad, P, net->cfg.out_channels, t.C);
+  if ((s = backward(net, batch, dx != nullptr))) return s;
+  if (dparams)
+    NCK(cudaMemcpyAsync(dparams, net->grad, net->n_params * sizeof(float), cudaMemcpyDeviceToDevice, net->st));
+  if (dx) {
+    const Tensor& tx = net->T[net->x_t];
+    k_crop_channels<<<blocks(P * net->cfg.in_channels), 256, 0, net->st>>>(tx.grad, dx, P, tx.C,
+                                                                          net->cfg.in_channels);
+  }
+  NCK(cudaStreamSynchronize(net->st));
+  return launch_check(net, "nop_backward");
+}
+
+lbm_status nop_train_step(nop_net* net, int batch, const float* x, const float* target, float lr, double* loss) {
+  if (!net || !x || !target || !(lr >= 0.f)) return LBM_EINVAL;
+  lbm_status s = check_batch(net, batch);
+  if (s) return s;
+  NCK(cudaSetDevice(net->cfg.device));
+  if ((s = load_input(net, batch, x)) || (s = forward(net, batch))) return s;
+  const Tensor& t = net->T[net->y_t];
+  const long long P = pixels(net, 0, batch);
+  const double inv_count = 1.0 / ((double)P * net->cfg.out_channels);
+  const int nb = (int)blocks(P * t.C);
+  k_mse<<<nb, 256, 0, net->st>>>(t.act, target, t.grad, net->loss_part, P, t.C, net->cfg.out_channels, inv_count);
+  k_mse_total<<<1, 1, 0, net->st>>>(net->loss_part, nb, inv_count, net->loss_dev);
+  if ((s = backward(net, batch, false))) return s;
+  net->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - std::pow(0.9, (double)net->adam_t));
+  const float c2 = (float)(1.0 - std::pow(0.999, (double)net->adam_t));
+  k_adam<<<blocks(net->n_params), 256, 0, net->st>>>(net->master, net->grad, net->adam_m, net->adam_v, net->n_params,
+                                                      lr, b1, b2, 1e-8f, c1, c2);
+  net->prepared = false;
+  double l = 0.0;
+  NCK(cudaMemcpyAsync(&l, net->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, net->st));
+  NCK(cudaStreamSynchronize(net->st));
+  if (loss) *loss = l;
+  return launch_check(net, "nop_train_step");
+}
+
+lbm_status nop_infer_into(nop_net* net, lbm_handle* h, const float* x, const double off[4], const double scale[4]) {
+  if (!net || !h || !x || !off || !scale) return LBM_EINVAL;
+  if (h->D != 2 || h->g.n[0] != net->cfg.width || h->g.n[1] != net->cfg.height || net->cfg.out_channels != 4)
+    return fail(net, LBM_EINVAL, "solver must be D2Q9 of the network's grid, network with 4 outputs");
+  NCK(cudaSetDevice(net->cfg.device));
+  lbm_status s;
+  if ((s = load_input(net, 1, x)) || (s = forward(net, 1))) return s;
+  const long long N = (long long)net->cfg.height * net->cfg.width;
+  double* rho = net->fields;
+  double* u = rho + N;
+  double* T = u + 2 * N;
+  k_to_fields<<<blocks(N), 256, 0, net->st>>>(net->T[net->y_t].act, net->T[net->y_t].C, N, off[0], off[1], off[2],
+                                              off[3], scale[0], scale[1], scale[2], scale[3], rho, u, T);
+  NCK(cudaStreamSynchronize(net->st));
+  if ((s = launch_check(net, "k_to_fields"))) return s;
+  s = lbm_set_fields(h, 1, rho, u, T);
+  if (s) return fail(net, s, "lbm_set_fields failed");
+  return LBM_OK;
+}
+
+}  // extern "C"

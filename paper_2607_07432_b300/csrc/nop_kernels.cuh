@@ -1,0 +1,501 @@
+// Kernels of the warm-start neural operator: 3x3 convolution as an implicit
+// GEMM on the tensor cores (BF16 operands, FP32 accumulation), its weight
+// gradient with deterministic split-K partials, and the elementwise pieces
+// (pooling, up-sampling, skip sums, ReLU masks, loss, Adam).
+//
+// Layout: activations and gradients NHWC FP32, pixel index
+// p = (b H + y) W + x, channels fastest.  Weights of a layer are BF16
+// Wt[c_out][tap][c_in] with tap = 3 ky + kx multiplying pixel
+// (y + ky - 1, x + kx - 1), channel counts padded to multiples of 16.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmib {
+namespace nop {
+
+constexpr int kTM = 64;    // pixels per CTA tile (forward / input gradient)
+constexpr int kTN = 32;    // output channels per CTA tile
+constexpr int kKB = 4;     // k16 blocks staged per shared-memory fill
+constexpr int kLDA = 24;   // padded row of a 16-wide k block (bank-conflict free)
+constexpr int kWChunk = 1024;  // pixels per weight-gradient partial
+constexpr int kWPix = 64;      // pixels staged per fill in the weight gradient
+constexpr int kLDW = kWPix + 8;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// D = A B + D for one m16n8k16 tile: A row-major 16x16, B column-major 16x8,
+// BF16 inputs, FP32 accumulators.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Y[p][co] (+)= sum_{tap, ci} X[p + tap][ci] Wt[co][tap][ci] (+ bias[co]),
+// optionally followed by ReLU, zero padding outside the image.  GEMM view:
+// M = pixels, N = c_out, K = 9 c_in, one k16 block = (tap, 16 channels).
+// accumulate adds the previous content of Y (used for gradient sums; every
+// element is written by exactly one thread, so the sum is deterministic).
+// Cin and Cout are multiples of 16; the input gradient of a convolution is
+// this kernel applied to the output gradient with the flipped, transposed
+// weights Wf[ci][8 - tap][co] = Wt[co][tap][ci].
+__global__ void __launch_bounds__(128) k_conv3x3(const float* __restrict__ X,
+                                                 const __nv_bfloat16* __restrict__ Wt,
+                                                 const float* __restrict__ bias, float* __restrict__ Y,
+                                                 long long P, int H, int W, int Cin, int Cout, int relu,
+                                                 int accumulate) {
+  __shared__ __align__(16) __nv_bfloat16 As[kKB][kTM][kLDA];
+  __shared__ __align__(16) __nv_bfloat16 Bs[kKB][kTN][kLDA];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const long long p0 = (long long)blockIdx.x * kTM;
+  const int n0 = blockIdx.y * kTN;
+  const int cblk = Cin >> 4;
+  const int nkb = 9 * cblk;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  // staging role for A: pixel row ar of the tile, channel half ah (8 channels)
+  const int ar = tid >> 1, ah = tid & 1;
+  const long long pa = p0 + ar;
+  const bool avalid = pa < P;
+  int ay = 0, ax = 0;
+  long long abase = 0;
+  if (avalid) {
+    const long long HW = (long long)H * W;
+    const long long b = pa / HW;
+    const int rem = (int)(pa - b * HW);
+    ay = rem / W;
+    ax = rem - ay * W;
+    abase = b * HW;
+  }
+  for (int kb0 = 0; kb0 < nkb; kb0 += kKB) {
+#pragma unroll
+    for (int k = 0; k < kKB; ++k) {
+      const int kb = kb0 + k;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = 0.f;
+      if (kb < nkb && avalid) {
+        const int tap = kb / cblk, c0 = (kb - tap * cblk) * 16 + ah * 8;
+        const int yy = ay + tap / 3 - 1, xx = ax + tap % 3 - 1;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+          const float4* src = reinterpret_cast<const float4*>(X + (abase + (long long)yy * W + xx) * Cin + c0);
+          const float4 u0 = src[0], u1 = src[1];
+          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+          v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+        }
+      }
+      uint4 pk;
+      pk.x = pack_bf16x2(v[0], v[1]);
+      pk.y = pack_bf16x2(v[2], v[3]);
+      pk.z = pack_bf16x2(v[4], v[5]);
+      pk.w = pack_bf16x2(v[6], v[7]);
+      *reinterpret_cast<uint4*>(&As[k][ar][ah * 8]) = pk;
+    }
+    for (int e = tid; e < kKB * kTN * 2; e += 128) {
+      const int k = e / (kTN * 2), r = (e >> 1) % kTN, h = e & 1;
+      const int kb = kb0 + k, co = n0 + r;
+      uint4 w = make_uint4(0u, 0u, 0u, 0u);
+      if (kb < nkb && co < Cout) {
+        const int tap = kb / cblk, c0 = (kb - tap * cblk) * 16 + h * 8;
+        w = *reinterpret_cast<const uint4*>(Wt + ((long long)co * 9 + tap) * Cin + c0);
+      }
+      *reinterpret_cast<uint4*>(&Bs[k][r][h * 8]) = w;
+    }
+    __syncthreads();
+    const int m = warp * 16;
+#pragma unroll
+    for (int k = 0; k < kKB; ++k) {
+      if (kb0 + k < nkb) {
+        const uint32_t a0 = lds32(&As[k][m + g][2 * tq]);
+        const uint32_t a1 = lds32(&As[k][m + g + 8][2 * tq]);
+        const uint32_t a2 = lds32(&As[k][m + g][2 * tq + 8]);
+        const uint32_t a3 = lds32(&As[k][m + g + 8][2 * tq + 8]);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const uint32_t b0 = lds32(&Bs[k][nt * 8 + g][2 * tq]);
+          const uint32_t b1 = lds32(&Bs[k][nt * 8 + g][2 * tq + 8]);
+          mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int co = n0 + nt * 8 + 2 * tq;
+    if (co >= Cout) continue;
+    const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const long long p = p0 + warp * 16 + g + hr * 8;
+      if (p >= P) continue;
+      float v0 = acc[nt][2 * hr] + b0, v1 = acc[nt][2 * hr + 1] + b1;
+      if (relu) {
+        v0 = v0 > 0.f ? v0 : 0.f;
+        v1 = v1 > 0.f ? v1 : 0.f;
+      }
+      float2* dst = reinterpret_cast<float2*>(Y + p * Cout + co);
+      if (accumulate) {
+        const float2 o = *dst;
+        v0 = o.x + v0;
+        v1 = o.y + v1;
+      }
+      *dst = make_float2(v0, v1);
+    }
+  }
+}
+
+// Weight-gradient partials of one pixel chunk:
+// part[chunk][co][tap][ci] = sum_{p in chunk} G[p][co] X[p + tap][ci].
+// GEMM view: M = c_out (tile 32), N = 16-channel blocks of one tap (tile
+// 32 channels), K = pixels of the chunk.  grid = (chunks, Cout/32,
+// 9 ceil(Cin/32)).  The chunk partials are added in chunk order by
+// k_sum_chunks.
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad(const float* __restrict__ G,
+                                                       const float* __restrict__ X,
+                                                       float* __restrict__ part, long long P, int H,
+                                                       int W, int Cin, int Cout) {
+  __shared__ __align__(16) __nv_bfloat16 As[32][kLDW];  // [co][pixel]
+  __shared__ __align__(16) __nv_bfloat16 Bs[32][kLDW];  // [ci][pixel]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int chunk = blockIdx.x;
+  const int m0 = blockIdx.y * 32;
+  const int cib = (Cin + 31) / 32;
+  const int tap = blockIdx.z / cib;
+  const int c00 = (blockIdx.z - tap * cib) * 32;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int wm = warp & 1, wn = warp >> 1;
+  float acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  const long long HW = (long long)H * W;
+  const long long pbeg = (long long)chunk * kWChunk;
+  const int r = tid >> 1, h = tid & 1;  // staging: pixel r, channel half h (16 channels)
+  for (int s = 0; s < kWChunk; s += kWPix) {
+    const long long p = pbeg + s + r;
+    float ga[16], xb[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) ga[j] = xb[j] = 0.f;
+    if (p < P) {
+      const int co0 = m0 + h * 16;
+      if (co0 < Cout) {
+        const float4* src = reinterpret_cast<const float4*>(G + p * Cout + co0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 u = src[q];
+          ga[4 * q] = u.x; ga[4 * q + 1] = u.y; ga[4 * q + 2] = u.z; ga[4 * q + 3] = u.w;
+        }
+      }
+      const long long b = p / HW;
+      const int rem = (int)(p - b * HW);
+      const int y = rem / W, x = rem - (rem / W) * W;
+      const int yy = y + dy, xx = x + dx;
+      const int ci0 = c00 + h * 16;
+      if (ci0 < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W) {
+        const float4* src = reinterpret_cast<const float4*>(X + (b * HW + (long long)yy * W + xx) * Cin + ci0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 u = src[q];
+          xb[4 * q] = u.x; xb[4 * q + 1] = u.y; xb[4 * q + 2] = u.z; xb[4 * q + 3] = u.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      As[h * 16 + j][r] = __float2bfloat16_rn(ga[j]);
+      Bs[h * 16 + j][r] = __float2bfloat16_rn(xb[j]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kWPix / 16; ++kk) {
+      const int kc = kk * 16 + 2 * tq;
+      const uint32_t a0 = lds32(&As[wm * 16 + g][kc]);
+      const uint32_t a1 = lds32(&As[wm * 16 + g + 8][kc]);
+      const uint32_t a2 = lds32(&As[wm * 16 + g][kc + 8]);
+      const uint32_t a3 = lds32(&As[wm * 16 + g + 8][kc + 8]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int n = wn * 16 + nt * 8 + g;
+        mma_bf16(acc[nt], a0, a1, a2, a3, lds32(&Bs[n][kc]), lds32(&Bs[n][kc + 8]));
+      }
+    }
+    __syncthreads();
+  }
+  float* out = part + (long long)chunk * Cout * 9 * Cin;
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    const int ci = c00 + wn * 16 + nt * 8 + 2 * tq;
+    if (ci >= Cin) continue;
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int co = m0 + wm * 16 + g + hr * 8;
+      if (co >= Cout) continue;
+      *reinterpret_cast<float2*>(out + ((long long)co * 9 + tap) * Cin + ci) =
+          make_float2(acc[nt][2 * hr], acc[nt][2 * hr + 1]);
+    }
+  }
+}
+
+// Bias-gradient partials: part[chunk][co] = sum_{p in chunk} G[p][co], pixels
+// in order.  grid = chunks, block = Cout threads.
+__global__ void k_bias_partial(const float* __restrict__ G, float* __restrict__ part, long long P, int Cout) {
+  const int co = threadIdx.x;
+  const long long pbeg = (long long)blockIdx.x * kWChunk;
+  const long long pend = pbeg + kWChunk < P ? pbeg + kWChunk : P;
+  float s = 0.f;
+  for (long long p = pbeg; p < pend; ++p) s += G[p * Cout + co];
+  part[(long long)blockIdx.x * Cout + co] = s;
+}
+
+// out[j] = sum_{c = 0..n-1} part[c][j] in chunk order (deterministic).
+__global__ void k_sum_chunks(const float* __restrict__ part, int n, long long len, float* __restrict__ out) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  float s = 0.f;
+  for (int c = 0; c < n; ++c) s += part[(long long)c * len + j];
+  out[j] = s;
+}
+
+}  // namespace nop
+}  // namespace lbmib
+
+namespace lbmib {
+namespace nop {
+
+// 2x2 average pooling: out (H/2 x W/2) = mean of the four children, summed
+// in the order (2y,2x), (2y,2x+1), (2y+1,2x), (2y+1,2x+1).
+__global__ void k_pool2(const float* __restrict__ in, float* __restrict__ out, long long n_out, int Ho, int Wo,
+                        int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const int c = (int)(i % C);
+  const long long q = i / C;
+  const int x = (int)(q % Wo);
+  const long long r = q / Wo;
+  const int y = (int)(r % Ho);
+  const long long b = r / Ho;
+  const int Wi = 2 * Wo;
+  const long long base = ((b * 2 * Ho + 2 * y) * Wi + 2 * x) * C + c;
+  const float s = ((in[base] + in[base + C]) + in[base + (long long)Wi * C]) + in[base + (long long)Wi * C + C];
+  out[i] = 0.25f * s;
+}
+
+// adjoint of k_pool2, accumulated: din(y, x) += dout(y/2, x/2) / 4
+__global__ void k_pool2_bwd(const float* __restrict__ dout, float* __restrict__ din, long long n_in, int Hi,
+                            int Wi, int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_in) return;
+  const int c = (int)(i % C);
+  const long long q = i / C;
+  const int x = (int)(q % Wi);
+  const long long r = q / Wi;
+  const int y = (int)(r % Hi);
+  const long long b = r / Hi;
+  din[i] += 0.25f * dout[((b * (Hi / 2) + y / 2) * (Wi / 2) + x / 2) * C + c];
+}
+
+// nearest-neighbour x2 up-sampling: out(y, x) = in(y/2, x/2)
+__global__ void k_up2(const float* __restrict__ in, float* __restrict__ out, long long n_out, int Ho, int Wo,
+                      int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const int c = (int)(i % C);
+  const long long q = i / C;
+  const int x = (int)(q % Wo);
+  const long long r = q / Wo;
+  const int y = (int)(r % Ho);
+  const long long b = r / Ho;
+  out[i] = in[((b * (Ho / 2) + y / 2) * (Wo / 2) + x / 2) * C + c];
+}
+
+// adjoint of k_up2, accumulated: din(y, x) += sum of the four children
+__global__ void k_up2_bwd(const float* __restrict__ dout, float* __restrict__ din, long long n_in, int Hi,
+                          int Wi, int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_in) return;
+  const int c = (int)(i % C);
+  const long long q = i / C;
+  const int x = (int)(q % Wi);
+  const long long r = q / Wi;
+  const int y = (int)(r % Hi);
+  const long long b = r / Hi;
+  const int Wo = 2 * Wi;
+  const long long base = ((b * 2 * Hi + 2 * y) * Wo + 2 * x) * C + c;
+  const float s = ((dout[base] + dout[base + C]) + dout[base + (long long)Wo * C]) + dout[base + (long long)Wo * C + C];
+  din[i] += s;
+}
+
+// out = a + b
+__global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out,
+                      long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + b[i];
+}
+
+// dst += src
+__global__ void k_acc(const float* __restrict__ src, float* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] += src[i];
+}
+
+// ReLU backward in place: g = g if y > 0 else 0 (y is the activation output)
+__global__ void k_relu_mask(const float* __restrict__ y, float* __restrict__ g, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !(y[i] > 0.f)) g[i] = 0.f;
+}
+
+// channel padding: dst[p][c] = c < Cs ? src[p][c] : 0 (Cd >= Cs)
+__global__ void k_pad_channels(const float* __restrict__ src, float* __restrict__ dst, long long P, int Cs,
+                               int Cd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * Cd) return;
+  const int c = (int)(i % Cd);
+  const long long p = i / Cd;
+  dst[i] = c < Cs ? src[p * Cs + c] : 0.f;
+}
+
+// channel cropping: dst[p][c] = src[p][c] for c < Cd (Cs >= Cd)
+__global__ void k_crop_channels(const float* __restrict__ src, float* __restrict__ dst, long long P, int Cs,
+                                int Cd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * Cd) return;
+  const int c = (int)(i % Cd);
+  const long long p = i / Cd;
+  dst[i] = src[p * Cs + c];
+}
+
+// Mean-squared error over the first Cr of Cp channels: per-block partial
+// sums of (y - t)^2 (fixed tree order) and the output gradient
+// dy = 2 (y - t) / count (zero in the padding channels).
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ dy,
+                      double* __restrict__ part, long long P, int Cp, int Cr, double inv_count) {
+  __shared__ double red[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e2 = 0.0;
+  if (i < P * Cp) {
+    const int c = (int)(i % Cp);
+    const long long p = i / Cp;
+    float d = 0.f;
+    if (c < Cr) {
+      d = y[i] - t[p * Cr + c];
+      e2 = (double)d * (double)d;
+    }
+    dy[i] = (float)(2.0 * inv_count) * d;
+  }
+  red[threadIdx.x] = e2;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// loss = inv_count * sum_b part[b], blocks in order (one thread)
+__global__ void k_mse_total(const double* __restrict__ part, int n, double inv_count, double* __restrict__ out) {
+  double s = 0.0;
+  for (int b = 0; b < n; ++b) s += part[b];
+  *out = s * inv_count;
+}
+
+// Adam with bias correction on the FP32 master weights.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Master FP32 layer (W[co][tap][ci] real sizes, then b[co]) -> padded BF16
+// forward weights Wt[co][tap][ci], flipped transposed weights
+// Wf[ci][8 - tap][co] for the input gradient, and the padded FP32 bias.
+__global__ void k_prep_layer(const float* __restrict__ master, int cin, int cout, int cinp, int coutp,
+                             __nv_bfloat16* __restrict__ Wt, __nv_bfloat16* __restrict__ Wf,
+                             float* __restrict__ bias) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)coutp * 9 * cinp;
+  if (i < coutp) bias[i] = i < cout ? master[(long long)cout * 9 * cin + i] : 0.f;
+  if (i >= n) return;
+  const int ci = (int)(i % cinp);
+  const long long q = i / cinp;
+  const int tap = (int)(q % 9);
+  const int co = (int)(q / 9);
+  const float w = (co < cout && ci < cin) ? master[((long long)co * 9 + tap) * cin + ci] : 0.f;
+  const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+  Wt[i] = wb;
+  Wf[((long long)ci * 9 + (8 - tap)) * coutp + co] = wb;
+}
+
+// Padded weight / bias gradients -> the master layout of the layer.
+__global__ void k_unpad_grad(const float* __restrict__ dW, const float* __restrict__ db, int cin, int cout,
+                             int cinp, float* __restrict__ grad) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)cout * 9 * cin;
+  if (i < cout) grad[n + i] = db[i];
+  if (i >= n) return;
+  const int ci = (int)(i % cin);
+  const long long q = i / cin;
+  const int tap = (int)(q % 9);
+  const int co = (int)(q / 9);
+  grad[i] = dW[((long long)co * 9 + tap) * cinp + ci];
+}
+
+// He-uniform initialisation from splitmix64(seed, index): weights uniform in
+// [-a, a] with a = sqrt(6 / (9 cin)), biases zero.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_init_layer(float* __restrict__ master, int cin, int cout, unsigned long long seed,
+                             long long offset) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nw = (long long)cout * 9 * cin;
+  if (i >= nw + cout) return;
+  if (i >= nw) {
+    master[i] = 0.f;
+    return;
+  }
+  const unsigned long long r = splitmix64(seed ^ splitmix64((unsigned long long)(offset + i)));
+  const float u = (float)(r >> 40) * (1.0f / 16777216.0f);
+  const float a = sqrtf(6.0f / (9.0f * (float)cin));
+  master[i] = (2.f * u - 1.f) * a;
+}
+
+// Network output (NHWC, Cp channels, first four used) -> solver fields in
+// the solver's layout (x fastest): rho, u (two planes), T as doubles.
+__global__ void k_to_fields(const float* __restrict__ y, int Cp, long long N, double o0, double o1, double o2,
+                            double o3, double s0, double s1, double s2, double s3, double* __restrict__ rho,
+                            double* __restrict__ u, double* __restrict__ T) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const float* q = y + p * Cp;
+  rho[p] = o0 + s0 * (double)q[0];
+  u[p] = o1 + s1 * (double)q[1];
+  u[N + p] = o2 + s2 * (double)q[2];
+  T[p] = o3 + s3 * (double)q[3];
+}
+
+}  // namespace nop
+}  // namespace lbmib

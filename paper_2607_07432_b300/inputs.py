@@ -143,3 +143,80 @@ def random_state(lattice_q, shape_zyx, seed, amp=1e-3):
     """Small seeded perturbation field (for parity of a single step)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return amp * rng.standard_normal((lattice_q,) + tuple(shape_zyx))
+
+
+def warmstart_cases(n_cases, seed, shape=(512, 256), d_range=(10.0, 60.0), mach_range=(0.1, 0.45),
+                    re_range=(20.0, 200.0)):
+    """Seeded two-body 2D cases for the warm-start network: one circle and
+    one ellipse (aspect 1-3, random orientation), diameters (major axis for
+    the ellipse) uniform in d_range, both centres in the upstream half of
+    the grid and at least 10 cells apart surface to surface (bounding
+    circles), so that the interpolation and spreading stencils of one body
+    never reach the other; ellipse minor semi-axis at least 3 cells; Mach
+    and Re uniform in their ranges, Re on the larger diameter."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny = shape
+    out = []
+    while len(out) < n_cases:
+        dc = rng.uniform(*d_range)
+        de = rng.uniform(*d_range)
+        aspect = rng.uniform(1.0, 3.0)
+        ang = rng.uniform(0.0, np.pi)
+        lo_x, hi_x = 0.15 * nx, 0.5 * nx
+        pc = np.array([rng.uniform(lo_x, hi_x), rng.uniform(0.25 * ny, 0.75 * ny)])
+        pe = np.array([rng.uniform(lo_x, hi_x), rng.uniform(0.25 * ny, 0.75 * ny)])
+        if np.hypot(*(pc - pe)) < 0.5 * (dc + de) + 10.0 or 0.5 * de / aspect < 3.0:
+            continue
+        if min(pc[1], pe[1]) - 0.5 * max(dc, de) < 6 or max(pc[1], pe[1]) + 0.5 * max(dc, de) > ny - 6:
+            continue
+        out.append(dict(shape=(nx, ny), circle=dict(center=(float(pc[0]), float(pc[1])), diameter=dc),
+                        ellipse=dict(center=(float(pe[0]), float(pe[1])), a=0.5 * de, b=0.5 * de / aspect,
+                                     angle=ang),
+                        mach=rng.uniform(*mach_range), reynolds=rng.uniform(*re_range),
+                        ref_length=max(dc, de)))
+    return out
+
+
+def two_body_geometry(case, t_value, spacing=1.0):
+    """Lagrangian points of both bodies (about one point per cell of
+    perimeter), their outward normals, and the inside mask of the union
+    (strict interiors) in the solver layout [ny][nx]."""
+    nx, ny = case["shape"]
+    c, e = case["circle"], case["ellipse"]
+    nc = max(16, int(round(np.pi * c["diameter"] / spacing)))
+    a, b = e["a"], e["b"]
+    per = np.pi * (3 * (a + b) - np.sqrt((3 * a + b) * (a + 3 * b)))
+    ne = max(16, int(round(per / spacing)))
+    g1 = cylinder(c["center"], c["diameter"], nc, tbc=0, t_value=t_value)
+    g2 = ellipse(e["center"], a, b, e["angle"], ne, tbc=0, t_value=t_value)
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r = 0.5 * c["diameter"]
+    inside = (xx - c["center"][0]) ** 2 + (yy - c["center"][1]) ** 2 < r * r
+    cs, sn = math.cos(e["angle"]), math.sin(e["angle"])
+    dx, dy = xx - e["center"][0], yy - e["center"][1]
+    xr, yr = cs * dx + sn * dy, -sn * dx + cs * dy
+    inside |= (xr / a) ** 2 + (yr / b) ** 2 < 1.0
+    geo = dict(X=np.concatenate([g1["X"], g2["X"]]), normals=np.concatenate([g1["normals"], g2["normals"]]),
+               shape=dict(kind="mask", mask=inside.astype(np.uint8)),
+               tbc=np.concatenate([g1["tbc"], g2["tbc"]]), t_value=np.concatenate([g1["t_value"], g2["t_value"]]),
+               u_target=np.zeros((nc + ne, 2)))
+    return geo
+
+
+def signed_distance(case):
+    """Signed distance to the nearer body surface, negative inside, in cells
+    ([ny][nx]); exact for the circle, for the ellipse the distance to its
+    surface measured along the ray from its centre (an approximation that is
+    exact on the axes)."""
+    nx, ny = case["shape"]
+    c, e = case["circle"], case["ellipse"]
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    d1 = np.hypot(xx - c["center"][0], yy - c["center"][1]) - 0.5 * c["diameter"]
+    cs, sn = math.cos(e["angle"]), math.sin(e["angle"])
+    dx, dy = xx - e["center"][0], yy - e["center"][1]
+    xr, yr = cs * dx + sn * dy, -sn * dx + cs * dy
+    rho = np.hypot(xr, yr)
+    k = np.hypot(xr / e["a"], yr / e["b"])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        d2 = np.where(k > 0, rho * (1.0 - 1.0 / k), -min(e["a"], e["b"]))
+    return np.minimum(d1, d2)
