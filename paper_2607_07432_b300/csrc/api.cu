@@ -172,6 +172,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     if (zc) h->zchunk = std::max(1, std::atoi(zc));
     const char* tr = std::getenv("LBMIB_TILE_ROWS");
     if (tr) h->tile_rows = std::atoi(tr);
+    const char* bk = std::getenv("LBMIB_BC_SEPARATE");
+    if (bk && bk[0] == '1') h->bc_in_kernel = 0;
   }
   alloc(&h->f, N * h->Q * h->ssize);
   if (h->use_fused) {

@@ -149,9 +149,10 @@ struct Engine {
   static lbm_status bc_fused(lbm_handle* h) {
     BCFaces bf;
     int maxplane = 0;
+    const int skip_x = bc_in_kernel(h) ? 1 : 0;
     for (int face = 0; face < 6; ++face) {
       bf.type[face] = face < 2 * L::D ? h->cfg.bc[face] : 0;
-      if (face < 2 * L::D && bf.type[face]) {
+      if (face < 2 * L::D && bf.type[face] && !(skip_x && face < 2)) {
         FacePlane fp{face / 2, face % 2};
         maxplane = std::max(maxplane, fp.count(h->g));
       }
@@ -159,7 +160,7 @@ struct Engine {
     if (!maxplane) return LBM_OK;
     return launch(h, kProfBC, [&] {
       k_bc_all_m<L, S, C><<<dim3(nblk(maxplane, 128), 2 * L::D), 128, 0, h->st>>>(
-          h->g, (S*)h->f, (C*)h->M, bf, (const C*)h->feq_inf, C(h->E_inf));
+          h->g, (S*)h->f, (C*)h->M, bf, (const C*)h->feq_inf, C(h->E_inf), skip_x);
     });
   }
   // fused form: predicted moments from the populations and rho E
@@ -195,7 +196,24 @@ struct Engine {
     a.cell_id = h->cell_id;
     a.n_rows = h->n_rows;
     a.FU = h->FU;
+    a.bc_fused = bc_in_kernel(h) ? 1 : 0;
+    a.bct[0] = h->cfg.bc[0];
+    a.bct[1] = h->cfg.bc[1];
+    a.feq_inf = (const C*)h->feq_inf;
+    a.E_inf = C(h->E_inf);
     return a;
+  }
+  // x faces inside the fused kernel: both x faces non-periodic, at least
+  // four nodes along x, an x+ outlet node in the same tile as its inner
+  // neighbour, and no outlet face on y or z (whose copies would read x-face
+  // nodes before the kernel's equilibrium wins on the edges)
+  static bool bc_in_kernel(lbm_handle* h) {
+    if (!h->use_fused || !h->bc_in_kernel || h->g.n[0] < 4) return false;
+    if (h->cfg.bc[0] == LBM_BC_PERIODIC || h->cfg.bc[1] == LBM_BC_PERIODIC) return false;
+    if (h->cfg.bc[1] == LBM_BC_OUTLET && (h->g.n[0] - 1) % FusedTile<L, C>::TX == 0) return false;
+    for (int f = 2; f < 2 * L::D; ++f)
+      if (h->cfg.bc[f] == LBM_BC_OUTLET) return false;
+    return true;
   }
   template <int HY>
   static void batch_tiles(lbm_handle* h, int& tx, int& ty, int& tz) {
@@ -358,19 +376,7 @@ struct Engine {
 
 template <class L, class S, class C>
 inline lbm_status Engine<L, S, C>::fused_step(lbm_handle* h, const Phys<C>& ph) {
-  FusedArgs<S, C> a;
-  a.f_in = (const S*)h->f;
-  a.f_out = (S*)h->f2;
-  a.M_in = (const C*)h->M;
-  a.M_out = (C*)h->M2;
-  a.Pp = (const C*)h->P[h->cur];
-  a.Pn = (C*)h->P[1 - h->cur];
-  a.Ap = (const C*)h->A[h->cur];
-  a.An = (C*)h->A[1 - h->cur];
-  a.forced = h->has_ib ? h->forced : nullptr;
-  a.cell_id = h->cell_id;
-  a.n_rows = h->n_rows;
-  a.FU = h->FU;
+  const FusedArgs<S, C> a = fused_args(h, 0);
   lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st, h->zchunk, h->tile_rows); });
   if (s) return s;
   std::swap(h->f, h->f2);

@@ -39,6 +39,7 @@ struct lbm_handle {
   int cur = 0;
   int use_fused = 1;         // fused shared-memory step (0: unfused global-memory form)
   int zchunk = 16;           // planes per CTA along z in the fused step
+  int bc_in_kernel = 1;  // far-field boundaries inside the fused kernel when the faces allow it
   int tile_rows = 0;         // tile height of the 3D FP32 fused step (0 = default)
   void* f2 = nullptr;        // second population buffer (fused form)
   void* M2 = nullptr;        // second predicted-moment buffer (fused form)
@@ -139,6 +140,7 @@ struct Ops {
 struct BatchPlan {
   std::vector<lbm_handle*> cases;
   cudaStream_t st = nullptr;
+  int bc_in_kernel = 1;  // far-field boundaries inside the fused kernel when the faces allow it
   int tile_rows = 0;   // 0: the default tile of the lattice / precision
   int schedule = 0;    // 0 case-major, 1 round-robin over cases, 2 largest case first
   void* descs[2] = {nullptr, nullptr};   // device CaseDesc arrays, parity 0 / 1

@@ -37,6 +37,17 @@ struct FusedArgs {
   const int* cell_id;  // n_rows, ascending
   int n_rows;
   const double* FU;    // n_rows*D
+  // The two x faces applied in the kernel (bc_fused != 0; their nodes are
+  // one per grid row, so a separate kernel would touch a 32-byte sector per
+  // value): a node on an inlet / far-field x face stores the free-stream
+  // equilibrium and E_inf; a node on an outlet x face stores what its inner
+  // neighbour stores (zero gradient), computed by the same operations from
+  // the neighbour's data in shared memory.  The y and z faces, and
+  // equilibrium on shared edges, follow in the boundary kernel.
+  int bc_fused;
+  int bct[2];          // LBM_BC_* of the x- and x+ faces
+  const C* feq_inf;    // Q free-stream equilibrium populations
+  C E_inf;
 };
 
 // Tile: one thread per node of the halo-1 region HX1 x HY1 (the collision
@@ -326,13 +337,28 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     }
   };
   auto fcol_at = [&](int i, int z, int kx, int ky) { return fr[((size_t)fslot(z) * Q + i) * NH1 + ky * HX1 + kx]; };
-  // energy flux through the + face (axis AX) of this thread's node of plane bz
-  auto face = [&](auto AXc, int bz) {
+  // x-face role of this thread's node: xeq = equilibrium face node; xs = -1
+  // / +1 = outlet face node that takes the values of its inner neighbour
+  // at x + xs (same tile: the host checks the tile alignment)
+  bool xeq = false;
+  int xs = 0;
+  if (a.bc_fused) {
+    const bool lo = gx == 0, hi = gx == g.n[0] - 1;
+    const int t0 = a.bct[0], t1 = a.bct[1];
+    xeq = (lo && (t0 == 1 || t0 == 3)) || (hi && (t1 == 1 || t1 == 3));
+    if (lo && t0 == 2) xs = 1;
+    if (hi && t1 == 2) xs = -1;
+  }
+  const int sx = cx + xs;  // the node whose stream, faces and energy this thread computes
+  const int st = t + xs;
+  // energy flux through the + face (axis AX) of plane bz of the node at
+  // x offset sh from this thread's node
+  auto face = [&](auto AXc, int bz, int sh) {
     constexpr int AX = decltype(AXc)::value;
     auto MAl = [&](int k) {
-      return macro_at(bz + (AX == 2 ? k : 0), hx + (AX == 0 ? k : 0), hy + (AX == 1 ? k : 0));
+      return macro_at(bz + (AX == 2 ? k : 0), hx + sh + (AX == 0 ? k : 0), hy + (AX == 1 ? k : 0));
     };
-    auto FCl = [&](int i, int dx, int dy, int dz) { return fcol_at(i, bz + dz, cx + dx, cy + dy); };
+    auto FCl = [&](int i, int dx, int dy, int dz) { return fcol_at(i, bz + dz, cx + sh + dx, cy + dy); };
     return energy_face_flux<L, C, AX>(MAl, FCl, ph);
   };
 
@@ -350,7 +376,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   // the -z face of plane z is the +z face of plane z-1: carried in a register
   C Fz_prev = C(0);
   if constexpr (D == 3) {
-    if (interior) Fz_prev = face(std::integral_constant<int, 2>{}, z0 - 1);
+    if (interior) Fz_prev = face(std::integral_constant<int, 2>{}, z0 - 1, xs);
   }
   const bool xface = cx <= TX && cy >= 1 && cy <= TY;  // +x faces of nodes cx = 0..TX
   const bool yface = cy <= TY && cx >= 1 && cx <= TX;  // +y faces of nodes cy = 0..TY
@@ -362,13 +388,14 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     if (interior) {
       const C* fx = Fx + (zp & 1) * NH1;
       const C* fy = Fy + (zp & 1) * NH1;
-      C E = macro_at(zp, hx, hy).E;
-      E = E - (fx[t] - fx[t - 1]);
-      E = E - (fy[t] - fy[t - HX1]);
+      C E = macro_at(zp, hx + xs, hy).E;
+      E = E - (fx[st] - fx[st - 1]);
+      E = E - (fy[st] - fy[st - HX1]);
       if constexpr (D == 3) {
         E = E - (Fz_pend - Fz_prev);
         Fz_prev = Fz_pend;
       }
+      if (xeq) E = a.E_inf;
       a.M_out[(1 + D) * N + g.lin(gx, gy, zp)] = E;
     }
   };
@@ -397,7 +424,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       // Eq. LB pull streaming and the predicted moments of step n+1
       sfor<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const C v = fcol_at(i, z - L::c(i, 2), cx - L::c(i, 0), cy - L::c(i, 1));
+        const C v = fcol_at(i, z - L::c(i, 2), sx - L::c(i, 0), cy - L::c(i, 1));
         store_pop<L, S, C>(a.f_out, i, N, n, v);
         rho += v;
         sfor<0, D>([&](auto A) {
@@ -405,6 +432,21 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
           if constexpr (L::c(i, d) != 0) j[d] += C(L::c(i, d)) * v;
         });
       });
+      if (xeq) {
+        // free-stream equilibrium and its moments, as stored
+        rho = C(0);
+        j[0] = j[1] = j[2] = C(0);
+        sfor<0, Q>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          store_pop<L, S, C>(a.f_out, i, N, n, a.feq_inf[i]);
+          const C v = roundtrip_pop<L, S, C>(i, a.feq_inf[i]);
+          rho += v;
+          sfor<0, D>([&](auto A) {
+            constexpr int d = decltype(A)::value;
+            if constexpr (L::c(i, d) != 0) j[d] += C(L::c(i, d)) * v;
+          });
+        });
+      }
     }
     if (interior) {
       a.M_out[n] = rho;
@@ -412,10 +454,10 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       for (int d = 0; d < D; ++d) a.M_out[(1 + d) * N + n] = j[d];
     }
     // Eq. energy face fluxes, each face once
-    if (xface) Fx[(z & 1) * NH1 + t] = face(std::integral_constant<int, 0>{}, z);
-    if (yface) Fy[(z & 1) * NH1 + t] = face(std::integral_constant<int, 1>{}, z);
+    if (xface) Fx[(z & 1) * NH1 + t] = face(std::integral_constant<int, 0>{}, z, 0);
+    if (yface) Fy[(z & 1) * NH1 + t] = face(std::integral_constant<int, 1>{}, z, 0);
     if constexpr (D == 3) {
-      if (interior) Fz_pend = face(std::integral_constant<int, 2>{}, z);
+      if (interior) Fz_pend = face(std::integral_constant<int, 2>{}, z, xs);
     }
   }
   __syncthreads();
@@ -563,12 +605,12 @@ struct BCFaces {
 };
 
 template <class L, class S, class C>
-__global__ void k_bc_all_m(Grid g, S* f, C* M, BCFaces bf, const C* feq_inf, C E_inf) {
+__global__ void k_bc_all_m(Grid g, S* f, C* M, BCFaces bf, const C* feq_inf, C E_inf, int skip_x) {
   constexpr int D = L::D;
   const int face = blockIdx.y;
   const int axis = face / 2, side = face % 2;
   const int ft = bf.type[face];
-  if (ft == 0) return;
+  if (ft == 0 || (skip_x && axis == 0)) return;
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.n[a1] * g.n[a2]) return;

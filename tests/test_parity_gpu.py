@@ -114,3 +114,29 @@ def test_determinism():
     fa, Ea = a.state()
     fb, Eb = b.state()
     assert np.array_equal(fa, fb) and np.array_equal(Ea, Eb)
+
+
+@pytest.mark.parametrize("lattice,precision", [("D2Q9", "fp32"), ("D3Q19", "fp32"), ("D3Q19", "fp64")])
+def test_boundaries_in_kernel_match_separate_kernel(lattice, precision, monkeypatch):
+    """The fused kernel's in-place far-field faces (equilibrium on inlet and
+    far-field faces, the outlet written as a copy by its inner neighbour)
+    equal the separate boundary kernel bit for bit."""
+    from paper_2607_07432_b300 import inputs, lbmib
+    if lattice == "D2Q9":
+        case = C.cylinder_c1()
+    else:
+        case = dict(lattice="D3Q19", shape=(40, 24, 24), mach=0.3, reynolds=100.0, ref_length=8.0,
+                    bc=[C.BC_IN, C.BC_OUT, C.BC_FF, C.BC_FF, C.BC_FF, C.BC_FF], method=2,
+                    geo=lambda th: inputs.icosphere((12.3, 12.1, 11.8), 8.0, 4, tbc=0, t_value=1.05 * th))
+    out = []
+    for sep in ("0", "1"):
+        monkeypatch.setenv("LBMIB_BC_SEPARATE", sep)
+        s = lbmib.Solver(case["lattice"], precision, case["shape"], mach=case["mach"], reynolds=case["reynolds"],
+                         ref_length=case["ref_length"], method=case["method"], bc=case["bc"])
+        s.set_geometry(case["geo"](s.constants()["theta_inf"]))
+        s.step(25)
+        s.check()
+        out.append(s.state())
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
