@@ -110,7 +110,7 @@ struct Engine {
     s.tB = h->tB;
     s.G = h->G;
     lbm_status st = launch(h, kProfIBForce, [&] {
-      k_ib_force<L, S, C><<<nblk((long long)h->NL * 32, 128), 128, 0, h->st>>>(
+      k_ib_force<L, S, C><<<nblk(h->NL, kIBPointsPerWarp * kIBWarps), 32 * kIBWarps, 0, h->st>>>(
           h->g, s, (const S*)h->f, (const C*)h->E, h->use_fused ? (const C*)h->M : nullptr);
     });
     if (st) return st;

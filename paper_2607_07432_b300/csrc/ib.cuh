@@ -434,84 +434,103 @@ __device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, lo
   T_o = double(T);
 }
 
+// Points per warp of k_ib_force and warps per block.
+constexpr int kIBPointsPerWarp = 4;
+constexpr int kIBWarps = 2;
+
 template <class L, class S, class C>
-static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E, const C* M) {
+static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E,
+                                                                   const C* M) {
   constexpr int D = L::D;
   constexpr int KS = D == 2 ? 16 : 64;
   constexpr int KP = D == 2 ? 4 : 8;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= s.NL) return;
-  const int l = warp;
-  // Eq. int2: each lane evaluates its stencil slots; lane 0 then adds the
-  // slot contributions in slot order (z, y, x), the same order as a plain
-  // sequential sum, so the FP64 result is reproducible bit for bit.
   constexpr int NV = 2 + 2 * D;
-  double v[(KS + 31) / 32][NV];
+  constexpr int NP = kIBPointsPerWarp;
+  static_assert(NP * 8 == 32 && NV <= 8, "one lane per (point, quantity)");
+  // slot values staged per (point, quantity) row, slots contiguous; rows
+  // padded by one so that a lane per row reads distinct banks
+  __shared__ double stage[kIBWarps][NP * NV][KS + 1];
+  __shared__ double pstage[kIBWarps][NP * (D + 1)][KP + 1];
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int l0 = (blockIdx.x * kIBWarps + wib) * NP;
+  if (l0 >= s.NL) return;
+  // Eq. int2 / Eq. int1 at P: every lane evaluates stencil slots of each of
+  // the warp's points
+#pragma unroll 1
+  for (int p = 0; p < NP; ++p) {
+    const int l = l0 + p;
+    if (l >= s.NL) break;
 #pragma unroll
-  for (int rep = 0; rep < (KS + 31) / 32; ++rep) {
+    for (int rep = 0; rep < (KS + 31) / 32; ++rep) {
+      const int k = lane + 32 * rep;
+      if (k < KS) {
+        double v[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[rep][k] = 0.0;
-    const int k = lane + 32 * rep;
-    if (k < KS) {
-      const int n = s.sten_node[l * KS + k];
+        for (int q = 0; q < NV; ++q) v[q] = 0.0;
+        const int n = s.sten_node[l * KS + k];
+        if (n >= 0) {
+          const double w = s.sten_w[l * KS + k];
+          double rho, j[3], u[3], T;
+          node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
+          v[0] = rho * w;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            v[1 + a] = j[a] * w;
+            v[1 + D + a] = u[a] * w;
+          }
+          v[1 + 2 * D] = T * w;
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) stage[wib][p * NV + q][k] = v[q];
+      }
+    }
+    if (lane < KP) {
+      double pv[D + 1];
+#pragma unroll
+      for (int q = 0; q < D + 1; ++q) pv[q] = 0.0;
+      const int n = s.psten_node[l * KP + lane];
       if (n >= 0) {
-        const double w = s.sten_w[l * KS + k];
+        const double w = s.psten_w[l * KP + lane];
         double rho, j[3], u[3], T;
         node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
-        v[rep][0] = rho * w;
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          v[rep][1 + a] = j[a] * w;
-          v[rep][1 + D + a] = u[a] * w;
-        }
-        v[rep][1 + 2 * D] = T * w;
+        for (int a = 0; a < D; ++a) pv[a] = u[a] * w;
+        pv[D] = T * w;
+      }
+#pragma unroll
+      for (int q = 0; q < D + 1; ++q) pstage[wib][p * (D + 1) + q][lane] = pv[q];
+    }
+  }
+  __syncwarp();
+  // lane (p, q) adds quantity q of point p over the slots in slot order
+  // (z, y, x), the order of a plain sequential sum, so FP64 results are
+  // reproducible bit for bit
+  {
+    const int p = lane >> 3, q = lane & 7;
+    if (l0 + p < s.NL) {
+      if (q < NV) {
+        double a_ = 0.0;
+        for (int k = 0; k < KS; ++k) a_ = a_ + stage[wib][p * NV + q][k];
+        stage[wib][p * NV + q][0] = a_;
+      }
+      if (q < D + 1) {
+        double a_ = 0.0;
+        for (int k = 0; k < KP; ++k) a_ = a_ + pstage[wib][p * (D + 1) + q][k];
+        pstage[wib][p * (D + 1) + q][0] = a_;
       }
     }
   }
-  double pv[D + 1];
-#pragma unroll
-  for (int k = 0; k < D + 1; ++k) pv[k] = 0.0;
-  if (lane < KP) {
-    const int n = s.psten_node[l * KP + lane];
-    if (n >= 0) {
-      const double w = s.psten_w[l * KP + lane];
-      double rho, j[3], u[3], T;
-      node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
-#pragma unroll
-      for (int a = 0; a < D; ++a) pv[a] = u[a] * w;
-      pv[D] = T * w;
-    }
-  }
-  // stage the slot values in shared memory; lane k < NV then adds quantity k
-  // over the slots in order (one FP64 add per slot instead of one per lane)
-  __shared__ double stage[4][64 + 8][NV];
-  const int wib = threadIdx.x >> 5;
-#pragma unroll
-  for (int rep = 0; rep < (KS + 31) / 32; ++rep)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) stage[wib][lane + 32 * rep][k] = v[rep][k];
-  if (lane < KP)
-#pragma unroll
-    for (int k = 0; k < D + 1; ++k) stage[wib][64 + lane][k] = pv[k];
   __syncwarp();
-  double acc[NV];
-  double pacc[D + 1];
-  if (lane < NV) {
-    double a_ = 0.0;
-    for (int k = 0; k < KS; ++k) a_ = a_ + stage[wib][k][lane];
-    stage[wib][0][lane] = a_;
-  } else if (lane >= 16 && lane < 16 + D + 1) {
-    double a_ = 0.0;
-    for (int k = 0; k < KP; ++k) a_ = a_ + stage[wib][64 + k][lane - 16];
-    stage[wib][64][lane - 16] = a_;
-  }
-  __syncwarp();
+  if ((lane & 7) != 0) return;
+  const int pp = lane >> 3;
+  const int l = l0 + pp;
+  if (l >= s.NL) return;
+  double acc[NV], pacc[D + 1];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = stage[wib][0][k];
+  for (int q = 0; q < NV; ++q) acc[q] = stage[wib][pp * NV + q][0];
 #pragma unroll
-  for (int k = 0; k < D + 1; ++k) pacc[k] = stage[wib][64][k];
-  if (lane != 0) return;
+  for (int q = 0; q < D + 1; ++q) pacc[q] = pstage[wib][pp * (D + 1) + q][0];
   const double ph = s.phi[l];
   const double rho_s = ph * acc[0];
   double j_s[3], u_s[3], uP[3], uV[3];
@@ -553,20 +572,49 @@ static __global__ void __launch_bounds__(128) k_ib_force(Grid g, IBStepDev s, co
   s.G[l * (D + 2) + D + 1] = s.Cv * rho_s * (TV - T_s);
 }
 
-// Eq. spr2 as an Eulerian-side gather: f_u, w + q of each forced node
+// Eq. spr2 as an Eulerian-side gather: f_u, w + q of each forced node.
+// Entries are fetched eight at a time (independent loads in flight) and
+// added in CSR order.
 static __global__ void k_ib_spread(int D, int n_rows, const int* row_ptr, const int* col, const double* wt,
-                            const double* G, double* FU, double* WQ) {
+                                   const double* G, double* FU, double* WQ) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-    const int l = col[e];
-    const double w = wt[e];
-    for (int a = 0; a < D; ++a) acc[a] = acc[a] + w * G[l * (D + 2) + a];
-    acc[D] = acc[D] + w * (G[l * (D + 2) + D] + G[l * (D + 2) + D + 1]);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // f_u (D components), w + q in slot 3
+  const int e0 = row_ptr[r], e1 = row_ptr[r + 1];
+  for (int eb = e0; eb < e1; eb += 8) {
+    int lc[8];
+    double wc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      lc[k] = eb + k < e1 ? col[eb + k] : -1;
+      wc[k] = eb + k < e1 ? wt[eb + k] : 0.0;
+    }
+    double gv[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) gv[k][a] = 0.0;
+      if (lc[k] >= 0) {
+        const double* gl = G + (long long)lc[k] * (D + 2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (a < D) gv[k][a] = gl[a];
+        gv[k][3] = gl[D] + gl[D + 1];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (lc[k] < 0) break;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < D) acc[a] = acc[a] + wc[k] * gv[k][a];
+      acc[3] = acc[3] + wc[k] * gv[k][3];
+    }
   }
-  for (int a = 0; a < D; ++a) FU[(long long)r * D + a] = acc[a];
-  WQ[r] = acc[D];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < D) FU[(long long)r * D + a] = acc[a];
+  WQ[r] = acc[3];
 }
 
 // wall loads: fixed-order block reduction (deterministic)
