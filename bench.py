@@ -48,11 +48,21 @@ def kernel_traffic():
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
+    return float(d["dram_bytes_per_launch"]) if fused_sources_sha() == d["src_sha256"] else None
+
+
+def fused_sources_sha():
+    """sha256 over the sources that define the fused step kernel."""
+    import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2607_07432_b300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(f).encode())
+    for name in FUSED_SOURCES:
+        f = os.path.join(ROOT, "paper_2607_07432_b300", "csrc", name)
+        h.update(name.encode())
         h.update(open(f, "rb").read())
-    return float(d["dram_bytes_per_launch"]) if h.hexdigest() == d["src_sha256"] else None
+    return h.hexdigest()
+
+
+FUSED_SOURCES = ["grid.cuh", "inst_d3q19_fp32.cu", "lattice.cuh", "physics.cuh", "step_fused.cuh"]
 
 
 def peaks():
@@ -72,23 +82,53 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.p = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append((time.perf_counter(), line))
 
     def start(self):
+        """Start sampling and wait (at most 5 s) for the first sample, so the
+        sampler is running when the timed region begins."""
+        import threading
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+        t = time.perf_counter()
+        while not self.lines and time.perf_counter() - t < 5.0:
+            time.sleep(0.005)
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.p is None:
             return None
+        time.sleep(0.05)
         self.p.terminate()
-        out, _ = self.p.communicate(timeout=10)
+        try:
+            self.p.wait(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        # samples inside the timed region, plus the last one before it
+        t0 = self.t0 if self.t0 is not None else -1e30
+        t1 = self.t1 if self.t1 is not None else 1e30
+        inside = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.025]
+        before = [ln for (t, ln) in self.lines if t < t0]
+        sel = (before[-1:] + inside) if before else inside
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in sel:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -254,7 +294,7 @@ def run_warmstart(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
@@ -299,10 +339,12 @@ def main():
     clocks.start()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.begin()
     e0.record()
     s.step(args.steps)
     e1.record()
     barrier()
+    clocks.end()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     prof = s.get_profile()
