@@ -365,11 +365,88 @@ __device__ __forceinline__ C muscl3(C A, C B, C Cc, C uB, bool plus) {
   return (plus ? pp : pm) + C(0.5) * uB * (pm - pp);
 }
 
+// FP32 form of the face flux below, algebraically the same: the LB mass
+// and momentum fluxes are sums over the crossing populations grouped by
+// direction (the transverse pairs of a diagonal population are added before
+// the common 1/2 is applied), and the MUSCL-Hancock face value
+// B +- delta/2 - uB delta/2 of Eq. linear is written as
+// B + alpha (B - A) + beta (Cc - B) with the weights computed once per face.
+template <class L, class C, int AX, class MacroAlong, class FcolAt>
+__device__ __forceinline__ C energy_face_flux_fast(const MacroAlong& MA, const FcolAt& FC, const Phys<C>& ph) {
+  constexpr int D = L::D;
+  const C cs2 = C(kCs2);
+  C Ps = C(0), Ns = C(0), Pd = C(0), Nd = C(0);
+  C Tm[3] = {C(0), C(0), C(0)};
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int ca = L::c(i, AX);
+    if constexpr (ca != 0) {
+      constexpr int b0 = (ca < 0 && AX == 0) ? 1 : 0;
+      constexpr int b1 = (ca < 0 && AX == 1) ? 1 : 0;
+      constexpr int b2 = (ca < 0 && AX == 2) ? 1 : 0;
+      constexpr int t = transverse_axis<L>(i, AX);
+      if constexpr (t < 0) {
+        if constexpr (ca > 0) Ps += FC(i, b0, b1, b2);
+        else Ns += FC(i, b0, b1, b2);
+      } else {
+        constexpr int o0 = b0 - (t == 0 ? L::c(i, 0) : 0);
+        constexpr int o1 = b1 - (t == 1 ? L::c(i, 1) : 0);
+        constexpr int o2 = b2 - (t == 2 ? L::c(i, 2) : 0);
+        const C u = FC(i, b0, b1, b2) + FC(i, o0, o1, o2);
+        if constexpr (ca > 0) Pd += u;
+        else Nd += u;
+        constexpr int sgn = L::c(i, t) * ca;
+        if constexpr (sgn > 0) Tm[t] += u;
+        else Tm[t] -= u;
+      }
+    }
+  });
+  const C Frho = (Ps - Ns) + C(0.5) * (Pd - Nd);
+  C Fm[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) Fm[b] = C(0.5) * Tm[b];
+  Fm[AX] = (Ps + Ns) + C(0.5) * (Pd + Nd);
+  const Macro<C> m1 = MA(0), m2 = MA(1);
+  const bool plus = C(0.5) * (m1.u[AX] + m2.u[AX]) >= C(0);
+  const Macro<C> mo = MA(plus ? -1 : 2);
+  const Macro<C>& A = plus ? mo : m1;
+  const Macro<C>& B = plus ? m1 : m2;
+  const Macro<C>& Cc = plus ? m2 : mo;
+  const C pA = A.rho * cs2 * A.th, pB = B.rho * cs2 * B.th, pC = Cc.rho * cs2 * Cc.th;
+  const C uB = B.u[AX];
+  const C sg = uB > C(0) ? C(1) : (uB < C(0) ? C(-1) : C(0));
+  const C eta = third<C>(C(2) * uB - sg);
+  const C kap = C(0.25) * ((plus ? C(1) : C(-1)) - uB);
+  const C al = kap * (C(1) + eta), be = kap * (C(1) - eta);
+  auto rec = [&](C a, C b, C c) { return b + al * (b - a) + be * (c - b); };
+  const C FH = rec((A.E + pA) * A.u[AX], (B.E + pB) * B.u[AX], (Cc.E + pC) * Cc.u[AX]);
+  const C Fr = rec(A.rho * A.u[AX], B.rho * B.u[AX], Cc.rho * Cc.u[AX]);
+  C k1 = C(0), k2 = C(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    k1 += m1.u[b] * m1.u[b];
+    k2 += m2.u[b] * m2.u[b];
+  }
+  const C hk = C(0.5) * ((ph.Cp * m1.th + ph.Cp * m2.th) - C(0.5) * (k1 + k2));
+  C FE = FH + hk * (Frho - Fr);
+  const C rA = A.rho * A.u[AX], rB = B.rho * B.u[AX], rC = Cc.rho * Cc.u[AX];
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const C Fb = rec(rA * A.u[b] + (AX == b ? pA : C(0)), rB * B.u[b] + (AX == b ? pB : C(0)),
+                     rC * Cc.u[b] + (AX == b ? pC : C(0)));
+    const C ub = C(0.5) * (m1.u[b] + m2.u[b]);
+    FE = FE + ub * (Fm[b] - Fb);
+  }
+  FE = FE - ph.lam * (m2.th - m1.th);
+  return FE;
+}
+
 // Total-energy flux F^{rhoE}_{+axis/2} through the face x + e_axis/2
 // (Eq. energy).  MacroAlong(k) returns the Macro of cell x + k e_axis
 // (k = -1..2); FcolAt(i, dx, dy, dz) returns f^col_i at x + (dx,dy,dz).
 template <class L, class C, int AX, class MacroAlong, class FcolAt>
 __device__ __forceinline__ C energy_face_flux(const MacroAlong& MA, const FcolAt& FC, const Phys<C>& ph) {
+  if constexpr (sizeof(C) == 4) return energy_face_flux_fast<L, C, AX>(MA, FC, ph);
   constexpr int D = L::D;
   const C cs2 = C(kCs2);
   // LB mass and momentum fluxes (Eqs. fluxx-z and the rule below them)
