@@ -302,29 +302,35 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
   });
   const C R1 = m.rho * (m.th - C(1));
   const C base = m.rho + R1 - cs2 * trB;
-  sfor<0, Q>([&](auto I) {
+  // f_i = w_i (E_i + O_i) and f_opp(i) = w_i (E_i - O_i): the even (zeroth and
+  // second order) part is shared by a direction and its opposite, the odd
+  // (first and third order) part changes sign
+  fcol[0] = C(L::w(0)) * base - R1;
+  sfor<1, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    C t = base;
-    sfor<0, D>([&](auto A) {
-      constexpr int a = decltype(A)::value;
-      if constexpr (L::c(i, a) == 1) t += A1[a] + B2[a][a];
-      if constexpr (L::c(i, a) == -1) t += B2[a][a] - A1[a];
-      sfor<decltype(A)::value + 1, D>([&](auto B) {
-        constexpr int b = decltype(B)::value;
-        constexpr int cc = L::c(i, a) * L::c(i, b);
-        if constexpr (cc == 1) t += C(2) * B2[a][b];
-        if constexpr (cc == -1) t -= C(2) * B2[a][b];
+    constexpr int o = opposite<L>(i);
+    if constexpr (i < o) {
+      C E = base, O = C(0);
+      sfor<0, D>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        if constexpr (L::c(i, a) != 0) E += B2[a][a];
+        if constexpr (L::c(i, a) == 1) O += A1[a];
+        if constexpr (L::c(i, a) == -1) O -= A1[a];
+        sfor<decltype(A)::value + 1, D>([&](auto B) {
+          constexpr int b = decltype(B)::value;
+          constexpr int cc = L::c(i, a) * L::c(i, b);
+          if constexpr (cc == 1) E += C(2) * B2[a][b];
+          if constexpr (cc == -1) E -= C(2) * B2[a][b];
+        });
       });
-    });
-    sfor<0, L::N3>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      constexpr double h = H3r<L>(k, i);
-      if constexpr (h != 0.0) t += C(h) * A3[k];
-    });
-    if constexpr (i == 0) {
-      fcol[i] = C(L::w(i)) * t - R1;
-    } else {
-      fcol[i] = C(L::w(i)) * t;
+      sfor<0, L::N3>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        constexpr double h = H3r<L>(k, i);
+        if constexpr (h != 0.0) O += C(h) * A3[k];
+      });
+      const C wE = C(L::w(i)) * E, wO = C(L::w(i)) * O;
+      fcol[i] = wE + wO;
+      fcol[o] = wE - wO;
     }
   });
   P_new = P;
