@@ -291,6 +291,22 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (every rank gets it); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, nodes, steps, seconds):
+    """Whole-job throughput: every rank advances its own replica of `nodes`
+    nodes by `steps` steps in `seconds` (the slowest rank's time)."""
+    return world * nodes * steps / seconds / 1e6
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,12 +366,9 @@ def main():
     prof = s.get_profile()
     s.profile(False, True)
     launches = s.launch_count() - l0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / args.steps
-    value = world * N * args.steps / (ms / 1e3) / 1e6
+    value = job_mlups(world, N, args.steps, ms / 1e3)
     s.check()
 
     # end-to-end through the public API with host buffers: the job uploads
@@ -374,8 +387,8 @@ def main():
         s.step(1)
         s.wall_loads()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": job_mlups(world, N, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(N * 5 * 8 / args.steps), "d2h_bytes_per_step": 5 * 8}
 
     if rank != 0:
