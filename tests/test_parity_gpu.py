@@ -140,3 +140,31 @@ def test_boundaries_in_kernel_match_separate_kernel(lattice, precision, monkeypa
         s.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_naca_downscale_fp32_against_oracle():
+    """Airfoil case at its 512x256 downscale (NACA0012, chord 100, 256
+    points, Ma 0.5, Re 5000, adiabatic wall, 2 degrees): FP32 path vs FP64
+    oracle after 60 steps.  Fields: relative L2 of velocity and temperature
+    <= 1e-5.  Wall distributions: the per-point Lagrangian force split into
+    its normal part (wall pressure) and tangential part (skin friction),
+    relative L2 <= 1e-4 each."""
+    case = C.naca_downscale()
+    sim, geo = C.make_oracle(case)
+    g = C.make_gpu(case, "fp32", geo)
+    sim.run(60)
+    g.step(60)
+    g.check()
+    rho, u, T, p = g.fields()
+    r0, u0, T0, p0 = sim.fields()
+    assert _rel_l2(u, u0) < 1e-5
+    assert _rel_l2(T, T0) < 1e-5
+    wl = g.wall_loads(per_point=True)
+    F, F0 = wl["F"], sim.last_loads["F"]
+    n = np.asarray(geo["normals"])
+    t = np.stack([-n[:, 1], n[:, 0]], axis=1)
+    fn, fn0 = np.sum(F * n, axis=1), np.sum(F0 * n, axis=1)
+    ft, ft0 = np.sum(F * t, axis=1), np.sum(F0 * t, axis=1)
+    assert _rel_l2(fn, fn0) < 1e-4
+    assert _rel_l2(ft, ft0) < 1e-4
+    g.close()
