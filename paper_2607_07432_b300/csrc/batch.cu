@@ -1,6 +1,6 @@
-// Batched stepping of several cases (lbm_batch_*): the per-case immersed
-// boundary and boundary kernels surround one fused launch that covers the
-// tiles of every case, from a schedule table; two consecutive steps (both
+// Batched stepping of several cases (lbm_batch_*): one launch each of the
+// immersed-boundary force, spreading and boundary kernels and one fused
+// launch cover every case, from work tables; two consecutive steps (both
 // buffer parities) are captured once as a CUDA graph and replayed.  The
 // autotuner times the tile heights and schedules on the batch and keeps the
 // fastest; it restores the state it advanced.
@@ -70,20 +70,18 @@ lbm_status rebuild(lbm_batch* b) {
 // one step of every case, eager (also used while capturing)
 lbm_status one_step(lbm_batch* b, int parity) {
   BatchPlan& p = b->plan;
-  for (lbm_handle* h : p.cases) {
+  for (lbm_handle* h : p.cases)
     if (h->sticky) return (lbm_status)h->sticky;
-    lbm_status s = b->ops->ib_part(h);
-    if (s) return bfail(b, s, h->err);
-  }
-  lbm_status s = b->ops->batch_fused(&p, parity);
+  lbm_status s = b->ops->batch_aux(&p, parity, 0);
+  if (!s) s = b->ops->batch_fused(&p, parity);
   if (s) return bfail(b, s, p.err);
   for (lbm_handle* h : p.cases) {
     std::swap(h->f, h->f2);
     std::swap(h->M, h->M2);
     h->cur = 1 - h->cur;
-    lbm_status s2 = b->ops->bc_part(h);
-    if (s2) return bfail(b, s2, h->err);
   }
+  s = b->ops->batch_aux(&p, parity, 1);
+  if (s) return bfail(b, s, p.err);
   return LBM_OK;
 }
 
@@ -125,9 +123,12 @@ void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   drop_graph(b);
   for (lbm_handle* h : b->plan.cases) lbm_destroy(h);
+  BatchPlan& pl = b->plan;
   for (int p = 0; p < 2; ++p)
-    if (b->plan.descs[p]) cudaFree(b->plan.descs[p]);
-  if (b->plan.work) cudaFree(b->plan.work);
+    for (void* d : {pl.descs[p], pl.ib_descs[p], pl.sp_descs[p], pl.bc_descs[p]})
+      if (d) cudaFree(d);
+  for (void* d : {pl.work, pl.ib_work, pl.sp_work, pl.bc_work})
+    if (d) cudaFree(d);
   if (b->st) cudaStreamDestroy(b->st);
   delete b;
 }

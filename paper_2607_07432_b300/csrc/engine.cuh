@@ -92,7 +92,7 @@ struct Engine {
   static lbm_status set_fields_api(lbm_handle* h, const double* rho, const double* u, const double* T) {
     return set_fields(h, rho, u, T, true);
   }
-  static lbm_status ib_force(lbm_handle* h) {
+  static IBStepDev ib_step_dev(lbm_handle* h) {
     IBStepDev s;
     s.NL = h->NL;
     s.method = h->cfg.method;
@@ -109,6 +109,15 @@ struct Engine {
     s.uB = h->uB;
     s.tB = h->tB;
     s.G = h->G;
+    return s;
+  }
+  static BCFaces bc_faces(lbm_handle* h) {
+    BCFaces bf;
+    for (int face = 0; face < 6; ++face) bf.type[face] = face < 2 * L::D ? h->cfg.bc[face] : 0;
+    return bf;
+  }
+  static lbm_status ib_force(lbm_handle* h) {
+    const IBStepDev s = ib_step_dev(h);
     lbm_status st = launch(h, kProfIBForce, [&] {
       k_ib_force<L, S, C><<<nblk(h->NL, kIBPointsPerWarp * kIBWarps), 32 * kIBWarps, 0, h->st>>>(
           h->g, s, (const S*)h->f, (const C*)h->E, h->use_fused ? (const C*)h->M : nullptr);
@@ -273,6 +282,7 @@ struct Engine {
           for (int by = 0; by < ty[k]; ++by)
             for (int bx = 0; bx < tx[k]; ++bx) w.push_back(make_int4(k, bx, by, bz));
     }
+    if (lbm_status sa = batch_aux_build(b)) return sa;
     for (int p = 0; p < 2; ++p) {
       if (b->descs[p]) cudaFree(b->descs[p]);
       if (cudaMalloc(&b->descs[p], sizeof(CaseDesc<S, C>) * n) != cudaSuccess) return LBM_ENOMEM;
@@ -285,6 +295,109 @@ struct Engine {
     if (cudaMemcpy(b->work, w.data(), sizeof(int4) * w.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return LBM_ECUDA;
     b->n_work = (int)w.size();
+    return LBM_OK;
+  }
+  template <class T>
+  static lbm_status upload(void*& dst, const std::vector<T>& v) {
+    if (dst) cudaFree(dst);
+    dst = nullptr;
+    if (v.empty()) return LBM_OK;
+    if (cudaMalloc(&dst, sizeof(T) * v.size()) != cudaSuccess) return LBM_ENOMEM;
+    if (cudaMemcpy(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) return LBM_ECUDA;
+    return LBM_OK;
+  }
+  // descriptors and work items of the batched IB and boundary launches; the
+  // pointers of parity p are those the per-case kernels would use after p
+  // buffer swaps from the build-time state
+  static lbm_status batch_aux_build(BatchPlan* b) {
+    const int n = (int)b->cases.size();
+    std::vector<IBCaseDesc<S, C>> ib[2];
+    std::vector<SpreadCaseDesc<C>> sp[2];
+    std::vector<BCCaseDesc<S, C>> bcd[2];
+    std::vector<int2> ibw, spw;
+    std::vector<int4> bcw;
+    for (int k = 0; k < n; ++k) {
+      lbm_handle* h = b->cases[k];
+      for (int p = 0; p < 2; ++p) {
+        IBCaseDesc<S, C> d;
+        d.g = h->g;
+        d.s = ib_step_dev(h);
+        d.f = (const S*)(p ? h->f2 : h->f);
+        d.E = (const C*)h->E;
+        d.M = (const C*)(p ? h->M2 : h->M);
+        ib[p].push_back(d);
+        SpreadCaseDesc<C> q;
+        q.D = L::D;
+        q.N = h->g.N;
+        q.n_rows = h->n_rows;
+        q.row_ptr = h->row_ptr;
+        q.col = h->col;
+        q.wt = h->wt;
+        q.G = h->G;
+        q.cell_id = h->cell_id;
+        q.FU = h->FU;
+        q.WQ = h->WQ;
+        q.M = (C*)(p ? h->M2 : h->M);
+        sp[p].push_back(q);
+        BCCaseDesc<S, C> c;
+        c.g = h->g;
+        c.f = (S*)(p ? h->f : h->f2);
+        c.M = (C*)(p ? h->M : h->M2);
+        c.bf = bc_faces(h);
+        c.feq_inf = (const C*)h->feq_inf;
+        c.E_inf = C(h->E_inf);
+        c.skip_x = bc_in_kernel(h) ? 1 : 0;
+        bcd[p].push_back(c);
+      }
+      if (h->has_ib) {
+        const int nb = (int)nblk(h->NL, kIBPointsPerWarp * kIBWarps);
+        for (int q = 0; q < nb; ++q) ibw.push_back(make_int2(k, q));
+        const int nr = (int)nblk(h->n_rows, 128);
+        for (int q = 0; q < nr; ++q) spw.push_back(make_int2(k, q));
+      }
+      const BCFaces bf = bc_faces(h);
+      const int skip_x = bc_in_kernel(h) ? 1 : 0;
+      for (int face = 0; face < 2 * L::D; ++face) {
+        if (!bf.type[face] || (skip_x && face < 2)) continue;
+        FacePlane fp{face / 2, face % 2};
+        const int nb = (int)nblk(fp.count(h->g), 128);
+        for (int q = 0; q < nb; ++q) bcw.push_back(make_int4(k, face, q, 0));
+      }
+    }
+    lbm_status s = LBM_OK;
+    for (int p = 0; p < 2 && !s; ++p) {
+      s = upload(b->ib_descs[p], ib[p]);
+      if (!s) s = upload(b->sp_descs[p], sp[p]);
+      if (!s) s = upload(b->bc_descs[p], bcd[p]);
+    }
+    if (!s) s = upload(b->ib_work, ibw);
+    if (!s) s = upload(b->sp_work, spw);
+    if (!s) s = upload(b->bc_work, bcw);
+    b->n_ib_work = (int)ibw.size();
+    b->n_sp_work = (int)spw.size();
+    b->n_bc_work = (int)bcw.size();
+    return s;
+  }
+  static lbm_status batch_aux(BatchPlan* b, int parity, int part) {
+    if (part == 0) {
+      if (b->n_ib_work) {
+        k_ib_force_batched<L, S, C><<<b->n_ib_work, 32 * kIBWarps, 0, b->st>>>(
+            (const IBCaseDesc<S, C>*)b->ib_descs[parity], (const int2*)b->ib_work);
+        k_spread_apply_batched<C><<<b->n_sp_work, 128, 0, b->st>>>((const SpreadCaseDesc<C>*)b->sp_descs[parity],
+                                                                   (const int2*)b->sp_work);
+        for (lbm_handle* h : b->cases)
+          if (h->has_ib) h->launches += 2;
+      }
+    } else if (b->n_bc_work) {
+      k_bc_batched<L, S, C><<<b->n_bc_work, 128, 0, b->st>>>((const BCCaseDesc<S, C>*)b->bc_descs[parity],
+                                                            (const int4*)b->bc_work);
+      for (lbm_handle* h : b->cases) h->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      b->err = std::string("batched launch: ") + cudaGetErrorString(e);
+      return LBM_ECUDA;
+    }
     return LBM_OK;
   }
   template <int HY>
@@ -369,7 +482,7 @@ struct Engine {
   }
   static const Ops* ops() {
     static const Ops o = {&init,   &step,        &fields,      &get_state, &set_state, &set_fields_api,
-                          &health, &batch_build, &batch_fused, &ib_part,   &bc_part};
+                          &health, &batch_build, &batch_fused, &batch_aux, &ib_part,   &bc_part};
     return &o;
   }
 };

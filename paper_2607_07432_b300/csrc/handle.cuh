@@ -130,6 +130,9 @@ struct Ops {
   // of a plan, and launch one batched fused step of the given parity
   lbm_status (*batch_build)(BatchPlan*);
   lbm_status (*batch_fused)(BatchPlan*, int parity);
+  // the IB part (part 0: interpolation, forcing, spreading) or the boundary
+  // part (part 1) of every case of a plan, one launch per kernel
+  lbm_status (*batch_aux)(BatchPlan*, int parity, int part);
   // per-case parts of a step around the fused kernel
   lbm_status (*ib_part)(lbm_handle*);
   lbm_status (*bc_part)(lbm_handle*);
@@ -140,12 +143,22 @@ struct Ops {
 struct BatchPlan {
   std::vector<lbm_handle*> cases;
   cudaStream_t st = nullptr;
-  int bc_in_kernel = 1;  // far-field boundaries inside the fused kernel when the faces allow it
   int tile_rows = 0;   // 0: the default tile of the lattice / precision
   int schedule = 0;    // 0 case-major, 1 round-robin over cases, 2 largest case first
   void* descs[2] = {nullptr, nullptr};   // device CaseDesc arrays, parity 0 / 1
   void* work = nullptr;                  // device int4 work items
   int n_work = 0;
+  // IB force, spread + apply and boundary launches over all cases:
+  // per-parity case descriptors and work items (case, block [, face])
+  void* ib_descs[2] = {nullptr, nullptr};
+  void* ib_work = nullptr;
+  int n_ib_work = 0;
+  void* sp_descs[2] = {nullptr, nullptr};
+  void* sp_work = nullptr;
+  int n_sp_work = 0;
+  void* bc_descs[2] = {nullptr, nullptr};
+  void* bc_work = nullptr;
+  int n_bc_work = 0;
   std::vector<void*> built_f;            // per case h->f at build time (parity 0)
   std::vector<int> built_geom;           // per case geometry version at build time
   bool built = false;

@@ -438,9 +438,11 @@ __device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, lo
 constexpr int kIBPointsPerWarp = 4;
 constexpr int kIBWarps = 2;
 
+// Body of the IB force step for block blk (kIBWarps warps of
+// kIBPointsPerWarp Lagrangian points each) of one case.
 template <class L, class S, class C>
-static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E,
-                                                                   const C* M) {
+__device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s, const S* f, const C* E,
+                                              const C* M, int blk) {
   constexpr int D = L::D;
   constexpr int KS = D == 2 ? 16 : 64;
   constexpr int KP = D == 2 ? 4 : 8;
@@ -453,7 +455,7 @@ static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBSte
   __shared__ double pstage[kIBWarps][NP * (D + 1)][KP + 1];
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int l0 = (blockIdx.x * kIBWarps + wib) * NP;
+  const int l0 = (blk * kIBWarps + wib) * NP;
   if (l0 >= s.NL) return;
   // Eq. int2 / Eq. int1 at P: every lane evaluates stencil slots of each of
   // the warp's points
@@ -572,14 +574,36 @@ static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBSte
   s.G[l * (D + 2) + D + 1] = s.Cv * rho_s * (TV - T_s);
 }
 
+template <class L, class S, class C>
+static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E,
+                                                                   const C* M) {
+  ib_force_body<L, S, C>(g, s, f, E, M, blockIdx.x);
+}
+
+// Several cases in one launch: work item = (case, block of the case).
+template <class S, class C>
+struct IBCaseDesc {
+  Grid g;
+  IBStepDev s;
+  const S* f;
+  const C* E;
+  const C* M;
+};
+
+template <class L, class S, class C>
+static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force_batched(const IBCaseDesc<S, C>* d,
+                                                                           const int2* work) {
+  const int2 w = work[blockIdx.x];
+  const IBCaseDesc<S, C>& c = d[w.x];
+  ib_force_body<L, S, C>(c.g, c.s, c.f, c.E, c.M, w.y);
+}
+
 // Eq. spr2 as an Eulerian-side gather: f_u, w + q of each forced node.
 // Entries are fetched eight at a time (independent loads in flight) and
-// added in CSR order.
-static __global__ void k_ib_spread(int D, int n_rows, const int* row_ptr, const int* col, const double* wt,
-                                   const double* G, double* FU, double* WQ) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_rows) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // f_u (D components), w + q in slot 3
+// added in CSR order.  acc receives f_u (D components) and w + q (slot 3).
+__device__ __forceinline__ void spread_row(int D, int r, const int* row_ptr, const int* col, const double* wt,
+                                           const double* G, double (&acc)[4]) {
+  acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
   const int e0 = row_ptr[r], e1 = row_ptr[r + 1];
   for (int eb = e0; eb < e1; eb += 8) {
     int lc[8];
@@ -611,10 +635,57 @@ static __global__ void k_ib_spread(int D, int n_rows, const int* row_ptr, const 
       acc[3] = acc[3] + wc[k] * gv[k][3];
     }
   }
+}
+
+static __global__ void k_ib_spread(int D, int n_rows, const int* row_ptr, const int* col, const double* wt,
+                                   const double* G, double* FU, double* WQ) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  double acc[4];
+  spread_row(D, r, row_ptr, col, wt, G, acc);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     if (a < D) FU[(long long)r * D + a] = acc[a];
   WQ[r] = acc[3];
+}
+
+// Spreading and its application to the moments, several cases in one
+// launch: the same sums as k_ib_spread and the same updates as
+// k_apply_forcing, for one row per thread.
+template <class C>
+struct SpreadCaseDesc {
+  int D;
+  long long N;
+  int n_rows;
+  const int* row_ptr;
+  const int* col;
+  const double* wt;
+  const double* G;
+  const int* cell_id;
+  double* FU;
+  double* WQ;
+  C* M;
+};
+
+template <class C>
+static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const int2* work) {
+  const int2 w = work[blockIdx.x];
+  const SpreadCaseDesc<C>& c = d[w.x];
+  const int r = w.y * blockDim.x + threadIdx.x;
+  if (r >= c.n_rows) return;
+  const int D = c.D;
+  double acc[4];
+  spread_row(D, r, c.row_ptr, c.col, c.wt, c.G, acc);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < D) c.FU[(long long)r * D + a] = acc[a];
+  c.WQ[r] = acc[3];
+  const long long n = c.cell_id[r];
+  const long long N = c.N;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < D) c.M[(1 + a) * N + n] = c.M[(1 + a) * N + n] + C(0.5) * C(acc[a]);
+  c.M[(1 + D) * N + n] = c.M[(1 + D) * N + n] + C(acc[3]);
 }
 
 // wall loads: fixed-order block reduction (deterministic)

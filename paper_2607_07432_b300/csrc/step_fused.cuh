@@ -604,15 +604,15 @@ struct BCFaces {
   int type[6];  // LBM_BC_* per face: 0 periodic, 1 inlet, 2 outlet, 3 far field
 };
 
+// boundary node t of face `face` (see k_bc_all_m)
 template <class L, class S, class C>
-__global__ void k_bc_all_m(Grid g, S* f, C* M, BCFaces bf, const C* feq_inf, C E_inf, int skip_x) {
+__device__ __forceinline__ void bc_node(const Grid& g, S* f, C* M, const BCFaces& bf, const C* feq_inf, C E_inf,
+                                        int skip_x, int face, int t) {
   constexpr int D = L::D;
-  const int face = blockIdx.y;
   const int axis = face / 2, side = face % 2;
   const int ft = bf.type[face];
   if (ft == 0 || (skip_x && axis == 0)) return;
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.n[a1] * g.n[a2]) return;
   int c[3];
   c[a1] = t % g.n[a1];
@@ -654,5 +654,31 @@ __global__ void k_bc_all_m(Grid g, S* f, C* M, BCFaces bf, const C* feq_inf, C E
 #pragma unroll
   for (int k = 0; k < L::D + 2; ++k) M[k * g.N + dst] = M[k * g.N + src];
 }
+
+template <class L, class S, class C>
+__global__ void k_bc_all_m(Grid g, S* f, C* M, BCFaces bf, const C* feq_inf, C E_inf, int skip_x) {
+  bc_node<L, S, C>(g, f, M, bf, feq_inf, E_inf, skip_x, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Several cases in one launch.
+template <class S, class C>
+struct BCCaseDesc {
+  Grid g;
+  S* f;
+  C* M;
+  BCFaces bf;
+  const C* feq_inf;
+  C E_inf;
+  int skip_x;
+};
+
+// work item = (case, face, block of that face's nodes)
+template <class L, class S, class C>
+__global__ void k_bc_batched(const BCCaseDesc<S, C>* d, const int4* work) {
+  const int4 w = work[blockIdx.x];
+  const BCCaseDesc<S, C>& c = d[w.x];
+  bc_node<L, S, C>(c.g, c.f, c.M, c.bf, c.feq_inf, c.E_inf, c.skip_x, w.y, w.z * blockDim.x + threadIdx.x);
+}
+
 
 }  // namespace lbmib
