@@ -169,7 +169,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     const char* env = std::getenv("LBMIB_UNFUSED");
     h->use_fused = (env && env[0] == '1') ? 0 : 1;
     const char* zc = std::getenv("LBMIB_ZCHUNK");
-    if (zc) h->zchunk = std::max(1, std::atoi(zc));
+    if (zc) {
+      h->zchunk = std::max(1, std::atoi(zc));
+      h->zchunk_fixed = 1;
+    }
     const char* tr = std::getenv("LBMIB_TILE_ROWS");
     if (tr) h->tile_rows = std::atoi(tr);
     const char* bk = std::getenv("LBMIB_BC_SEPARATE");

@@ -51,7 +51,37 @@ struct Engine {
                                                                   (C*)h->P[h->cur], (C*)h->A[h->cur]);
     });
   }
+  // Planes per CTA of the 3D fused step: every chunk recomputes two
+  // collision planes, and the last wave of CTAs runs partly empty, so take
+  // the chunk that minimises (waves of CTAs) x (planes a CTA collides).
+  static void choose_zchunk(lbm_handle* h) {
+    if (L::D != 3 || !h->use_fused || h->zchunk_fixed) return;
+    using Lay = FusedLayout<L, S, C, 0>;
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->cfg.device) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fused<L, S, C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<L, S, C, 0>, Lay::NT, Lay::bytes) !=
+            cudaSuccess ||
+        sms <= 0 || occ <= 0) {
+      cudaGetLastError();
+      return;
+    }
+    const long long tiles = (long long)((h->g.n[0] + Lay::TX - 1) / Lay::TX) * ((h->g.n[1] + Lay::TY - 1) / Lay::TY);
+    const int nz = h->g.n[2];
+    long long best = -1;
+    for (int zc = 4; zc <= std::max(4, nz); ++zc) {
+      const long long ctas = tiles * ((nz + zc - 1) / zc);
+      const long long waves = (ctas + (long long)sms * occ - 1) / ((long long)sms * occ);
+      const long long cost = waves * (zc + 2);
+      if (best < 0 || cost < best) {
+        best = cost;
+        h->zchunk = zc;
+      }
+    }
+  }
   static lbm_status init(lbm_handle* h) {
+    choose_zchunk(h);
     lbm_status s = launch(h, kProfOther, [&] {
       k_feq_inf<L, C><<<1, 32, 0, h->st>>>((C*)h->feq_inf, C(h->rho_inf), C(h->u_inf[0]), C(h->u_inf[1]),
                                            C(h->u_inf[2]), C(h->theta_inf));

@@ -39,6 +39,7 @@ struct lbm_handle {
   int cur = 0;
   int use_fused = 1;         // fused shared-memory step (0: unfused global-memory form)
   int zchunk = 16;           // planes per CTA along z in the fused step
+  int zchunk_fixed = 0;      // set by the environment: keep it
   int bc_in_kernel = 1;  // far-field boundaries inside the fused kernel when the faces allow it
   int tile_rows = 0;         // tile height of the 3D FP32 fused step (0 = default)
   void* f2 = nullptr;        // second population buffer (fused form)

@@ -396,8 +396,8 @@ static __device__ __forceinline__ double warp_sum(double v) {
 // Evaluated in the compute type C (the precision of the stored state) and
 // widened to FP64 for the Lagrangian sums.
 template <class L, class S, class C>
-__device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, long long N, long long n,
-                                          double& rho_o, double* j_o, double* u_o, double& T_o, C Cv) {
+__device__ __forceinline__ void node_pred_c(const S* f, const C* E, const C* M, long long N, long long n,
+                                            C& rho_o, C* j_o, C* u_o, C& T_o, C Cv) {
   constexpr int D = L::D;
   C rho, j[3], En;
   if (M) {
@@ -418,21 +418,47 @@ __device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, lo
     }
     En = E[n];
   }
-  C uu = C(0), u[3];
+  C uu = C(0), u[3], T;
+  if constexpr (sizeof(C) == 8) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = j[a] / rho;
+      uu += u[a] * u[a];
+    }
+    T = (En / rho - C(0.5) * uu) / Cv;
+  } else {
+    const C ir = C(1) / rho;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      u[a] = j[a] * ir;
+      uu += u[a] * u[a];
+    }
+    T = (En * ir - C(0.5) * uu) * (C(1) / Cv);
+  }
+  rho_o = rho;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    u[a] = j[a] / rho;
-    uu += u[a] * u[a];
+    j_o[a] = j[a];
+    u_o[a] = u[a];
   }
-  const C T = (En / rho - C(0.5) * uu) / Cv;
+  T_o = T;
+}
+
+template <class L, class S, class C>
+__device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, long long N, long long n,
+                                          double& rho_o, double* j_o, double* u_o, double& T_o, C Cv) {
+  C rho, j[3], u[3], T;
+  node_pred_c<L, S, C>(f, E, M, N, n, rho, j, u, T, Cv);
   rho_o = double(rho);
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
+  for (int a = 0; a < L::D; ++a) {
     j_o[a] = double(j[a]);
     u_o[a] = double(u[a]);
   }
   T_o = double(T);
 }
+
+
 
 // Points per warp of k_ib_force and warps per block.
 constexpr int kIBPointsPerWarp = 4;
@@ -472,16 +498,30 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
         for (int q = 0; q < NV; ++q) v[q] = 0.0;
         const int n = s.sten_node[l * KS + k];
         if (n >= 0) {
-          const double w = s.sten_w[l * KS + k];
-          double rho, j[3], u[3], T;
-          node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
-          v[0] = rho * w;
+          if constexpr (sizeof(C) == 8) {
+            const double w = s.sten_w[l * KS + k];
+            double rho, j[3], u[3], T;
+            node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
+            v[0] = rho * w;
 #pragma unroll
-          for (int a = 0; a < D; ++a) {
-            v[1 + a] = j[a] * w;
-            v[1 + D + a] = u[a] * w;
+            for (int a = 0; a < D; ++a) {
+              v[1 + a] = j[a] * w;
+              v[1 + D + a] = u[a] * w;
+            }
+            v[1 + 2 * D] = T * w;
+          } else {
+            // FP32 state: the slot products in FP32, their sums in FP64
+            const C w = C(s.sten_w[l * KS + k]);
+            C rho, j[3], u[3], T;
+            node_pred_c<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
+            v[0] = double(rho * w);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+              v[1 + a] = double(j[a] * w);
+              v[1 + D + a] = double(u[a] * w);
+            }
+            v[1 + 2 * D] = double(T * w);
           }
-          v[1 + 2 * D] = T * w;
         }
 #pragma unroll
         for (int q = 0; q < NV; ++q) stage[wib][p * NV + q][k] = v[q];
