@@ -153,14 +153,15 @@ struct Engine {
           h->g, s, (const S*)h->f, (const C*)h->E, h->use_fused ? (const C*)h->M : nullptr);
     });
     if (st) return st;
-    st = launch(h, kProfIBSpread, [&] {
+    if (h->use_fused)
+      return launch(h, kProfIBSpread, [&] {
+        k_ib_spread_apply<C><<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->g.N, h->n_rows, h->row_ptr, h->col,
+                                                                      h->wt, h->G, h->cell_id, h->FU, h->WQ,
+                                                                      (C*)h->M);
+      });
+    return launch(h, kProfIBSpread, [&] {
       k_ib_spread<<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->n_rows, h->row_ptr, h->col, h->wt, h->G,
                                                           h->FU, h->WQ);
-    });
-    if (st || !h->use_fused) return st;
-    return launch(h, kProfIBSpread, [&] {
-      k_apply_forcing<C><<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->g.N, h->n_rows, h->cell_id, h->FU,
-                                                                  h->WQ, (C*)h->M);
     });
   }
   static lbm_status bc(lbm_handle* h) {

@@ -728,6 +728,27 @@ static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const 
   c.M[(1 + D) * N + n] = c.M[(1 + D) * N + n] + C(acc[3]);
 }
 
+// One case: spreading and its application to the moments in one thread per
+// row (the sums of k_ib_spread, the updates of k_apply_forcing).
+template <class C>
+static __global__ void k_ib_spread_apply(int D, long long N, int n_rows, const int* row_ptr, const int* col,
+                                         const double* wt, const double* G, const int* cell_id, double* FU,
+                                         double* WQ, C* M) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  double acc[4];
+  spread_row(D, r, row_ptr, col, wt, G, acc);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < D) FU[(long long)r * D + a] = acc[a];
+  WQ[r] = acc[3];
+  const long long n = cell_id[r];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < D) M[(1 + a) * N + n] = M[(1 + a) * N + n] + C(0.5) * C(acc[a]);
+  M[(1 + D) * N + n] = M[(1 + D) * N + n] + C(acc[3]);
+}
+
 // wall loads: fixed-order block reduction (deterministic)
 static __global__ void k_wall_loads(int D, int NL, const double* G, const double* W, double* out) {
   __shared__ double sh[256][5];
