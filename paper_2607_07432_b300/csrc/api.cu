@@ -175,6 +175,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     }
     const char* tr = std::getenv("LBMIB_TILE_ROWS");
     if (tr) h->tile_rows = std::atoi(tr);
+    const char* ng = std::getenv("LBMIB_NO_GRAPH");
+    if (ng && ng[0] == '1') h->use_graph = 0;
     const char* bk = std::getenv("LBMIB_BC_SEPARATE");
     if (bk && bk[0] == '1') h->bc_in_kernel = 0;
   }
@@ -203,9 +205,15 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   return LBM_OK;
 }
 
+namespace {
+void drop_step_graph(lbm_handle* h);
+}
+
 void lbm_destroy(lbm_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  drop_step_graph(h);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   free_ib(h);
   void* ptrs[] = {h->f, h->f2, h->fcol, h->M, h->M2, h->E, h->P[0], h->P[1], h->A[0], h->A[1], h->feq_inf, h->d_bad};
   for (void* p : ptrs)
@@ -427,12 +435,81 @@ done:
   return s;
 }
 
+namespace {
+
+void drop_step_graph(lbm_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->graph_f = nullptr;
+}
+
+// Capture two steps (both buffer parities) of the current state as a graph;
+// the host-side buffer swaps of the two steps cancel, so the handle is back
+// at the captured parity afterwards.
+lbm_status capture_step_graph(lbm_handle* h) {
+  drop_step_graph(h);
+  // the legacy default stream cannot be captured: record on a private
+  // stream (the graph keeps no stream) and launch on the handle's stream
+  cudaStream_t run_st = h->st;
+  if (!run_st && !h->cap_st && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LBM_ECUDA, "capture stream");
+  }
+  cudaStream_t st = run_st ? run_st : h->cap_st;
+  const long long l0 = h->launches;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LBM_ECUDA, "graph capture begin");
+  }
+  h->st = st;
+  lbm_status s = h->ops->step(h);
+  if (!s) s = h->ops->step(h);
+  h->st = run_st;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  h->graph_launches = h->launches - l0;
+  h->launches = l0;
+  if (s || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return s ? s : fail(h, LBM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    h->gexec = nullptr;
+    cudaGetLastError();
+    return fail(h, LBM_ECUDA, "graph instantiate");
+  }
+  h->graph_f = h->f;
+  h->graph_geom = h->geom_version;
+  return LBM_OK;
+}
+
+}  // namespace
+
 lbm_status lbm_step(lbm_handle* h, int n_steps) {
   if (!h || n_steps < 0) return LBM_EINVAL;
   if (h->sticky) return (lbm_status)h->sticky;
-  for (int k = 0; k < n_steps; ++k) {
+  // pairs of steps replay a captured graph (fewer host launches for small
+  // grids); profiling runs, the unfused form and odd remainders step eagerly
+  const bool graphs = h->use_graph && h->use_fused && !h->prof;
+  int k = 0;
+  while (k < n_steps) {
+    if (graphs && h->stepped && n_steps - k >= 2) {
+      if (!h->gexec || h->graph_f != h->f || h->graph_geom != h->geom_version) {
+        lbm_status s = capture_step_graph(h);
+        if (s) return s;
+      }
+      if (cudaGraphLaunch(h->gexec, h->st) != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch");
+      h->launches += h->graph_launches;
+      k += 2;
+      continue;
+    }
     lbm_status s = h->ops->step(h);
     if (s) return s;
+    h->stepped = true;
+    ++k;
   }
   return LBM_OK;
 }

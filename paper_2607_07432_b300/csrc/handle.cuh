@@ -65,6 +65,16 @@ struct lbm_handle {
   int sticky = LBM_OK;
   int geom_version = 0;
   bool prof = false;
+  // two steps (both buffer parities) captured as a CUDA graph for
+  // lbm_step: valid while the buffers are at the captured parity and the
+  // geometry is unchanged
+  cudaGraphExec_t gexec = nullptr;
+  void* graph_f = nullptr;
+  int graph_geom = -1;
+  long long graph_launches = 0;
+  int use_graph = 1;
+  bool stepped = false;      // a first eager step has set the kernels' launch attributes
+  cudaStream_t cap_st = nullptr;  // capture stream when the handle runs on the legacy default stream
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   double prof_ms[lbmib_host::kProfClasses] = {0, 0, 0, 0, 0};

@@ -168,3 +168,33 @@ def test_naca_downscale_fp32_against_oracle():
     assert _rel_l2(fn, fn0) < 1e-4
     assert _rel_l2(ft, ft0) < 1e-4
     g.close()
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_step_graph_matches_eager_steps(lattice, monkeypatch):
+    """lbm_step replays pairs of steps from a captured CUDA graph; the state
+    equals eager stepping (LBMIB_NO_GRAPH=1) bit for bit, for even and odd
+    step counts and after the geometry is replaced."""
+    from paper_2607_07432_b300 import inputs, lbmib
+    if lattice == "D2Q9":
+        case = C.cylinder_c1()
+    else:
+        case = dict(lattice="D3Q19", shape=(40, 24, 24), mach=0.3, reynolds=100.0, ref_length=8.0,
+                    bc=[C.BC_IN, C.BC_OUT, C.BC_FF, C.BC_FF, C.BC_FF, C.BC_FF], method=2,
+                    geo=lambda th: inputs.icosphere((12.3, 12.1, 11.8), 8.0, 4, tbc=0, t_value=1.05 * th))
+    out = []
+    for off in ("0", "1"):
+        monkeypatch.setenv("LBMIB_NO_GRAPH", off)
+        s = lbmib.Solver(case["lattice"], "fp32", case["shape"], mach=case["mach"], reynolds=case["reynolds"],
+                         ref_length=case["ref_length"], method=case["method"], bc=case["bc"])
+        th = s.constants()["theta_inf"]
+        s.set_geometry(case["geo"](th))
+        s.step(7)
+        s.step(4)
+        s.set_geometry(case["geo"](th))
+        s.step(5)
+        s.check()
+        out.append(s.state())
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
