@@ -185,9 +185,8 @@ lbm_status forward(nop_net* net, int B) {
     switch (op.kind) {
       case kConv: {
         const Layer& l = net->L[op.layer];
-        const long long P = pixels(net, to.level, B);
-        dim3 grid((unsigned)((P + kTM - 1) / kTM), (unsigned)((l.coutp + kTN - 1) / kTN));
-        k_conv3x3<<<grid, 128, 0, net->st>>>(ti.act, l.Wt, l.bias, to.act, P, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
+        dim3 grid((unsigned)((long long)B * Ho * ((Wo + kRowPx - 1) / kRowPx)), (unsigned)((l.coutp + kTN - 1) / kTN));
+        k_conv3x3<<<grid, 128, 0, net->st>>>(ti.act, l.Wt, l.bias, to.act, B, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
         break;
       }
       case kPool:
@@ -232,8 +231,8 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
         k_bias_partial<<<nchunk, l.coutp, 0, net->st>>>(to.grad, net->part, P, l.coutp);
         k_sum_chunks<<<blocks(l.coutp), 256, 0, net->st>>>(net->part, nchunk, l.coutp, l.db);
         if (op.in != net->x_t || want_dx) {
-          dim3 grid((unsigned)((P + kTM - 1) / kTM), (unsigned)((l.cinp + kTN - 1) / kTN));
-          k_conv3x3<<<grid, 128, 0, net->st>>>(to.grad, l.Wf, nullptr, ti.grad, P, Hi, Wi, l.coutp, l.cinp, 0, 1);
+          dim3 grid((unsigned)((long long)B * Hi * ((Wi + kRowPx - 1) / kRowPx)), (unsigned)((l.cinp + kTN - 1) / kTN));
+          k_conv3x3<<<grid, 128, 0, net->st>>>(to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
         }
         break;
       }

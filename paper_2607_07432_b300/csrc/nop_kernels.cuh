@@ -15,10 +15,7 @@
 namespace lbmib {
 namespace nop {
 
-constexpr int kTM = 64;    // pixels per CTA tile (forward / input gradient)
 constexpr int kTN = 32;    // output channels per CTA tile
-constexpr int kKB = 4;     // k16 blocks staged per shared-memory fill
-constexpr int kLDA = 24;   // padded row of a 16-wide k block (bank-conflict free)
 constexpr int kWChunk = 1024;  // pixels per weight-gradient partial
 constexpr int kWPix = 64;      // pixels staged per fill in the weight gradient
 constexpr int kLDW = kWPix + 8;
@@ -45,88 +42,85 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 
 // Y[p][co] (+)= sum_{tap, ci} X[p + tap][ci] Wt[co][tap][ci] (+ bias[co]),
 // optionally followed by ReLU, zero padding outside the image.  GEMM view:
-// M = pixels, N = c_out, K = 9 c_in, one k16 block = (tap, 16 channels).
-// accumulate adds the previous content of Y (used for gradient sums; every
-// element is written by exactly one thread, so the sum is deterministic).
-// Cin and Cout are multiples of 16; the input gradient of a convolution is
-// this kernel applied to the output gradient with the flipped, transposed
-// weights Wf[ci][8 - tap][co] = Wt[co][tap][ci].
+// M = pixels, N = c_out, K = 9 c_in.  A CTA computes 64 consecutive
+// pixels of one image row for 32 output channels: per chunk of 32 input
+// channels it stages the three input rows (66 columns, BF16) and the
+// chunk's weights of all nine taps once, and every tap's A fragments are
+// read from that tile at a column offset.  accumulate adds the previous
+// content of Y (gradient sums; every element is written by one thread, so
+// the sum is deterministic).  Cin and Cout are multiples of 16; the input
+// gradient of a convolution is this kernel applied to the output gradient
+// with the flipped, transposed weights Wf[ci][8 - tap][co] = Wt[co][tap][ci].
+constexpr int kRowPx = 64;            // pixels per CTA tile (one image row)
+constexpr int kRowCols = kRowPx + 2;  // staged input columns
+constexpr int kChunk = 32;            // input channels per staged chunk
+constexpr int kChLd = 40;             // padded channel stride of a staged pixel (bank-conflict free)
+
 __global__ void __launch_bounds__(128) k_conv3x3(const float* __restrict__ X,
                                                  const __nv_bfloat16* __restrict__ Wt,
-                                                 const float* __restrict__ bias, float* __restrict__ Y,
-                                                 long long P, int H, int W, int Cin, int Cout, int relu,
-                                                 int accumulate) {
-  __shared__ __align__(16) __nv_bfloat16 As[kKB][kTM][kLDA];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kKB][kTN][kLDA];
+                                                 const float* __restrict__ bias, float* __restrict__ Y, int B,
+                                                 int H, int W, int Cin, int Cout, int relu, int accumulate) {
+  __shared__ __align__(16) __nv_bfloat16 In[3][kRowCols][kChLd];
+  __shared__ __align__(16) __nv_bfloat16 Ws[9][kTN][kChLd];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
-  const long long p0 = (long long)blockIdx.x * kTM;
+  const int tiles_x = (W + kRowPx - 1) / kRowPx;
+  int bid = blockIdx.x;
+  const int xt = bid % tiles_x;
+  bid /= tiles_x;
+  const int y = bid % H;
+  const int b = bid / H;
+  const int x0 = xt * kRowPx;
   const int n0 = blockIdx.y * kTN;
-  const int cblk = Cin >> 4;
-  const int nkb = 9 * cblk;
+  const int m0 = warp * 16;
   float acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-  // staging role for A: pixel row ar of the tile, channel half ah (8 channels)
-  const int ar = tid >> 1, ah = tid & 1;
-  const long long pa = p0 + ar;
-  const bool avalid = pa < P;
-  int ay = 0, ax = 0;
-  long long abase = 0;
-  if (avalid) {
-    const long long HW = (long long)H * W;
-    const long long b = pa / HW;
-    const int rem = (int)(pa - b * HW);
-    ay = rem / W;
-    ax = rem - ay * W;
-    abase = b * HW;
-  }
-  for (int kb0 = 0; kb0 < nkb; kb0 += kKB) {
-#pragma unroll
-    for (int k = 0; k < kKB; ++k) {
-      const int kb = kb0 + k;
+  for (int c0 = 0; c0 < Cin; c0 += kChunk) {
+    // input rows y-1..y+1, columns x0-1..x0+64, channels c0..c0+31, in units of 8 channels
+    for (int u = tid; u < 3 * kRowCols * 4; u += 128) {
+      const int r = u / (kRowCols * 4), rem = u - r * (kRowCols * 4);
+      const int col = rem >> 2, q = rem & 3;
+      const int yy = y + r - 1, xx = x0 + col - 1, c = c0 + q * 8;
       float v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = 0.f;
-      if (kb < nkb && avalid) {
-        const int tap = kb / cblk, c0 = (kb - tap * cblk) * 16 + ah * 8;
-        const int yy = ay + tap / 3 - 1, xx = ax + tap % 3 - 1;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-          const float4* src = reinterpret_cast<const float4*>(X + (abase + (long long)yy * W + xx) * Cin + c0);
-          const float4 u0 = src[0], u1 = src[1];
-          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
-          v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
-        }
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W && c < Cin) {
+        const float4* src = reinterpret_cast<const float4*>(X + (((long long)b * H + yy) * W + xx) * Cin + c);
+        const float4 u0 = src[0], u1 = src[1];
+        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
       }
       uint4 pk;
       pk.x = pack_bf16x2(v[0], v[1]);
       pk.y = pack_bf16x2(v[2], v[3]);
       pk.z = pack_bf16x2(v[4], v[5]);
       pk.w = pack_bf16x2(v[6], v[7]);
-      *reinterpret_cast<uint4*>(&As[k][ar][ah * 8]) = pk;
+      *reinterpret_cast<uint4*>(&In[r][col][q * 8]) = pk;
     }
-    for (int e = tid; e < kKB * kTN * 2; e += 128) {
-      const int k = e / (kTN * 2), r = (e >> 1) % kTN, h = e & 1;
-      const int kb = kb0 + k, co = n0 + r;
+    // weights of the 32 output channels, all taps, the chunk's channels
+    for (int u = tid; u < 9 * kTN * 4; u += 128) {
+      const int tap = u / (kTN * 4), rem = u - tap * (kTN * 4);
+      const int co = rem >> 2, q = rem & 3;
+      const int c = c0 + q * 8;
       uint4 w = make_uint4(0u, 0u, 0u, 0u);
-      if (kb < nkb && co < Cout) {
-        const int tap = kb / cblk, c0 = (kb - tap * cblk) * 16 + h * 8;
-        w = *reinterpret_cast<const uint4*>(Wt + ((long long)co * 9 + tap) * Cin + c0);
-      }
-      *reinterpret_cast<uint4*>(&Bs[k][r][h * 8]) = w;
+      if (n0 + co < Cout && c < Cin) w = *reinterpret_cast<const uint4*>(Wt + ((long long)(n0 + co) * 9 + tap) * Cin + c);
+      *reinterpret_cast<uint4*>(&Ws[tap][co][q * 8]) = w;
     }
     __syncthreads();
-    const int m = warp * 16;
 #pragma unroll
-    for (int k = 0; k < kKB; ++k) {
-      if (kb0 + k < nkb) {
-        const uint32_t a0 = lds32(&As[k][m + g][2 * tq]);
-        const uint32_t a1 = lds32(&As[k][m + g + 8][2 * tq]);
-        const uint32_t a2 = lds32(&As[k][m + g][2 * tq + 8]);
-        const uint32_t a3 = lds32(&As[k][m + g + 8][2 * tq + 8]);
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+      for (int kk = 0; kk < kChunk / 16; ++kk) {
+        const int kc = kk * 16 + 2 * tq;
+        const uint32_t a0 = lds32(&In[ky][m0 + g + kx][kc]);
+        const uint32_t a1 = lds32(&In[ky][m0 + g + 8 + kx][kc]);
+        const uint32_t a2 = lds32(&In[ky][m0 + g + kx][kc + 8]);
+        const uint32_t a3 = lds32(&In[ky][m0 + g + 8 + kx][kc + 8]);
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
-          const uint32_t b0 = lds32(&Bs[k][nt * 8 + g][2 * tq]);
-          const uint32_t b1 = lds32(&Bs[k][nt * 8 + g][2 * tq + 8]);
+          const uint32_t b0 = lds32(&Ws[tap][nt * 8 + g][kc]);
+          const uint32_t b1 = lds32(&Ws[tap][nt * 8 + g][kc + 8]);
           mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
         }
       }
@@ -140,14 +134,14 @@ __global__ void __launch_bounds__(128) k_conv3x3(const float* __restrict__ X,
     const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
 #pragma unroll
     for (int hr = 0; hr < 2; ++hr) {
-      const long long p = p0 + warp * 16 + g + hr * 8;
-      if (p >= P) continue;
+      const int x = x0 + m0 + g + hr * 8;
+      if (x >= W) continue;
       float v0 = acc[nt][2 * hr] + b0, v1 = acc[nt][2 * hr + 1] + b1;
       if (relu) {
         v0 = v0 > 0.f ? v0 : 0.f;
         v1 = v1 > 0.f ? v1 : 0.f;
       }
-      float2* dst = reinterpret_cast<float2*>(Y + p * Cout + co);
+      float2* dst = reinterpret_cast<float2*>(Y + (((long long)b * H + y) * W + x) * Cout + co);
       if (accumulate) {
         const float2 o = *dst;
         v0 = o.x + v0;

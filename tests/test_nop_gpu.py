@@ -130,8 +130,10 @@ def test_backward_matches_oracle(net, data):
     heavily, and BF16 operand rounding alone moves the oracle's own layer
     gradients by 0.4-20% from their FP64 values.  The GPU gradients are
     another such BF16 estimate, so each layer must be as close to the FP64
-    gradient as the BF16-operand oracle is (within 1.5x), and close to that
-    oracle.  The 16-channel test below holds the kernels to 1e-2."""
+    gradient as the BF16-operand oracle is (within 1.5x), and no farther
+    from that oracle than twice the oracle's own distance from FP64 (two
+    independent BF16 estimates).  The 16-channel test holds the kernels to
+    1e-2."""
     import torch
     x, dy, _ = data
     theta = net.params().astype(np.float64)
@@ -146,9 +148,9 @@ def test_backward_matches_oracle(net, data):
     for k, (a, b, c) in enumerate(zip(_layers(dp), _layers(g), _layers(g64))):
         name = onop.LAYER_NAMES[k]
         assert _rel(a, c) <= 1.5 * _rel(b, c) + 1e-3, (name, _rel(a, c), _rel(b, c))
-        assert _rel(a, b) < 0.1, (name, _rel(a, b))
+        assert _rel(a, b) <= 2.0 * _rel(b, c) + 1e-2, (name, _rel(a, b), _rel(b, c))
     assert _rel(dx, gx64) <= 1.5 * _rel(gx, gx64) + 1e-3
-    assert _rel(dx, gx) < 0.1
+    assert _rel(dx, gx) <= 2.0 * _rel(gx, gx64) + 1e-2
 
 
 def test_backward_is_bitwise_reproducible(net, data):
