@@ -198,3 +198,21 @@ def test_step_graph_matches_eager_steps(lattice, monkeypatch):
         s.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_moving_wall_couette_fp64_parity():
+    """Two immersed flat walls, the upper one moving (non-zero velocity
+    targets): FP64 path vs oracle after 300 steps, max relative error
+    <= 1e-12."""
+    from tests import test_oracle_couette as K
+    from paper_2607_07432_b300 import lbmib
+    sim, U = K._sim(2)
+    g = lbmib.Solver("D2Q9", "fp64", (K.NX, K.NY), bc=[C.BC_P] * 4, **K.config())
+    assert abs(g.constants()["u_mag"] - U) < 1e-15
+    g.set_geometry(K.geometry(U, g.constants()["theta_inf"]))
+    sim.run(300)
+    g.step(300)
+    f, E = g.state()
+    assert _maxrel(f, sim.f) < 1e-12
+    assert _maxrel(E, sim.E) < 1e-12
+    g.close()
