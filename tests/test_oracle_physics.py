@@ -149,3 +149,14 @@ def test_entropy_mode_decay():
     rate = -np.polyfit(np.arange(100, 300), np.log(amps[100:]), 1)[0]
     expect = prm.lam / prm.Cp * (2 * np.pi / nx) ** 2
     assert abs(rate / expect - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("theta,U", [(1.0, 0.0), (0.5, 0.1)])
+def test_shear_wave_second_order_convergence(theta, U):
+    """Grid convergence in diffusive scaling (steps ~ nx^2): the error of the
+    shear-wave decay rate falls by about 4 when the wavelength in cells
+    doubles, i.e. the scheme is second order in space (the order the paper
+    reports for its flow solver)."""
+    e24 = abs(_shear_rate(theta, U, mu=0.02, nx=24, steps=60) - 1.0)
+    e48 = abs(_shear_rate(theta, U, mu=0.02, nx=48, steps=240) - 1.0)
+    assert 3.0 < e24 / e48 < 5.0
