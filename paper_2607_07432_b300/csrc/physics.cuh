@@ -415,18 +415,23 @@ __device__ __forceinline__ C energy_face_flux_fast(const MacroAlong& MA, const F
   const Macro<C> m1 = MA(0), m2 = MA(1);
   const bool plus = C(0.5) * (m1.u[AX] + m2.u[AX]) >= C(0);
   const Macro<C> mo = MA(plus ? -1 : 2);
-  const Macro<C>& A = plus ? mo : m1;
-  const Macro<C>& B = plus ? m1 : m2;
-  const Macro<C>& Cc = plus ? m2 : mo;
-  const C pA = A.rho * cs2 * A.th, pB = B.rho * cs2 * B.th, pC = Cc.rho * cs2 * Cc.th;
-  const C uB = B.u[AX];
+  const C uB = plus ? m1.u[AX] : m2.u[AX];
   const C sg = uB > C(0) ? C(1) : (uB < C(0) ? C(-1) : C(0));
   const C eta = third<C>(C(2) * uB - sg);
   const C kap = C(0.25) * ((plus ? C(1) : C(-1)) - uB);
   const C al = kap * (C(1) + eta), be = kap * (C(1) - eta);
-  auto rec = [&](C a, C b, C c) { return b + al * (b - a) + be * (c - b); };
-  const C FH = rec((A.E + pA) * A.u[AX], (B.E + pB) * B.u[AX], (Cc.E + pC) * Cc.u[AX]);
-  const C Fr = rec(A.rho * A.u[AX], B.rho * B.u[AX], Cc.rho * Cc.u[AX]);
+  // the face value B + al (B - A) + be (Cc - B) as weights of the cells
+  // (outer, x, x + e): (A, B, Cc) = (outer, x, x + e) upwind of +, else
+  // (x, x + e, outer)
+  const C wB = C(1) + al - be;
+  const C wo = plus ? -al : be;
+  const C w1 = plus ? wB : -al;
+  const C w2 = plus ? be : wB;
+  auto rec = [&](C fo, C f1, C f2) { return wo * fo + w1 * f1 + w2 * f2; };
+  const C po = mo.rho * cs2 * mo.th, p1 = m1.rho * cs2 * m1.th, p2 = m2.rho * cs2 * m2.th;
+  const C FH = rec((mo.E + po) * mo.u[AX], (m1.E + p1) * m1.u[AX], (m2.E + p2) * m2.u[AX]);
+  const C ro = mo.rho * mo.u[AX], r1 = m1.rho * m1.u[AX], r2 = m2.rho * m2.u[AX];
+  const C Fr = rec(ro, r1, r2);
   C k1 = C(0), k2 = C(0);
 #pragma unroll
   for (int b = 0; b < D; ++b) {
@@ -435,11 +440,10 @@ __device__ __forceinline__ C energy_face_flux_fast(const MacroAlong& MA, const F
   }
   const C hk = C(0.5) * ((ph.Cp * m1.th + ph.Cp * m2.th) - C(0.5) * (k1 + k2));
   C FE = FH + hk * (Frho - Fr);
-  const C rA = A.rho * A.u[AX], rB = B.rho * B.u[AX], rC = Cc.rho * Cc.u[AX];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
-    const C Fb = rec(rA * A.u[b] + (AX == b ? pA : C(0)), rB * B.u[b] + (AX == b ? pB : C(0)),
-                     rC * Cc.u[b] + (AX == b ? pC : C(0)));
+    const C Fb = rec(ro * mo.u[b] + (AX == b ? po : C(0)), r1 * m1.u[b] + (AX == b ? p1 : C(0)),
+                     r2 * m2.u[b] + (AX == b ? p2 : C(0)));
     const C ub = C(0.5) * (m1.u[b] + m2.u[b]);
     FE = FE + ub * (Fm[b] - Fb);
   }
