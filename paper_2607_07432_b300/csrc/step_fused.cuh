@@ -138,8 +138,9 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   const bool interior = cx >= 1 && cx <= TX && cy >= 1 && cy <= TY && gx < g.n[0] && gy < g.n[1];
   const int wx = g.wrap(0, gx), wy = g.wrap(1, gy);
 
-  auto mslot = [&](int z) { return D == 3 ? ((z % RM) + RM) % RM : 0; };
-  auto fslot = [&](int z) { return D == 3 ? ((z % RF) + RF) % RF : 0; };
+  // ring slots of plane z (z >= z0 - 3 >= -3 here): unsigned remainders
+  auto mslot = [&](int z) { return D == 3 ? (int)((unsigned)(z + 4 * RM) % (unsigned)RM) : 0; };
+  auto fslot = [&](int z) { return D == 3 ? (int)((unsigned)(z + 4 * RF) % (unsigned)RF) : 0; };
   auto halo2_node = [&](int k, int gz) {
     const int kx = k % HX2, ky = k / HX2;
     return g.lin(g.wrap(0, x0 + kx - 2), g.wrap(1, y0 + ky - 2), gz);
