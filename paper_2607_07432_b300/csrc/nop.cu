@@ -93,6 +93,12 @@ long long pixels(const nop_net* net, int level, int batch) {
 
 unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// weight-gradient partials of a level: kWUnits row segments of kRowPx pixels each
+int wgrad_chunks(int B, int H, int W) {
+  const long long units = (long long)B * H * ((W + kRowPx - 1) / kRowPx);
+  return (int)((units + kWUnits - 1) / kWUnits);
+}
+
 int add_tensor(nop_net* net, int level, int C) {
   Tensor t;
   t.level = level;
@@ -223,13 +229,14 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
         const Layer& l = net->L[op.layer];
         const long long P = pixels(net, to.level, B);
         if (op.relu) k_relu_mask<<<blocks(P * to.C), 256, 0, net->st>>>(to.act, to.grad, P * to.C);
-        const int nchunk = (int)((P + kWChunk - 1) / kWChunk);
-        dim3 wg((unsigned)nchunk, (unsigned)((l.coutp + 31) / 32), (unsigned)(9 * ((l.cinp + 31) / 32)));
-        k_conv3x3_wgrad<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, P, Hi, Wi, l.cinp, l.coutp);
+        const int nchunk = wgrad_chunks(B, Hi, Wi);
+        dim3 wg((unsigned)nchunk, (unsigned)((l.coutp + 31) / 32), (unsigned)((l.cinp + 31) / 32));
+        k_conv3x3_wgrad<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp);
         const long long len = (long long)l.coutp * 9 * l.cinp;
         k_sum_chunks<<<blocks(len), 256, 0, net->st>>>(net->part, nchunk, len, l.dW);
-        k_bias_partial<<<nchunk, l.coutp, 0, net->st>>>(to.grad, net->part, P, l.coutp);
-        k_sum_chunks<<<blocks(l.coutp), 256, 0, net->st>>>(net->part, nchunk, l.coutp, l.db);
+        const int nbias = (int)((P + kWChunk - 1) / kWChunk);
+        k_bias_partial<<<nbias, l.coutp, 0, net->st>>>(to.grad, net->part, P, l.coutp);
+        k_sum_chunks<<<blocks(l.coutp), 256, 0, net->st>>>(net->part, nbias, l.coutp, l.db);
         if (op.in != net->x_t || want_dx) {
           dim3 grid((unsigned)((long long)B * Hi * ((Wi + kRowPx - 1) / kRowPx)), (unsigned)((l.cinp + kTN - 1) / kTN));
           k_conv3x3<<<grid, 128, 0, net->st>>>(to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
@@ -329,8 +336,10 @@ lbm_status nop_create(const nop_config* cfg, nop_net** out) {
   for (const Op& op : net->ops) {
     if (op.kind != kConv) continue;
     const Layer& l = net->L[op.layer];
-    const long long nchunk = (pixels(net, net->T[op.out].level, B) + kWChunk - 1) / kWChunk;
-    net->part_len = std::max(net->part_len, nchunk * ((long long)l.coutp * 9 * l.cinp + l.coutp));
+    const int lv = net->T[op.out].level;
+    const long long nw = wgrad_chunks(B, cfg->height >> lv, cfg->width >> lv);
+    const long long nb = (pixels(net, lv, B) + kWChunk - 1) / kWChunk;
+    net->part_len = std::max(net->part_len, std::max(nw * l.coutp * 9 * l.cinp, nb * l.coutp));
   }
   for (Layer& l : net->L) {
     const long long n = (long long)l.coutp * 9 * l.cinp;

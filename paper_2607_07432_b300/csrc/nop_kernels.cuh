@@ -17,8 +17,6 @@ namespace nop {
 
 constexpr int kTN = 32;    // output channels per CTA tile
 constexpr int kWChunk = 1024;  // pixels per weight-gradient partial
-constexpr int kWPix = 64;      // pixels staged per fill in the weight gradient
-constexpr int kLDW = kWPix + 8;
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -152,95 +150,115 @@ __global__ void __launch_bounds__(128) k_conv3x3(const float* __restrict__ X,
   }
 }
 
-// Weight-gradient partials of one pixel chunk:
+// Weight-gradient partials:
 // part[chunk][co][tap][ci] = sum_{p in chunk} G[p][co] X[p + tap][ci].
-// GEMM view: M = c_out (tile 32), N = 16-channel blocks of one tap (tile
-// 32 channels), K = pixels of the chunk.  grid = (chunks, Cout/32,
-// 9 ceil(Cin/32)).  The chunk partials are added in chunk order by
-// k_sum_chunks.
+// GEMM view per tap: M = c_out (tile 32), N = c_in (tile 32), K = pixels.
+// A chunk is kWUnits consecutive row segments of 64 pixels (segment u =
+// (b H + y) tiles_x + xt).  For each segment the CTA stages G^T (32 c_out x
+// 64 pixels) and the three input rows it meets, transposed (32 c_in x 66
+// columns) in two copies, the second shifted by one column so that every
+// tap's operand pairs start on an even column, and accumulates all nine taps.
+// The chunk partials are added in chunk order by k_sum_chunks.
+constexpr int kWUnits = 16;
+constexpr int kWLd = 72;  // padded row (bf16) of the transposed tiles
+
 __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const float* __restrict__ G,
                                                        const float* __restrict__ X,
-                                                       float* __restrict__ part, long long P, int H,
-                                                       int W, int Cin, int Cout) {
-  __shared__ __align__(16) __nv_bfloat16 As[32][kLDW];  // [co][pixel]
-  __shared__ __align__(16) __nv_bfloat16 Bs[32][kLDW];  // [ci][pixel]
+                                                       float* __restrict__ part, int B, int H, int W, int Cin,
+                                                       int Cout) {
+  __shared__ __align__(16) __nv_bfloat16 Gs[32][kWLd];        // [co][pixel]
+  __shared__ __align__(16) __nv_bfloat16 Xs[2][3][32][kWLd];  // [shift][row][ci][column]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
   const int chunk = blockIdx.x;
-  const int m0 = blockIdx.y * 32;
-  const int cib = (Cin + 31) / 32;
-  const int tap = blockIdx.z / cib;
-  const int c00 = (blockIdx.z - tap * cib) * 32;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int m0 = blockIdx.y * 32;   // c_out tile
+  const int c00 = blockIdx.z * 32;  // c_in tile
   const int wm = warp & 1, wn = warp >> 1;
-  float acc[2][4];
+  const int tiles_x = (W + kRowPx - 1) / kRowPx;
+  const long long n_units = (long long)B * H * tiles_x;
+  float acc[9][2][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-  const long long HW = (long long)H * W;
-  const long long pbeg = (long long)chunk * kWChunk;
-  const int r = tid >> 1, h = tid & 1;  // staging: pixel r, channel half h (16 channels)
-  for (int s = 0; s < kWChunk; s += kWPix) {
-    const long long p = pbeg + s + r;
-    float ga[16], xb[16];
+  for (int tp = 0; tp < 9; ++tp)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) ga[j] = xb[j] = 0.f;
-    if (p < P) {
-      const int co0 = m0 + h * 16;
-      if (co0 < Cout) {
-        const float4* src = reinterpret_cast<const float4*>(G + p * Cout + co0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 u = src[q];
-          ga[4 * q] = u.x; ga[4 * q + 1] = u.y; ga[4 * q + 2] = u.z; ga[4 * q + 3] = u.w;
-        }
-      }
-      const long long b = p / HW;
-      const int rem = (int)(p - b * HW);
-      const int y = rem / W, x = rem - (rem / W) * W;
-      const int yy = y + dy, xx = x + dx;
-      const int ci0 = c00 + h * 16;
-      if (ci0 < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W) {
-        const float4* src = reinterpret_cast<const float4*>(X + (b * HW + (long long)yy * W + xx) * Cin + ci0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 u = src[q];
-          xb[4 * q] = u.x; xb[4 * q + 1] = u.y; xb[4 * q + 2] = u.z; xb[4 * q + 3] = u.w;
-        }
-      }
+    for (int i = 0; i < 2; ++i) acc[tp][i][0] = acc[tp][i][1] = acc[tp][i][2] = acc[tp][i][3] = 0.f;
+  for (int uu = 0; uu < kWUnits; ++uu) {
+    const long long unit = (long long)chunk * kWUnits + uu;
+    if (unit >= n_units) break;
+    const int xt = (int)(unit % tiles_x);
+    const long long r0 = unit / tiles_x;
+    const int y = (int)(r0 % H);
+    const long long b = r0 / H;
+    const int x0 = xt * kRowPx;
+    // G^T of the segment: 64 pixels x 32 c_out, in units of 4 channels
+    for (int e = tid; e < kRowPx * 8; e += 128) {
+      const int px = e >> 3, q = e & 7;
+      const int x = x0 + px, co = m0 + q * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (x < W && co < Cout) v = *reinterpret_cast<const float4*>(G + ((b * H + y) * W + x) * Cout + co);
+      Gs[q * 4 + 0][px] = __float2bfloat16_rn(v.x);
+      Gs[q * 4 + 1][px] = __float2bfloat16_rn(v.y);
+      Gs[q * 4 + 2][px] = __float2bfloat16_rn(v.z);
+      Gs[q * 4 + 3][px] = __float2bfloat16_rn(v.w);
     }
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      As[h * 16 + j][r] = __float2bfloat16_rn(ga[j]);
-      Bs[h * 16 + j][r] = __float2bfloat16_rn(xb[j]);
+    // input rows y-1..y+1, columns x0-1..x0+64 (column c at index c), 32 c_in
+    for (int e = tid; e < 3 * kRowCols * 8; e += 128) {
+      const int r = e / (kRowCols * 8), rem = e - r * (kRowCols * 8);
+      const int col = rem >> 3, q = rem & 7;
+      const int yy = y + r - 1, xx = x0 + col - 1, ci = c00 + q * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W && ci < Cin)
+        v = *reinterpret_cast<const float4*>(X + ((b * H + yy) * W + xx) * Cin + ci);
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+      const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+      Xs[0][r][q * 4 + 0][col] = h0;
+      Xs[0][r][q * 4 + 1][col] = h1;
+      Xs[0][r][q * 4 + 2][col] = h2;
+      Xs[0][r][q * 4 + 3][col] = h3;
+      if (col >= 1) {
+        Xs[1][r][q * 4 + 0][col - 1] = h0;
+        Xs[1][r][q * 4 + 1][col - 1] = h1;
+        Xs[1][r][q * 4 + 2][col - 1] = h2;
+        Xs[1][r][q * 4 + 3][col - 1] = h3;
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < kWPix / 16; ++kk) {
-      const int kc = kk * 16 + 2 * tq;
-      const uint32_t a0 = lds32(&As[wm * 16 + g][kc]);
-      const uint32_t a1 = lds32(&As[wm * 16 + g + 8][kc]);
-      const uint32_t a2 = lds32(&As[wm * 16 + g][kc + 8]);
-      const uint32_t a3 = lds32(&As[wm * 16 + g + 8][kc + 8]);
+    for (int kk = 0; kk < kRowPx / 16; ++kk) {
+      const int kc = kk * 16 + 2 * tq;  // pixel of the operand pair
+      const uint32_t a0 = lds32(&Gs[wm * 16 + g][kc]);
+      const uint32_t a1 = lds32(&Gs[wm * 16 + g + 8][kc]);
+      const uint32_t a2 = lds32(&Gs[wm * 16 + g][kc + 8]);
+      const uint32_t a3 = lds32(&Gs[wm * 16 + g + 8][kc + 8]);
 #pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int n = wn * 16 + nt * 8 + g;
-        mma_bf16(acc[nt], a0, a1, a2, a3, lds32(&Bs[n][kc]), lds32(&Bs[n][kc + 8]));
+      for (int tp = 0; tp < 9; ++tp) {
+        const int ky = tp / 3, kx = tp % 3;
+        // pixel p meets input column p + kx: even offsets from copy 0, odd from copy 1
+        const int sh = kx & 1, off = kx - sh;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int n = wn * 16 + nt * 8 + g;
+          const uint32_t b0 = lds32(&Xs[sh][ky][n][kc + off]);
+          const uint32_t b1 = lds32(&Xs[sh][ky][n][kc + off + 8]);
+          mma_bf16(acc[tp][nt], a0, a1, a2, a3, b0, b1);
+        }
       }
     }
     __syncthreads();
   }
   float* out = part + (long long)chunk * Cout * 9 * Cin;
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    const int ci = c00 + wn * 16 + nt * 8 + 2 * tq;
-    if (ci >= Cin) continue;
+  for (int tp = 0; tp < 9; ++tp)
 #pragma unroll
-    for (int hr = 0; hr < 2; ++hr) {
-      const int co = m0 + wm * 16 + g + hr * 8;
-      if (co >= Cout) continue;
-      *reinterpret_cast<float2*>(out + ((long long)co * 9 + tap) * Cin + ci) =
-          make_float2(acc[nt][2 * hr], acc[nt][2 * hr + 1]);
+    for (int nt = 0; nt < 2; ++nt) {
+      const int ci = c00 + wn * 16 + nt * 8 + 2 * tq;
+      if (ci >= Cin) continue;
+#pragma unroll
+      for (int hr = 0; hr < 2; ++hr) {
+        const int co = m0 + wm * 16 + g + hr * 8;
+        if (co >= Cout) continue;
+        *reinterpret_cast<float2*>(out + ((long long)co * 9 + tp) * Cin + ci) =
+            make_float2(acc[tp][nt][2 * hr], acc[tp][nt][2 * hr + 1]);
+      }
     }
-  }
 }
 
 // Bias-gradient partials: part[chunk][co] = sum_{p in chunk} G[p][co], pixels
