@@ -153,6 +153,22 @@ lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* rh
  * previous-step auxiliaries are reset as for a fresh start. */
 lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, const double* rhoE);
 
+/* Checkpoint: write the complete time-stepping state of the handle to a
+ * file (populations in their storage format, the carried moments or rho E,
+ * and the previous-step auxiliaries rho(1-theta) and the a^F deviator), so
+ * that lbm_load_state on a handle of the same lattice, precision, grid and
+ * step form resumes bit for bit.  The immersed-body geometry is not part of
+ * the file: set it again with ib_set_geometry before loading.  LBM_EINVAL
+ * for a NULL path, LBM_ECUDA / LBM_ESTATE when the file cannot be written.
+ * (The paper has no counterpart: a service of the library.) */
+lbm_status lbm_save_state(lbm_handle* h, const char* path);
+
+/* Read a file written by lbm_save_state into the handle.  LBM_ESTATE when
+ * the file is missing, truncated or written by a handle of another lattice,
+ * precision, grid or step form; the handle is unchanged then.  Clears a
+ * sticky LBM_ENAN. */
+lbm_status lbm_load_state(lbm_handle* h, const char* path);
+
 /* Set the state to the equilibrium of given fields (warm start): rho (N),
  * u (D*N), T (N). */
 lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho,

@@ -595,6 +595,105 @@ lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, cons
   return s;
 }
 
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int version, lattice, precision, nx, ny, nz, fused, pad;
+  long long N;
+};
+
+// device arrays of the stepping state and their byte sizes
+int state_arrays(lbm_handle* h, void** ptr, size_t* bytes) {
+  const size_t N = (size_t)h->g.N;
+  int k = 0;
+  ptr[k] = h->f;
+  bytes[k++] = N * h->Q * h->ssize;
+  if (h->use_fused) {
+    ptr[k] = h->M;
+    bytes[k++] = N * (h->D + 2) * h->csize;
+  } else {
+    ptr[k] = h->E;
+    bytes[k++] = N * h->csize;
+  }
+  ptr[k] = h->P[h->cur];
+  bytes[k++] = N * h->csize;
+  ptr[k] = h->A[h->cur];
+  bytes[k++] = N * h->NDEV * h->csize;
+  return k;
+}
+
+StateHeader state_header(lbm_handle* h) {
+  StateHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "LBMIBST1", 8);
+  hd.version = 1;
+  hd.lattice = h->cfg.lattice;
+  hd.precision = h->cfg.precision;
+  hd.nx = h->g.n[0];
+  hd.ny = h->g.n[1];
+  hd.nz = h->g.n[2];
+  hd.fused = h->use_fused;
+  hd.N = h->g.N;
+  return hd;
+}
+
+}  // namespace
+
+lbm_status lbm_save_state(lbm_handle* h, const char* path) {
+  if (!h || !path) return LBM_EINVAL;
+  void* ptr[4];
+  size_t bytes[4];
+  const int n = state_arrays(h, ptr, bytes);
+  const StateHeader hd = state_header(h);
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(h, LBM_ESTATE, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1;
+  std::vector<unsigned char> host;
+  CK(cudaStreamSynchronize(h->st));
+  for (int k = 0; k < n && ok; ++k) {
+    host.resize(bytes[k]);
+    if (cudaMemcpy(host.data(), ptr[k], bytes[k], cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(fp);
+      return fail(h, LBM_ECUDA, "state copy to host");
+    }
+    ok = std::fwrite(host.data(), 1, bytes[k], fp) == bytes[k];
+  }
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) return fail(h, LBM_ESTATE, std::string("cannot write ") + path);
+  return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_handle* h, const char* path) {
+  if (!h || !path) return LBM_EINVAL;
+  void* ptr[4];
+  size_t bytes[4];
+  const int n = state_arrays(h, ptr, bytes);
+  const StateHeader want = state_header(h);
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(h, LBM_ESTATE, std::string("cannot open ") + path);
+  StateHeader hd;
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(&hd, &want, sizeof(hd)) != 0) {
+    std::fclose(fp);
+    return fail(h, LBM_ESTATE, "state file of another lattice, precision, grid or step form");
+  }
+  std::vector<std::vector<unsigned char>> host(n);
+  for (int k = 0; k < n; ++k) {
+    host[k].resize(bytes[k]);
+    if (std::fread(host[k].data(), 1, bytes[k], fp) != bytes[k]) {
+      std::fclose(fp);
+      return fail(h, LBM_ESTATE, "state file truncated");
+    }
+  }
+  std::fclose(fp);
+  CK(cudaStreamSynchronize(h->st));
+  for (int k = 0; k < n; ++k)
+    if (cudaMemcpy(ptr[k], host[k].data(), bytes[k], cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(h, LBM_ECUDA, "state copy to device");
+  h->sticky = LBM_OK;
+  return LBM_OK;
+}
+
 lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho, const double* u,
                           const double* T) {
   if (!h || !rho || !u || !T) return LBM_EINVAL;

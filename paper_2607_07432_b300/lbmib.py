@@ -30,7 +30,7 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", 
            "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_case", "lbm_batch_step",
            "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
-           "lbm_batch_autotune"]
+           "lbm_batch_autotune", "lbm_save_state", "lbm_load_state"]
 
 
 class Config(ct.Structure):
@@ -58,6 +58,8 @@ def load():
     lib.lbm_last_error.restype = ct.c_char_p
     lib.lbm_launch_count.restype = ct.c_longlong
     lib.lbm_create.argtypes = [ct.POINTER(Config), ct.POINTER(ct.c_void_p)]
+    lib.lbm_save_state.argtypes = [ct.c_void_p, ct.c_char_p]
+    lib.lbm_load_state.argtypes = [ct.c_void_p, ct.c_char_p]
     lib.lbm_batch_last_error.restype = ct.c_char_p
     lib.lbm_batch_last_error.argtypes = [ct.c_void_p]
     lib.lbm_batch_destroy.argtypes = [ct.c_void_p]
@@ -226,6 +228,12 @@ class Solver:
         u = np.ascontiguousarray(u, dtype=np.float64)
         T = np.ascontiguousarray(T, dtype=np.float64)
         self._check(lib().lbm_set_fields(self.h, 0, _ptr(rho), _ptr(u), _ptr(T)))
+
+    def save_state(self, path):
+        self._check(lib().lbm_save_state(self.h, str(path).encode()))
+
+    def load_state(self, path):
+        self._check(lib().lbm_load_state(self.h, str(path).encode()))
 
     def wall_loads(self, per_point=False):
         force = (ct.c_double * 3)()
