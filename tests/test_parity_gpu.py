@@ -216,3 +216,30 @@ def test_moving_wall_couette_fp64_parity():
     assert _maxrel(f, sim.f) < 1e-12
     assert _maxrel(E, sim.E) < 1e-12
     g.close()
+
+
+def test_rotating_cylinder_with_heat_flux_fp64_parity():
+    """Rotating wall (velocity targets omega x r on every Lagrangian point)
+    and a non-zero Neumann temperature condition (prescribed wall-normal
+    gradient, Eq. virtualneu): FP64 path vs oracle after 200 steps, max
+    relative error <= 1e-12."""
+    from paper_2607_07432_b300 import inputs
+    case = C.small_cylinder_periodic()
+
+    def geo(th):
+        g = inputs.cylinder((15.3, 16.4), 10.0, 32, tbc=1, t_value=0.004)
+        r = g["X"] - np.array([15.3, 16.4])
+        omega = 0.01
+        g["u_target"] = np.stack([-omega * r[:, 1], omega * r[:, 0]], axis=1)
+        return g
+    case["geo"] = geo
+    sim, g0 = C.make_oracle(case)
+    g = C.make_gpu(case, "fp64", g0)
+    sim.run(200)
+    g.step(200)
+    f, E = g.state()
+    assert _maxrel(f, sim.f) < 1e-12
+    assert _maxrel(E, sim.E) < 1e-12
+    wl = g.wall_loads(per_point=True)
+    assert np.max(np.abs(wl["F"] - sim.last_loads["F"])) < 1e-12 * max(1.0, np.abs(sim.last_loads["F"]).max())
+    g.close()
