@@ -246,7 +246,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps);
 lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps);
 /* Wait for the batch stream. */
 lbm_status lbm_batch_sync(lbm_batch* b);
-/* Fused-launch plan: tile_rows 0 (default tile) or 16 (2D FP32 only), and
+/* Fused-launch plan: tile_rows 0 (default tile), 16 or 32 (2D FP32 only), and
  * schedule 0 = case-major, 1 = round-robin over cases, 2 = largest first. */
 lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule);
 lbm_status lbm_batch_get_plan(const lbm_batch* b, int* tile_rows, int* schedule);

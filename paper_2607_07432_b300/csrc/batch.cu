@@ -142,7 +142,7 @@ lbm_status lbm_batch_case(lbm_batch* b, int i, lbm_handle** h) {
 }
 
 lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule) {
-  if (!b || (tile_rows != 0 && tile_rows != 16) || schedule < 0 || schedule > 2) return LBM_EINVAL;
+  if (!b || (tile_rows != 0 && tile_rows != 16 && tile_rows != 32) || schedule < 0 || schedule > 2) return LBM_EINVAL;
   b->plan.tile_rows = tile_rows;
   b->plan.schedule = schedule;
   b->plan.built = false;
@@ -267,8 +267,8 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, d
     for (size_t i = 0; i < sv.bufs.size(); ++i)
       cudaMemcpyAsync(sv.bufs[i].first, sv.copies[i], sv.bufs[i].second, cudaMemcpyDeviceToDevice, b->st);
   };
-  const int rows[2] = {0, 16};
-  const int nrows = (p.cases[0]->D == 2 && p.cases[0]->csize == 4) ? 2 : 1;
+  const int rows[3] = {0, 16, 32};
+  const int nrows = (p.cases[0]->D == 2 && p.cases[0]->csize == 4) ? 3 : 1;
   double best = 1e300;
   int best_r = 0, best_s = 0;
   cudaEvent_t e0, e1;

@@ -284,6 +284,9 @@ struct Engine {
         if (b->tile_rows == 16) {
           batch_tiles<16>(h, tx[k], ty[k], tz[k]);
           done = true;
+        } else if (b->tile_rows == 32) {
+          batch_tiles<32>(h, tx[k], ty[k], tz[k]);
+          done = true;
         }
       }
       if (!done) batch_tiles<0>(h, tx[k], ty[k], tz[k]);
@@ -448,6 +451,9 @@ struct Engine {
     if constexpr (L::D == 2 && sizeof(C) == 4) {
       if (b->tile_rows == 16) {
         batch_launch<16>(b, parity);
+        done = true;
+      } else if (b->tile_rows == 32) {
+        batch_launch<32>(b, parity);
         done = true;
       }
     }

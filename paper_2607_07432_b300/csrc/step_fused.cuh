@@ -505,14 +505,18 @@ inline void launch_fused_tile(const Grid& g, const FusedArgs<S, C>& a, const Phy
 }
 
 // zchunk: planes per CTA along z (3D); tile_rows selects the halo-1 tile
-// height of the 3D FP32 kernel (8: two CTAs per SM, 12: staged inputs,
-// 16: one CTA per SM), 0 = default
+// height: 3D FP32 8 (two CTAs per SM), 12 (staged inputs), 0 = 16 (one CTA
+// per SM); 2D FP32 0 = 8, 16 or 32 (1024 threads)
 template <class L, class S, class C>
 inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
                          int zchunk, int tile_rows) {
   if constexpr (L::D == 3 && sizeof(C) == 4) {
     if (tile_rows == 8) return launch_fused_tile<L, S, C, 8>(g, a, ph, st, zchunk);
     if (tile_rows == 12) return launch_fused_tile<L, S, C, 12>(g, a, ph, st, zchunk);
+  }
+  if constexpr (L::D == 2 && sizeof(C) == 4) {
+    if (tile_rows == 16) return launch_fused_tile<L, S, C, 16>(g, a, ph, st, zchunk);
+    if (tile_rows == 32) return launch_fused_tile<L, S, C, 32>(g, a, ph, st, zchunk);
   }
   launch_fused_tile<L, S, C, 0>(g, a, ph, st, zchunk);
 }

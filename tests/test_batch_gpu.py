@@ -45,7 +45,7 @@ def test_batched_equals_individual(precision):
         s.set_geometry(geo)
         b.case(k).set_geometry(geo)
         solo.append(s)
-    for tile_rows, sched in [(0, 0), (16, 1), (0, 2)] if precision == "fp32" else [(0, 0)]:
+    for tile_rows, sched in [(0, 0), (16, 1), (0, 2), (32, 2)] if precision == "fp32" else [(0, 0)]:
         b.set_plan(tile_rows, sched)
         b.step(5)   # graph path (2 + 2) and one eager step
         for s in solo:
