@@ -690,8 +690,8 @@ static __global__ void k_ib_spread(int D, int n_rows, const int* row_ptr, const 
 }
 
 // Spreading and its application to the moments, several cases in one
-// launch: the same sums as k_ib_spread and the same updates as
-// k_apply_forcing, for one row per thread.
+// launch: the same sums and updates as k_ib_spread_apply, one row per
+// thread.
 template <class C>
 struct SpreadCaseDesc {
   int D;
@@ -728,8 +728,9 @@ static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const 
   c.M[(1 + D) * N + n] = c.M[(1 + D) * N + n] + C(acc[3]);
 }
 
-// One case: spreading and its application to the moments in one thread per
-// row (the sums of k_ib_spread, the updates of k_apply_forcing).
+// One case: spreading (the sums of k_ib_spread) and its application to the
+// predicted moments in place, rho u += f_u / 2 and rho E += w + q on the
+// row's node (Sec. 2.2, reading Q15), one thread per row.
 template <class C>
 static __global__ void k_ib_spread_apply(int D, long long N, int n_rows, const int* row_ptr, const int* col,
                                          const double* wt, const double* G, const int* cell_id, double* FU,

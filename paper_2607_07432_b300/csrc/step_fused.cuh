@@ -521,18 +521,6 @@ inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>&
   launch_fused_tile<L, S, C, 0>(g, a, ph, st, zchunk);
 }
 
-// IB spreading applied to the predicted moments in place: rho u += f_u / 2,
-// rho E += w + q on the forced nodes (Sec. 2.2, reading Q15)
-template <class C>
-__global__ void k_apply_forcing(int D, long long N, int n_rows, const int* cell_id, const double* FU,
-                                const double* WQ, C* M) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_rows) return;
-  const long long n = cell_id[r];
-  for (int d = 0; d < D; ++d) M[(1 + d) * N + n] = M[(1 + d) * N + n] + C(0.5) * C(FU[(long long)r * D + d]);
-  M[(1 + D) * N + n] = M[(1 + D) * N + n] + C(WQ[r]);
-}
-
 // predicted moments rho, rho u, rho E of every node from populations and E
 template <class L, class S, class C>
 __global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
@@ -554,54 +542,8 @@ __global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
   M[(1 + D) * g.N + n] = E[n];
 }
 
-// boundary faces also refresh the predicted moments of the nodes they set
-template <class L, class S, class C>
-__global__ void k_bc_outlet_m(Grid g, S* f, C* M, int axis, int side) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
-  if (t >= g.n[a1] * g.n[a2]) return;
-  int c[3];
-  c[a1] = t % g.n[a1];
-  c[a2] = t / g.n[a1];
-  const int nax = g.n[axis];
-  c[axis] = side ? nax - 1 : 0;
-  const long long dst = g.lin(c[0], c[1], c[2]);
-  c[axis] = side ? nax - 2 : 1;
-  const long long src = g.lin(c[0], c[1], c[2]);
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) f[(long long)i * g.N + dst] = f[(long long)i * g.N + src];
-#pragma unroll
-  for (int k = 0; k < L::D + 2; ++k) M[k * g.N + dst] = M[k * g.N + src];
-}
-
-template <class L, class S, class C>
-__global__ void k_bc_equilibrium_m(Grid g, S* f, C* M, int axis, int side, const C* feq_inf, C E_inf) {
-  constexpr int D = L::D;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
-  if (t >= g.n[a1] * g.n[a2]) return;
-  int c[3];
-  c[a1] = t % g.n[a1];
-  c[a2] = t / g.n[a1];
-  c[axis] = side ? g.n[axis] - 1 : 0;
-  const long long dst = g.lin(c[0], c[1], c[2]);
-  C r = C(0), j[3] = {C(0), C(0), C(0)};
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i]);
-    const C v = load_pop<L, S, C>(f, i, g.N, dst);
-    r += v;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
-  }
-  M[dst] = r;
-#pragma unroll
-  for (int a = 0; a < D; ++a) M[(1 + a) * g.N + dst] = j[a];
-  M[(1 + D) * g.N + dst] = E_inf;
-}
-
-// all domain faces in one launch (reading Q24): a node on an inlet or far-field
+// All domain faces in one launch (reading Q24); the faces also refresh the
+// predicted moments of the nodes they set: a node on an inlet or far-field
 // face takes the free-stream equilibrium; a node on an outlet face and on no
 // equilibrium face copies its inner neighbour along the outlet axis.  This is
 // the outlet-copy-then-equilibrium order with the edges resolved up front.
