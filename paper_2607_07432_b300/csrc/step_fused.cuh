@@ -3,8 +3,8 @@
 //
 // Each CTA owns a TX x TY column of the (x, y) plane and marches along z
 // (2.5D blocking).  Shared memory holds two rings of planes:
-//   * corrected macroscopic fields (rho, u, theta, rho E') of five planes
-//     z-2..z+2 with a halo of two nodes in x and y (MUSCL stencils and the
+//   * corrected macroscopic fields (rho, u, theta, rho E') of four planes
+//     z-1..z+2 with a halo of two nodes in x and y (MUSCL stencils and the
 //     velocity gradients of halo nodes), and
 //   * post-collision populations of three planes z-1..z+1 with a halo of one
 //     node (pull streaming and the face-crossing flux tables).
@@ -52,7 +52,7 @@ struct FusedArgs {
 
 // Tile: one thread per node of the halo-1 region HX1 x HY1 (the collision
 // region), interior TX x TY = (HX1-2) x (HY1-2).  The D3Q19 FP32 tile uses
-// 512 threads and about 190 KB of shared memory.
+// 512 threads and about 180 KB of shared memory.
 template <class L, class C, int HY = 0>
 struct FusedTile {
   static constexpr int HX1 = sizeof(C) == 8 ? 16 : 32;
@@ -67,7 +67,10 @@ struct FusedLayout {
   static constexpr int HX1 = TX + 2, HY1 = TY + 2, NH1 = HX1 * HY1;
   static constexpr int HX2 = TX + 4, HY2 = TY + 4, NH2 = HX2 * HY2;
   static constexpr int NT = NH1;
-  static constexpr int RM = D == 3 ? 5 : 1;   // macro planes
+  // macro planes: iteration z reads planes z-1..z+2; plane z-2 was last
+  // read (z face of plane z-1) before the barrier that opens iteration z,
+  // so its slot takes plane z+2
+  static constexpr int RM = D == 3 ? 4 : 1;
   static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
   static constexpr int NMF = D + 3;           // rho, u (D), theta, E'
   // 3D FP32: the next plane's inputs are staged in shared memory with
