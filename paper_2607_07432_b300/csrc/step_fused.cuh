@@ -263,21 +263,28 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   };
   // 3D FP32 with the default tile: the populations and auxiliaries of the
   // next collision plane are loaded into registers one plane ahead, so their
-  // latency overlaps the streaming and energy stage of the current plane
+  // latency overlaps the streaming and energy stage of the current plane.
+  // The loads are issued in two groups (populations [LO, HI), the
+  // auxiliaries with the last group): a warp whose load queue is full
+  // stalls, so half of them go out before the pull stream and half after
+  // it, where the face fluxes give the queue time to drain.
   constexpr bool RP = D == 3 && !STG && !exact && sizeof(S) == 4;
+  constexpr int QH = (Q + 1) / 2;  // populations in the first group
   S rf[RP ? Q : 1];
   C rP = C(0);
   C rA[RP ? L::NDEV : 1];
   unsigned char rfl = 0;
-  auto prefetch_regs = [&](int z) {
+  auto prefetch_regs = [&](int z, auto LO, auto HI, bool aux) {
     if constexpr (RP) {
       const long long n = g.lin(wx, wy, g.wrap(2, z));
 #pragma unroll
-      for (int i = 0; i < Q; ++i) rf[i] = a.f_in[(long long)i * N + n];
-      rP = a.Pp[n];
+      for (int i = decltype(LO)::value; i < decltype(HI)::value; ++i) rf[i] = a.f_in[(long long)i * N + n];
+      if (aux) {
+        rP = a.Pp[n];
 #pragma unroll
-      for (int q = 0; q < L::NDEV; ++q) rA[q] = a.Ap[q * N + n];
-      rfl = a.forced ? a.forced[n] : 0;
+        for (int q = 0; q < L::NDEV; ++q) rA[q] = a.Ap[q * N + n];
+        rfl = a.forced ? a.forced[n] : 0;
+      }
     }
   };
   // collision of this thread's node of plane z (halo-1 region, one node per thread)
@@ -373,7 +380,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     collide_plane(z0 - 1, false, false);
     collide_plane(z0, false, false);
     prefetch(z0 + 2, z0 + 1);
-    prefetch_regs(z0 + 1);
+    prefetch_regs(z0 + 1, std::integral_constant<int, 0>{}, std::integral_constant<int, Q>{}, true);
     prefetch_moments(z0 + 2);
     __syncthreads();
   }
@@ -413,7 +420,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       collide_plane(z + 1, true, true);
       __syncthreads();
       prefetch(z + 3, z + 2);
-      prefetch_regs(z + 2);
+      prefetch_regs(z + 2, std::integral_constant<int, 0>{}, std::integral_constant<int, QH>{}, false);
       prefetch_moments(z + 3);
     } else {
       load_macros(0, false);
@@ -456,6 +463,9 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       a.M_out[n] = rho;
 #pragma unroll
       for (int d = 0; d < D; ++d) a.M_out[(1 + d) * N + n] = j[d];
+    }
+    if constexpr (D == 3) {
+      prefetch_regs(z + 2, std::integral_constant<int, QH>{}, std::integral_constant<int, Q>{}, true);
     }
     // Eq. energy face fluxes, each face once
     if (xface) Fx[(z & 1) * NH1 + t] = face(std::integral_constant<int, 0>{}, z, 0);
