@@ -264,12 +264,12 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   // 3D FP32 with the default tile: the populations and auxiliaries of the
   // next collision plane are loaded into registers one plane ahead, so their
   // latency overlaps the streaming and energy stage of the current plane.
-  // The loads are issued in two groups (populations [LO, HI), the
-  // auxiliaries with the last group): a warp whose load queue is full
-  // stalls, so half of them go out before the pull stream and half after
-  // it, where the face fluxes give the queue time to drain.
+  // The loads are issued in three groups (populations [LO, HI), the
+  // auxiliaries with the last): a warp whose load queue is full stalls, so
+  // one group goes out before the pull stream, one after it and one after
+  // the x face flux, where the arithmetic gives the queue time to drain.
   constexpr bool RP = D == 3 && !STG && !exact && sizeof(S) == 4;
-  constexpr int QH = (Q + 1) / 2;  // populations in the first group
+  constexpr int QA = (Q + 2) / 3, QB = (2 * Q + 1) / 3;  // population groups [0,QA) [QA,QB) [QB,Q)
   S rf[RP ? Q : 1];
   C rP = C(0);
   C rA[RP ? L::NDEV : 1];
@@ -420,7 +420,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       collide_plane(z + 1, true, true);
       __syncthreads();
       prefetch(z + 3, z + 2);
-      prefetch_regs(z + 2, std::integral_constant<int, 0>{}, std::integral_constant<int, QH>{}, false);
+      prefetch_regs(z + 2, std::integral_constant<int, 0>{}, std::integral_constant<int, QA>{}, false);
       prefetch_moments(z + 3);
     } else {
       load_macros(0, false);
@@ -459,17 +459,22 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         });
       }
     }
+    if constexpr (D == 3) {
+      prefetch_regs(z + 2, std::integral_constant<int, QA>{}, std::integral_constant<int, QB>{}, false);
+    }
+    // Eq. energy face fluxes, each face once
+    if (xface) Fx[(z & 1) * NH1 + t] = face(std::integral_constant<int, 0>{}, z, 0);
+    if constexpr (D == 3) {
+      prefetch_regs(z + 2, std::integral_constant<int, QB>{}, std::integral_constant<int, Q>{}, true);
+    }
+    if (yface) Fy[(z & 1) * NH1 + t] = face(std::integral_constant<int, 1>{}, z, 0);
+    // the predicted moments of step n+1, stored late so that the stores
+    // overlap the z face flux
     if (interior) {
       a.M_out[n] = rho;
 #pragma unroll
       for (int d = 0; d < D; ++d) a.M_out[(1 + d) * N + n] = j[d];
     }
-    if constexpr (D == 3) {
-      prefetch_regs(z + 2, std::integral_constant<int, QH>{}, std::integral_constant<int, Q>{}, true);
-    }
-    // Eq. energy face fluxes, each face once
-    if (xface) Fx[(z & 1) * NH1 + t] = face(std::integral_constant<int, 0>{}, z, 0);
-    if (yface) Fy[(z & 1) * NH1 + t] = face(std::integral_constant<int, 1>{}, z, 0);
     if constexpr (D == 3) {
       if (interior) Fz_pend = face(std::integral_constant<int, 2>{}, z, xs);
     }
