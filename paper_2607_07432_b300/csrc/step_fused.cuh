@@ -261,14 +261,15 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     m.E = src[(2 + D) * NH2 + k];
     return m;
   };
-  // 3D FP32 with the default tile: the populations and auxiliaries of the
-  // next collision plane are loaded into registers one plane ahead, so their
-  // latency overlaps the streaming and energy stage of the current plane.
+  // 3D FP32 arithmetic (FP32, FP16 or BF16 storage): the populations and
+  // auxiliaries of the next collision plane are loaded into registers one
+  // plane ahead, so their latency overlaps the streaming and energy stage
+  // of the current plane.
   // The loads are issued in three groups (populations [LO, HI), the
   // auxiliaries with the last): a warp whose load queue is full stalls, so
   // one group goes out before the pull stream, one after it and one after
   // the x face flux, where the arithmetic gives the queue time to drain.
-  constexpr bool RP = D == 3 && !STG && !exact && sizeof(S) == 4;
+  constexpr bool RP = D == 3 && !STG && !exact;
   constexpr int QA = (Q + 2) / 3, QB = (2 * Q + 1) / 3;  // population groups [0,QA) [QA,QB) [QB,Q)
   S rf[RP ? Q : 1];
   C rP = C(0);
