@@ -105,6 +105,16 @@ __device__ __forceinline__ void dev_expand(const C* s, C T[3][3]) {
   }
 }
 
+// quotient a / b: the hardware approximation (2 ulp) in FP32, exact otherwise
+template <class C>
+__device__ __forceinline__ C fdiv(C a, C b) {
+  if constexpr (sizeof(C) == 4) {
+    return __fdividef(a, b);
+  } else {
+    return a / b;
+  }
+}
+
 // HRR collision at one node (Eq. LB with dt = 1, Eqs. fi, af2, fneq, pi2,
 // pi3).  fbar: post-stream populations of the node; m: corrected macros;
 // du, aC: gradients; P_prev, dAFp: rho(1-theta) and the deviator of a^F of
@@ -223,6 +233,9 @@ __device__ __forceinline__ void collide(const C* fbar, const Macro<C>& m, const 
 //         + (w_i - delta_0i) rho (theta - 1),
 // algebraically identical to f^eq + (1 - 1/tau) f^neq + F/2 but with about a
 // third of the arithmetic (every population reuses the same coefficients).
+// Divisions by the constants c_s^2 and D are products with their
+// reciprocals, and the two data-dependent quotients (tau, 1/tau) use the
+// hardware division (2 ulp), which avoids the checked IEEE division.
 template <class L, class C>
 __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, const C du[3][3],
                                              const C aC[3][3], C P_prev, const C* dAFp, const C* fu,
@@ -242,8 +255,8 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
 #pragma unroll
     for (int b = 0; b < D; ++b) aF[a][b] = aC[a][b] + fu[a] * m.u[b] + fu[b] * m.u[a] + (a == b ? trace_term : C(0));
   const C th_m = ph.theta_tau ? m.th : C(1);
-  const C tau_bar = ph.mu / (m.rho * cs2 * th_m) + C(0.5);
-  const C omega = C(1) - C(1) / tau_bar;
+  const C tau_bar = fdiv(ph.mu, m.rho * cs2 * th_m) + C(0.5);
+  const C omega = C(1) - fdiv(C(1), tau_bar);
   const C fd = (C(1) - ph.sigma) * m.rho * cs2 * th_m * tau_bar;
   C Fp[3][3];
   dev_expand<L, C>(dAFp, Fp);
@@ -270,7 +283,7 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int b = a; b < D; ++b) {
-      C dev = S2[a][b] - m.rho * m.u[a] * m.u[b] - (a == b ? trS / C(D) : C(0));
+      C dev = S2[a][b] - m.rho * m.u[a] * m.u[b] - (a == b ? trS * C(1.0 / D) : C(0));
       const C S = du[a][b] + du[b][a] - (a == b ? (C(2) / C(D)) * div : C(0));
       Pi[a][b] = ph.sigma * (dev + C(0.5) * Fp[a][b]) - fd * S;
       Pi[b][a] = Pi[a][b];
@@ -278,7 +291,7 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
   // coefficients
   C A1[3], B2[3][3];
 #pragma unroll
-  for (int a = 0; a < D; ++a) A1[a] = (m.rho * m.u[a] + C(0.5) * fu[a]) / cs2;
+  for (int a = 0; a < D; ++a) A1[a] = (m.rho * m.u[a] + C(0.5) * fu[a]) * C(1.0 / kCs2);
   const C inv2cs4 = C(1) / (C(2) * cs2 * cs2);
   C trB = C(0);
 #pragma unroll
@@ -341,7 +354,7 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
     sfor<decltype(A)::value, D>([&](auto B) {
       constexpr int a = decltype(A)::value, b = decltype(B)::value;
       constexpr int k = dev_slot<L>(a, b);
-      if constexpr (k >= 0) dAF_new[k] = aF[a][b] - (a == b ? tr / C(D) : C(0));
+      if constexpr (k >= 0) dAF_new[k] = aF[a][b] - (a == b ? tr * C(1.0 / D) : C(0));
     });
   });
 }

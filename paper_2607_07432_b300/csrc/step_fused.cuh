@@ -97,11 +97,6 @@ __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int 
   return -1;
 }
 
-template <class C>
-__device__ __forceinline__ C recip(C x) {
-  return C(1) / x;
-}
-
 // 4-byte asynchronous global -> shared copy (sm_80+ LDGSTS) and its fences
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -181,7 +176,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       }
       th = (E / rho - C(0.5) * uu) / ph.Cv;
     } else {
-      const C ir = recip(rho);
+      const C ir = fdiv(C(1), rho);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         u[d] = jm[d] * ir;
