@@ -483,8 +483,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
   const int lane = threadIdx.x & 31;
   const int l0 = (blk * kIBWarps + wib) * NP;
   if (l0 >= s.NL) return;
-  // Eq. int2 / Eq. int1 at P: every lane evaluates stencil slots of each of
-  // the warp's points
+  // Eq. int2: every lane evaluates stencil slots of each of the warp's points
 #pragma unroll 1
   for (int p = 0; p < NP; ++p) {
     const int l = l0 + p;
@@ -527,13 +526,19 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
         for (int q = 0; q < NV; ++q) stage[wib][p * NV + q][k] = v[q];
       }
     }
-    if (lane < KP) {
+  }
+  // Eq. int1 at the projection points: lane (p, k) evaluates slot k of
+  // point p, all of the warp's points in one pass
+  {
+    const int p = lane >> 3, k = lane & 7;
+    const int l = l0 + p;
+    if (k < KP && l < s.NL) {
       double pv[D + 1];
 #pragma unroll
       for (int q = 0; q < D + 1; ++q) pv[q] = 0.0;
-      const int n = s.psten_node[l * KP + lane];
+      const int n = s.psten_node[l * KP + k];
       if (n >= 0) {
-        const double w = s.psten_w[l * KP + lane];
+        const double w = s.psten_w[l * KP + k];
         double rho, j[3], u[3], T;
         node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
 #pragma unroll
@@ -541,7 +546,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
         pv[D] = T * w;
       }
 #pragma unroll
-      for (int q = 0; q < D + 1; ++q) pstage[wib][p * (D + 1) + q][lane] = pv[q];
+      for (int q = 0; q < D + 1; ++q) pstage[wib][p * (D + 1) + q][k] = pv[q];
     }
   }
   __syncwarp();
