@@ -70,7 +70,11 @@ struct Engine {
     const long long tiles = (long long)((h->g.n[0] + Lay::TX - 1) / Lay::TX) * ((h->g.n[1] + Lay::TY - 1) / Lay::TY);
     const int nz = h->g.n[2];
     long long best = -1;
-    for (int zc = 4; zc <= std::max(4, nz); ++zc) {
+    // chunks longer than 24 planes measured slower on the 256x192x192 sphere
+    // (24: 0.893, 28: 0.912, 32: 0.959 ms per step) although they need fewer
+    // waves, so the search stops there
+    constexpr int kMaxZChunk = 24;
+    for (int zc = 4; zc <= std::max(4, std::min(nz, kMaxZChunk)); ++zc) {
       const long long ctas = tiles * ((nz + zc - 1) / zc);
       const long long waves = (ctas + (long long)sms * occ - 1) / ((long long)sms * occ);
       const long long cost = waves * (zc + 2);
