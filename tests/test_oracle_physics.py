@@ -160,3 +160,59 @@ def test_shear_wave_second_order_convergence(theta, U):
     e24 = abs(_shear_rate(theta, U, mu=0.02, nx=24, steps=60) - 1.0)
     e48 = abs(_shear_rate(theta, U, mu=0.02, nx=48, steps=240) - 1.0)
     assert 3.0 < e24 / e48 < 5.0
+
+
+def _sound_rate(theta, U, lattice="D2Q9", nx=48, steps=300, mu=0.02, gamma=1.4, use_ac=True, A=1e-5):
+    """Decay rate of a right-running sound wave (wavelength nx) measured on
+    the characteristic variable u' + p'/(rho c), divided by the linearized
+    Navier-Stokes rate (1/2) (nu_L + (gamma - 1) alpha) k^2 with the
+    longitudinal viscosity nu_L = 2 (1 - 1/D) nu of a traceless stress with
+    zero bulk viscosity and the thermal diffusivity alpha = lambda/(rho C_p)."""
+    D = 2 if lattice == "D2Q9" else 3
+    shape = (nx,) + (2,) * (D - 1)
+    prm = _periodic(lattice, shape, mu=mu, theta=theta, U=(U, 0.0, 0.0), gamma=gamma, use_ac=use_ac)
+    sim = lbm.Sim(prm)
+    zyx = tuple(reversed(shape))
+    c = np.sqrt(prm.gamma * prm.R * theta)
+    s = np.broadcast_to(np.sin(2 * np.pi * np.arange(nx) / nx), zyx)
+    u = np.stack([U + c * A * s] + [np.zeros(zyx)] * (D - 1))
+    _set(sim, 1.0 + A * s, u, theta * (1.0 + (prm.gamma - 1.0) * A * s))
+    amps = []
+    for _ in range(steps):
+        sim.step()
+        _, uu, _, p = sim.fields()
+        w = (uu[0].reshape(-1, nx)[0] - U) + (p.reshape(-1, nx)[0] - p.mean()) / c
+        amps.append(np.abs(np.fft.rfft(w))[1] * 2 / nx)
+    amps = np.array(amps)
+    n0 = steps // 3
+    rate = -np.polyfit(np.arange(n0, steps), np.log(amps[n0:]), 1)[0]
+    k = 2 * np.pi / nx
+    expect = 0.5 * (2.0 * (1.0 - 1.0 / D) * mu + (prm.gamma - 1.0) * prm.lam / prm.Cp) * k * k
+    return rate / expect
+
+
+@pytest.mark.parametrize("lattice,theta", [("D2Q9", 1.0), ("D2Q9", 0.5), ("D3Q19", 1.0)])
+def test_sound_wave_attenuation_at_rest(lattice, theta):
+    """Linearized N-S at rest: a sound wave decays at (1/2)(nu_L + (gamma-1)
+    alpha) k^2.  This pins the traceless projection with delta/D (Q4: nu_L =
+    nu in 2D, 4/3 nu in 3D), the zero bulk viscosity given by the trace terms
+    of Eq. af2, and the coupling of the LB pressure to the finite-difference
+    energy equation (the thermal part of the attenuation)."""
+    if lattice == "D2Q9":
+        r = _sound_rate(theta, 0.0)
+    else:
+        r = _sound_rate(theta, 0.0, lattice="D3Q19", nx=32, steps=150)
+    assert abs(r - 1.0) < 0.05
+
+
+def test_sound_wave_galilean_invariance_needs_aC():
+    """At theta = 1 and gamma close to 1 (the energy equation barely feeds
+    back into the pressure) the sound attenuation of the LB momentum part is
+    the same at rest and in frames moving at U = 0.1, -0.1 and 0.2: the
+    lattice-dependent force moment a^C (reading Q6) removes the defect of
+    the diagonal third moment.  Without a^C the moving-frame rate is off by
+    more than 30% (at U = 0.2 the wave grows)."""
+    rest = _sound_rate(1.0, 0.0, gamma=1.02)
+    for U in (0.1, -0.1, 0.2):
+        assert abs(_sound_rate(1.0, U, gamma=1.02) / rest - 1.0) < 0.06
+    assert abs(_sound_rate(1.0, 0.1, gamma=1.02, use_ac=False) / rest - 1.0) > 0.3
