@@ -28,7 +28,10 @@ design notes of the repository):
       Eq. af2 make the trace exactly the zero-bulk-viscosity one (linearized
       Chapman-Enskog), so no theta correction is left for a^C.  PARITY
       UNPINNED against the paper; pinned by physics tests (shear viscosity
-      equals mu at theta != 1 and in a moving frame; linear stability).
+      equals mu at theta != 1 and in a moving frame; sound attenuation the
+      same at rest and in moving frames at theta = 1, which fails without
+      a^C; linear stability).  Open: at theta != 1 the longitudinal
+      attenuation in a moving frame differs from the rest value.
   Q7  spatial derivatives are 2nd-order central; time derivative of
       rho(1-theta) is the backward difference with the stored previous value.
   Q8  the F_i(t - dt) term of Eq. pi2 enters through its traceless second
