@@ -238,6 +238,7 @@ struct Engine {
     a.An = (C*)h->A[1 - c0];
     a.forced = h->has_ib ? h->forced : nullptr;
     a.cell_id = h->cell_id;
+    a.row_of_node = h->has_ib ? h->row_of_node : nullptr;
     a.n_rows = h->n_rows;
     a.FU = h->FU;
     a.bc_fused = bc_in_kernel(h) ? 1 : 0;

@@ -35,6 +35,7 @@ struct FusedArgs {
   C* An;               // NDEV*N
   const unsigned char* forced;  // N flags (nullptr: no body)
   const int* cell_id;  // n_rows, ascending
+  const int* row_of_node;  // N: CSR row of a forced node, -1 otherwise (nullptr: search cell_id)
   int n_rows;
   const double* FU;    // n_rows*D
   // The two x faces applied in the kernel (bc_fused != 0; their nodes are
@@ -325,9 +326,13 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     }
     C fu[3] = {C(0), C(0), C(0)};
     if (is_forced) {
-      const int r = find_row_dev(a.cell_id, a.n_rows, (int)n);
+      // the node's CSR row: from the per-node map when there is one (one
+      // load), else by binary search over the ascending row nodes
+      const int r = a.row_of_node ? a.row_of_node[n] : find_row_dev(a.cell_id, a.n_rows, (int)n);
+      if (r >= 0) {
 #pragma unroll
-      for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
+        for (int d = 0; d < D; ++d) fu[d] = C(a.FU[(long long)r * D + d]);
+      }
     }
     C fcol[Q], Pn, dAFn[L::NDEV];
     if constexpr (exact) {
