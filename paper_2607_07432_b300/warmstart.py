@@ -1,7 +1,7 @@
 """Learned warm start for 2D cases: the solver generates its own steady
 fields (batched launch), the neural operator is trained on them on the GPU,
 and a new case starts from the network's field instead of uniform flow.
-The converged plain solve stays the judge: time-to-steady is the number of
+The converged plain solve stays the reference: time-to-steady is the number of
 steps until the drag stays within a tolerance of the drag that the
 uniform-start run converges to.
 
@@ -135,7 +135,7 @@ def steps_to_steady(hist, target, every, tol=1e-3):
 
 def compare(net, case, steps, every, tol=1e-3):
     """Uniform start vs warm start on one case.  The uniform run's final
-    drag is the converged answer both are judged against."""
+    drag is the converged answer both are measured against."""
     import torch
     s = solver_for(case)
     torch.cuda.synchronize()
