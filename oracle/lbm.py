@@ -61,6 +61,8 @@ CS2 = L.CS2
 
 BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD = 0, 1, 2, 3
 TAU_THETA, TAU_LITERAL = 0, 1
+# use_ac: True = reading Q6; AC_ADVECTIVE = Q6 plus the advective theta term (candidate, off by default)
+AC_ADVECTIVE = 2
 
 
 def theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, dim):
@@ -253,6 +255,15 @@ def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
             return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
         for a in range(D):
             aC[a][a] = -cdiff(rho * (u[a] * u[a] * u[a]), a)
+        if prm.use_ac == AC_ADVECTIVE:
+            # candidate reading, off by default: the advective parts of the
+            # theta-defect, d_a(rho u_a (1-theta)), and of the explicit
+            # -c_s^2 d_t[rho(1-theta)] term are not Galilean invariant; their
+            # xx weights 1 and c_s^2, halved because the force moment enters
+            # the collision at half weight
+            P_ = rho * (1.0 - theta)
+            for a in range(D):
+                aC[a][a] = aC[a][a] + 0.5 * (1.0 + CS2) * u[a] * cdiff(P_, a)
     # Eq. af2
     aF = [[None] * D for _ in range(D)]
     for a in range(D):

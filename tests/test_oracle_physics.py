@@ -226,3 +226,19 @@ def test_sound_wave_galilean_invariance_needs_aC_3d():
     rest = _sound_rate(1.0, 0.0, **kw)
     assert abs(_sound_rate(1.0, 0.1, **kw) / rest - 1.0) < 0.06
     assert abs(_sound_rate(1.0, 0.1, use_ac=False, **kw) / rest - 1.0) > 0.15
+
+
+def test_sound_wave_theta_defect_and_advective_candidate():
+    """At theta != 1 the reading Q6 of a^C leaves the longitudinal attenuation
+    frame-dependent (theta = 0.5, U = 0.1: about twice the rest value, and a
+    wave running against the flow slowly grows).  The candidate reading
+    lbm.AC_ADVECTIVE (off by default) adds (1 + c_s^2)/2 u_a d_a[rho(1-theta)]
+    to a^C_aa and restores the invariance in both directions, on D2Q9 and
+    D3Q19."""
+    rest = _sound_rate(0.5, 0.0, gamma=1.02)
+    assert _sound_rate(0.5, 0.1, gamma=1.02) / rest > 1.5
+    for U in (0.1, -0.1):
+        assert abs(_sound_rate(0.5, U, gamma=1.02, use_ac=lbm.AC_ADVECTIVE) / rest - 1.0) < 0.04
+    kw = dict(lattice="D3Q19", nx=32, steps=150, gamma=1.02)
+    rest3 = _sound_rate(0.5, 0.0, **kw)
+    assert abs(_sound_rate(0.5, 0.1, use_ac=lbm.AC_ADVECTIVE, **kw) / rest3 - 1.0) < 0.04
