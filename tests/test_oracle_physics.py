@@ -106,11 +106,13 @@ def test_shear_wave_viscosity_3d():
     assert abs(_shear_rate(0.6, 0.1, lattice="D3Q19", steps=180) - 1.0) < 0.02
 
 
+@pytest.mark.parametrize("use_ac", [True, lbm.AC_ADVECTIVE])
 @pytest.mark.parametrize("lattice,shape,theta,U", [("D2Q9", (16, 16), 0.3, 0.1), ("D3Q19", (10, 10, 10), 0.2, 0.09)])
-def test_linear_stability_at_low_theta(lattice, shape, theta, U):
+def test_linear_stability_at_low_theta(lattice, shape, theta, U, use_ac):
     """Seeded small noise on a uniform flow at theta < 1 does not grow: the
-    scheme under readings Q6/Q9 has no explicit anti-diffusion."""
-    prm = _periodic(lattice, shape, mu=0.015, theta=theta, U=(U, 0.0, 0.0))
+    scheme under readings Q6/Q9 has no explicit anti-diffusion (nor with the
+    candidate advective a^C term)."""
+    prm = _periodic(lattice, shape, mu=0.015, theta=theta, U=(U, 0.0, 0.0), use_ac=use_ac)
     D = prm.lat.D
     sim = lbm.Sim(prm)
     rng = np.random.default_rng(0)
