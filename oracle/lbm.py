@@ -20,18 +20,30 @@ design notes of the repository):
       N_k = sum_i w_i H3r_k,i^2 (2 c_s^6 for the '+' and 6 c_s^6 for the '-'
       D3Q19 combinations) in place of the printed single 1/(6 c_s^6).
   Q4  the trace projection in Eq. pi2 uses delta/D (delta/3 in 3D as printed).
-  Q6  a^C (Eq. af2, only cited as the lattice-dependent component) =
-      -delta_ab d_a(rho u_a^3): the divergence of the diagonal third-order
-      equilibrium moment that D2Q9/D3Q19 cannot represent.  With the literal
-      tau_LB = nu/c_s^2 the lattice already gives the shear stress
-      -tau rho c_s^2 (grad u + grad u^T), and the explicit delta_ab terms of
-      Eq. af2 make the trace exactly the zero-bulk-viscosity one (linearized
-      Chapman-Enskog), so no theta correction is left for a^C.  PARITY
-      UNPINNED against the paper; pinned by physics tests (shear viscosity
-      equals mu at theta != 1 and in a moving frame; sound attenuation the
-      same at rest and in moving frames at theta = 1, which fails without
-      a^C; linear stability).  Open: at theta != 1 the longitudinal
-      attenuation in a moving frame differs from the rest value.
+  Q6  a^C (Eq. af2, only cited as the lattice-dependent component) is the
+      second-order Hermite force moment that cancels, in the Chapman-Enskog
+      expansion, the part of the momentum-flux relaxation the lattice gets
+      wrong.  With the equilibrium of Eq. feq the lattice's third moment is
+      c_s^2 rho (u_a d_bg + u_b d_ag + u_g d_ab) plus the off-diagonal
+      rho u u u terms, not the Maxwellian's p/rho = c_s^2 theta form and not
+      the diagonal rho u_a^3.  Expanding d_t Pi^(0) + d_g Q^(0) with the
+      Euler equations then leaves, besides rho c_s^2 (grad u + grad u^T)
+      (which with the literal tau_LB = nu/c_s^2 is the right shear stress
+      at any theta), the trace terms Eq. af2 already carries explicitly
+      ((2/D) rho c_s^2 div u, -c_s^2 d_t[rho(1-theta)]) and two terms a^C
+      must remove:
+          a^C_ab = c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
+      P = rho(1-theta) (central differences, Q7).  The first part is the
+      advective remainder of the theta defect (zero at theta = 1 up to the
+      perturbation of theta), the second the diagonal cubic defect.
+      PARITY UNPINNED against the paper (only cited); pinned by physics
+      tests: sound attenuation equal at rest and in frames moving along and
+      against the wave at theta = 1, 0.5 and 0.25 (D2Q9, D3Q19), no
+      transverse velocity generated by a sound wave in a frame moving
+      across it (the off-diagonal part), shear viscosity mu at any theta
+      and frame, linear stability at low theta.  use_ac: AC_FULL (default),
+      AC_CUBIC (the cubic term only: frame-dependent attenuation at
+      theta != 1), AC_OFF.
   Q7  spatial derivatives are 2nd-order central; time derivative of
       rho(1-theta) is the backward difference with the stored previous value.
   Q8  the F_i(t - dt) term of Eq. pi2 enters through its traceless second
@@ -61,8 +73,8 @@ CS2 = L.CS2
 
 BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD = 0, 1, 2, 3
 TAU_THETA, TAU_LITERAL = 0, 1
-# use_ac: True = reading Q6; AC_ADVECTIVE = Q6 plus the advective theta term (candidate, off by default)
-AC_ADVECTIVE = 2
+# a^C readings (Q6): off, the diagonal cubic defect only, full (default)
+AC_OFF, AC_CUBIC, AC_FULL = 0, 1, 2
 
 
 def theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, dim):
@@ -93,7 +105,7 @@ class Params:
 
     def __init__(self, lattice, shape, mach, reynolds, ref_length, prandtl=0.71,
                  gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98,
-                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=True, mu=None):
+                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=AC_FULL, mu=None):
         self.lat = L.get(lattice)
         D = self.lat.D
         self.shape = tuple(int(s) for s in shape)  # (nx, ny[, nz])
@@ -244,26 +256,19 @@ def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
     div = sum(du[a][a] for a in range(D))
     P = rho * (1.0 - theta)
     dPdt = P - P_prev
-    # a^C (reading Q6): the lattice-dependent part of the force moment, the
-    # divergence of the diagonal third-order moment the lattice cannot carry
-    # (sum f^eq c_a^3 = rho u_a instead of rho u_a^3 + 3 rho c_s^2 theta u_a;
-    # with tau_LB = nu / c_s^2 the theta part of the defect is already
-    # absorbed by the explicit trace terms of Eq. af2)
+    # a^C (reading Q6): c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
+    # P = rho(1-theta), central differences
     aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
     if prm.use_ac:
         def cdiff(g, b):
             return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
         for a in range(D):
             aC[a][a] = -cdiff(rho * (u[a] * u[a] * u[a]), a)
-        if prm.use_ac == AC_ADVECTIVE:
-            # candidate reading, off by default: the advective parts of the
-            # theta-defect, d_a(rho u_a (1-theta)), and of the explicit
-            # -c_s^2 d_t[rho(1-theta)] term are not Galilean invariant; their
-            # xx weights 1 and c_s^2, halved because the force moment enters
-            # the collision at half weight
-            P_ = rho * (1.0 - theta)
+        if prm.use_ac == AC_FULL:
+            dP = [cdiff(rho * (1.0 - theta), b) for b in range(D)]
             for a in range(D):
-                aC[a][a] = aC[a][a] + 0.5 * (1.0 + CS2) * u[a] * cdiff(P_, a)
+                for b in range(D):
+                    aC[a][b] = aC[a][b] + CS2 * (u[a] * dP[b] + u[b] * dP[a])
     # Eq. af2
     aF = [[None] * D for _ in range(D)]
     for a in range(D):
