@@ -235,9 +235,19 @@ def regularized_neq(lat, u, Pi):
 
 
 def deviator(lat, T):
+    """Traceless part of a symmetric tensor, as carried between steps
+    (reading Q8): the independent components T_ab - delta_ab tr/D, and the
+    last diagonal component from the traceless condition (minus the sum of
+    the other diagonal components), so that the stored tensor is exactly
+    traceless."""
     D = lat.D
     tr = sum(T[a][a] for a in range(D))
-    return [[T[a][b] - (tr / D if a == b else 0.0) for b in range(D)] for a in range(D)]
+    out = [[T[a][b] - (tr / D if a == b else 0.0) for b in range(D)] for a in range(D)]
+    last = -out[0][0]
+    for a in range(1, D - 1):
+        last = last - out[a][a]
+    out[D - 1][D - 1] = last
+    return out
 
 
 def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
@@ -420,6 +430,19 @@ def apply_bc(prm, f, E):
             E[tuple(sl)] = E1
 
 
+def lift_axes(ed, D):
+    """Drag direction e_d (unit inflow direction) and the lift directions:
+    2D e_d rotated by +90 degrees; 3D the y axis made orthogonal to e_d,
+    then e_d x e_l1."""
+    ed = np.asarray(ed, dtype=np.float64)[:D]
+    if D == 2:
+        return ed, np.array([-ed[1], ed[0]]), np.zeros(2)
+    ey = np.array([0.0, 1.0, 0.0])
+    l1 = ey - (ey @ ed) * ed
+    l1 = l1 / np.sqrt(l1 @ l1)
+    return ed, l1, np.cross(ed, l1)
+
+
 class Sim:
     """Oracle state and the Sec. 2.5 time step.
 
@@ -493,6 +516,36 @@ class Sim:
     def run(self, n):
         for _ in range(n):
             self.step()
+
+    def wall_diagnostics(self):
+        """Wall diagnostics of the current (updated) field (reading Q26):
+        per point C_p, tau_w, u^s, T^s, (dT/dn)^s (oracle.ib), and the body
+        coefficients C_d, C_l (and C_l2 in 3D) from the last step's loads
+        and the Nusselt number from the heat into the fluid,
+          C_d = F.e_d / (q_inf A),  A = L (2D) or pi L^2/4 (3D),
+          Nu = heat L / (lambda (T_w - T_inf) S),  S = pi L (2D) or pi L^2 (3D),
+        e_d the inflow direction, T_w the mean Dirichlet wall target, L the
+        reference length (the diameter of a circle or sphere)."""
+        prm = self.prm
+        D = prm.lat.D
+        rho, u, T, _ = self.fields()
+        per = self.ib.diagnostics(rho, u, T)
+        L = self.last_loads
+        Lr = prm.ref_length
+        q_inf = 0.5 * prm.rho_inf * prm.u_mag * prm.u_mag
+        A = Lr if D == 2 else np.pi * Lr * Lr / 4.0
+        S = np.pi * Lr if D == 2 else np.pi * Lr * Lr
+        ed, el1, el2 = lift_axes(prm.u_inf / prm.u_mag, D)
+        F = L["force"]
+        coeffs = {"Cd": float(F @ ed) / (q_inf * A), "Cl": float(F @ el1) / (q_inf * A),
+                  "Cl2": float(F @ el2) / (q_inf * A) if D == 3 else 0.0}
+        dir_ = self.ib.tbc == IB.TBC_DIRICHLET
+        if dir_.any():
+            Tw = float(self.ib.tB[dir_].mean())
+            coeffs["Nu"] = L["heat"] * Lr / (prm.lam * (Tw - prm.theta_inf) * S) if Tw != prm.theta_inf else 0.0
+        else:
+            coeffs["Nu"] = 0.0
+        return coeffs, per
 
     def fields(self):
         """rho, u, T, p from the current state (predicted moments)."""
