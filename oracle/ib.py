@@ -10,6 +10,10 @@ Sec. 2.3 and 2.4 of the paper:
   * target-value reconstruction for Dirichlet (Eq. virtualdir) and Neumann
     (Eq. virtualneu) conditions
   * Lagrangian forcing F, W, Q (Eqs. fib/wib/qib and fib2/wib2/qib2)
+  * wall diagnostics on the updated field (Sec. 3.1-3.2): pressure
+    coefficient and velocity / temperature at X_l by Eq. int1 (d = 2 over
+    Omega), wall shear stress and normal temperature gradient from the
+    projection point (Eq. int1, d = 1)
 
 Readings (paper silent or ambiguous):
   Q17 the kernel support is strict, |r| < d; support sets contain only those
@@ -22,6 +26,10 @@ Readings (paper silent or ambiguous):
   Q21 projection-point interpolation of u and T both use d = 1.
   FODIBM with a Neumann temperature condition uses T^t = T^{P*} - g d_n,
   which is the paper's T^t = T^{P*} for the adiabatic case g = 0.
+  Q26 wall diagnostics (the paper defines C_p and the boundary errors, not
+      the discrete wall shear or heat flux): tau_w = mu [(u^P - u^B) minus
+      its normal part] / d_n, (dT/dn)^s = (T^P - T^s) / d_n, with u^P, T^P
+      by Eq. int1 at d = 1 and T^s by Eq. int1 at d = 2.
 """
 import functools
 import math
@@ -267,6 +275,65 @@ class Setup:
         return out
 
     # ----------------------------------------------------------------------
+    def two_sided_stencils(self):
+        """Eq. int1 stencils at X_l with d = 2 over Omega (nodes inside and
+        outside the body), the DIBM interpolation the paper uses to read the
+        updated field at the wall (Sec. 3.1-3.2)."""
+        if getattr(self, "_S2", None) is not None:
+            return self._S2
+        D = self.D
+        dims = list(self.prm.shape)
+        nodes_l, w_l = [], []
+        for l in range(self.NL):
+            base = [int(math.floor(self.X[l, a])) - 1 for a in range(D)]
+            nodes, wts = [], []
+            for off in np.ndindex(*([4] * D)):
+                node = [base[a] + off[D - 1 - a] for a in range(D)]
+                r = [float(node[a]) - self.X[l, a] for a in range(D)]
+                if any(abs(ra) >= 2.0 for ra in r):
+                    continue
+                idx = []
+                for a in range(D):
+                    v = node[a]
+                    if self.periodic[a]:
+                        v = v % dims[a]
+                    elif v < 0 or v >= dims[a]:
+                        raise GeometryError("diagnostic stencil of point %d leaves the domain" % l)
+                    idx.append(v)
+                wt = 1.0
+                for a in range(D):
+                    wt = wt * float(delta_tilde(r[a], 2.0))
+                nodes.append(sum(idx[a] * self.strides[a] for a in range(D)))
+                wts.append(wt)
+            nodes_l.append(nodes)
+            w_l.append(wts)
+        self._S2 = (nodes_l, w_l)
+        return self._S2
+
+    def diagnostics(self, rho, u, T):
+        """Wall quantities of the updated field (grid-shaped rho, u (D, grid),
+        T): per point C_p (Sec. 3.1), the wall shear stress vector tau_w,
+        u^s and T^s at X_l and (dT/dn)^s (reading Q26)."""
+        prm = self.prm
+        D = self.D
+        NL = self.NL
+        ones = np.ones(NL)
+        nodes, wts = self.two_sided_stencils()
+        p = rho * prm.R * T
+        p_s = self.interp(p.ravel(), nodes, wts, ones)
+        u_s = np.stack([self.interp(u[a].ravel(), nodes, wts, ones) for a in range(D)], axis=1)
+        T_s = self.interp(T.ravel(), nodes, wts, ones)
+        uP = np.stack([self.interp(u[a].ravel(), self.P_nodes, self.P_w, ones) for a in range(D)], axis=1)
+        TP = self.interp(T.ravel(), self.P_nodes, self.P_w, ones)
+        p_inf = prm.rho_inf * prm.R * prm.theta_inf
+        q_inf = 0.5 * prm.rho_inf * prm.u_mag * prm.u_mag
+        Cp = (p_s - p_inf) / q_inf
+        du = uP - self.uB
+        dn_comp = (du * self.nrm).sum(axis=1)
+        tau = prm.mu * (du - dn_comp[:, None] * self.nrm) / prm.d_n
+        dTdn = (TP - T_s) / prm.d_n
+        return dict(Cp=Cp, tau_w=tau, u_s=u_s, T_s=T_s, dTdn=dTdn, p_s=p_s)
+
     def interp(self, field_flat, nodes, wts, scale):
         return np.array([scale[l] * sum(field_flat[n] * w for n, w in zip(nodes[l], wts[l]))
                          for l in range(self.NL)])
