@@ -95,7 +95,22 @@ class Lattice:
                 h = h + s * self.H3(a, b, g)
             rows.append(h)
         self.H3r = np.array(rows)
-        self.N3r = np.array([(self.w * h * h).sum() for h in self.H3r])
+        # lattice norms N_k = sum_i w_i H3r_k,i^2 (reading Q3): exact
+        # rationals (weights k/36, polynomials in thirds), rounded once
+        cs2 = Fraction(1, 3)
+        d = lambda p, q: 1 if p == q else 0
+        norms = []
+        for combo in self.H3r_idx:
+            n = Fraction(0)
+            for i in range(self.Q):
+                ci = [int(v) for v in self.c[i]]
+                h = Fraction(0)
+                for s, (a, b, g) in combo:
+                    h += s * (ci[a] * ci[b] * ci[g] - cs2 * (d(a, b) * ci[g] + d(b, g) * ci[a] + d(a, g) * ci[b]))
+                n += self.w_exact[i] * h * h
+            norms.append(n)
+        self.N3r_exact = norms
+        self.N3r = np.array([float(v) for v in norms])
 
     def combo3(self, T3):
         """Contract a full symmetric third-order tensor T3[a,b,g] into the
