@@ -71,7 +71,7 @@ from . import ib as IB
 
 CS2 = L.CS2
 
-BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD = 0, 1, 2, 3
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_GHOST = 0, 1, 2, 3, 4
 TAU_THETA, TAU_LITERAL = 0, 1
 # a^C readings (Q6): off, the diagonal cubic defect only, full (default)
 AC_OFF, AC_CUBIC, AC_FULL = 0, 1, 2
@@ -105,7 +105,7 @@ class Params:
 
     def __init__(self, lattice, shape, mach, reynolds, ref_length, prandtl=0.71,
                  gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98,
-                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=AC_FULL, mu=None):
+                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=AC_FULL, mu=None, zoff=0):
         self.lat = L.get(lattice)
         D = self.lat.D
         self.shape = tuple(int(s) for s in shape)  # (nx, ny[, nz])
@@ -133,6 +133,10 @@ class Params:
             bc = [BC_PERIODIC] * (2 * D)
         self.bc = list(bc)[: 2 * D]
         self.ref_length = ref_length
+        # a z slab of a larger grid: global z of plane 0 (its faces towards
+        # neighbour slabs have bc BC_GHOST: no boundary condition, edge reads
+        # clamped, the planes refreshed from the neighbours between steps)
+        self.zoff = int(zoff)
 
 
 # --------------------------------------------------------------------------
@@ -236,13 +240,17 @@ def regularized_neq(lat, u, Pi):
 
 def deviator(lat, T):
     """Traceless part of a symmetric tensor, as carried between steps
-    (reading Q8): the independent components T_ab - delta_ab tr/D, and the
-    last diagonal component from the traceless condition (minus the sum of
-    the other diagonal components), so that the stored tensor is exactly
-    traceless."""
+    (reading Q8): its independent components T_ab - delta_ab tr/D (a <= b;
+    the lower triangle mirrors the upper one, so the carried tensor is
+    exactly symmetric), and the last diagonal component from the traceless
+    condition (minus the sum of the other diagonal components), so that it
+    is exactly traceless."""
     D = lat.D
     tr = sum(T[a][a] for a in range(D))
     out = [[T[a][b] - (tr / D if a == b else 0.0) for b in range(D)] for a in range(D)]
+    for a in range(D):
+        for b in range(a):
+            out[a][b] = out[b][a]
     last = -out[0][0]
     for a in range(1, D - 1):
         last = last - out[a][a]
