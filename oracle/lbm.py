@@ -465,14 +465,21 @@ class Sim:
         D = prm.lat.D
         self.zyx = tuple(reversed(prm.shape))
         self.f, self.E = freestream(prm, self.zyx)
-        rho = np.full(self.zyx, prm.rho_inf)
-        self.P_prev = rho * (1.0 - prm.theta_inf)
+        # Q25: the previous-step auxiliaries of the first step are those of
+        # the initial state, rho(1 - theta) from its own moments
+        self.reset_aux()
         self.devAF_prev = [[np.zeros(self.zyx) for _ in range(D)] for _ in range(D)]
         self.ib = None
         if geometry is not None:
             self.ib = IB.Setup(prm, self.grid, geometry)
         self.last_loads = None
         self.nstep = 0
+
+    def reset_aux(self):
+        """rho(1 - theta) of the current state as the previous-step value
+        (a fresh start, reading Q25)."""
+        rho, _, _, T = self.predicted()
+        self.P_prev = rho * (1.0 - T)
 
     # Sec. 2.2: rho = sum f-bar, j = sum c f-bar (moments before forcing)
     def moments(self):
