@@ -9,8 +9,11 @@ spreading, collision, streaming, energy update, boundaries).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas of
-the case, one per rank (the single case is not partitioned), weak scaling.
+Prints one JSON line (rank 0).  With N > 1 ranks (one per GPU) the case is
+partitioned into z slabs (lbm_create_slab), one per rank, with the ghost
+planes exchanged by NCCL after every step: a 256 x 192 x 192N channel with
+one sphere per 192 planes (weak scaling, each rank owns a 256 x 192 x 192
+slab around its sphere).
 """
 import argparse
 import json
@@ -30,13 +33,21 @@ UNIT = "MLUPS"
 SHAPE = (256, 192, 192)
 CASE = dict(lattice="D3Q19", shape=SHAPE, mach=0.3, reynolds=300.0, ref_length=48.0,
             center=(64.0, 96.0, 96.0), diameter=48.0, frequency=27)
-# algorithmic bytes per lattice update of the FP32 D3Q19 step: populations
-# read and written once (2 * 19 * 4) plus the state the method carries between
-# steps, read and written once: rho E, rho(1-theta) of the previous step and
-# the deviator of a^F of the previous step (5 components), 7 * 2 * 4.
-BYTES_PER_LU = {("D3Q19", "fp32"): 2 * 19 * 4 + 2 * 7 * 4, ("D3Q19", "fp16"): 2 * 19 * 2 + 2 * 7 * 4,
-                ("D3Q19", "bf16"): 2 * 19 * 2 + 2 * 7 * 4, ("D3Q19", "fp64"): 2 * 19 * 8 + 2 * 7 * 8,
-                ("D2Q9", "fp32"): 2 * 9 * 4 + 2 * 4 * 4, ("D2Q9", "fp64"): 2 * 9 * 8 + 2 * 4 * 8}
+# Algorithmic bytes per lattice update: populations read and written once
+# (2 Q s_f) plus the state the method carries between steps, read and written
+# once: rho E, rho(1-theta) of the previous step (the backward difference of
+# Eq. af2) and the deviator of a^F of the previous step (the F_i(t - dt) term
+# of Eq. pi2).  With the full a^C reading (off-diagonal advective terms) that
+# deviator has all D(D+1)/2 - 1 components (5 in 3D): 208 B for D3Q19 FP32.
+# A diagonal-only a^C would need D - 1 slots (184 B for D3Q19 FP32); both
+# fractions are reported.
+def bytes_per_lu(lattice, precision, ndev=None):
+    Q, D = (19, 3) if lattice == "D3Q19" else (9, 2)
+    sf = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
+    sa = 8 if precision == "fp64" else 4
+    if ndev is None:
+        ndev = D * (D + 1) // 2 - 1
+    return 2 * Q * sf + 2 * (2 + ndev) * sa
 
 
 def kernel_traffic():
@@ -179,9 +190,59 @@ def oracle_sample(steps_budget_s=15.0, max_steps=None):
     return nodes * n / el / 1e6, n, nodes, el
 
 
+def host_cpu():
+    """Host cores and CPU model (for the CPU baseline's record)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def _oracle_worker(budget):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    return oracle_sample(budget)
+
+
+def oracle_all_cores(budget_s, max_procs=32):
+    """Independent oracle processes (one per core, at most max_procs), each
+    stepping its own copy of the 64x48x48 downscale for budget_s seconds:
+    the host's aggregate oracle throughput.  Processes are spawned (never
+    forked from a process that has used the GPU)."""
+    import multiprocessing as mp
+    nproc, _ = host_cpu()
+    P = max(1, min(nproc, max_procs))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(P) as pool:
+        res = pool.map(_oracle_worker, [budget_s] * P)
+    return sum(r[0] for r in res), P, sum(r[1] for r in res)
+
+
+def cpu_baseline_record(budget_s=15.0, all_cores=True):
+    """The oracle as it stands on the host: one core, and (optionally) every
+    core running independent copies of the same downscale."""
+    nproc, model = host_cpu()
+    mlups, n, nodes, el = oracle_sample(budget_s)
+    rec = {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d steps of the 64x48x48 downscale of the sphere case (D=12, 492 points), %.1f s, "
+                     "one process" % (n, el),
+           "host_nproc": nproc, "cpu_model": model}
+    if all_cores:
+        agg, P, nsteps = oracle_all_cores(budget_s)
+        rec["all_cores"] = {"value": agg, "unit": UNIT, "cores": P,
+                            "sample": "%d independent oracle processes on the same downscale, %.0f s each, "
+                                      "%d steps in total" % (P, budget_s, nsteps)}
+    return rec
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
+    nproc, model = host_cpu()
     mlups, n, nodes, el = oracle_sample(steps_budget_s=max(5.0, 10.0 * args.steps / 20.0))
     line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
@@ -190,12 +251,13 @@ def run_reference(args, rank):
             "config": {"workload": "3D sphere D3Q19 256x192x192 (oracle on its 64x48x48 downscale)",
                        "precision": "fp64", "method": "FODIBM-R"},
             "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d steps of the 64x48x48 downscale (D=12, 492 points), %.1f s" % (n, el)},
+                             "sample": "%d steps of the 64x48x48 downscale (D=12, 492 points), %.1f s" % (n, el),
+                             "host_nproc": nproc, "cpu_model": model},
             "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """64 uneven 2D cases (seeded circles and ellipses, grids 256x128 ..
     1024x512, Re 20-200, FP32) in one batched launch per step (autotuned
     plan, graph replay) against 64 sequential per-case launches.  Mach is
@@ -245,8 +307,87 @@ def run_batch(args):
                        "plan": {"tile_rows": plan[0], "schedule": plan[1]}},
             "sequential": {"value": nodes * K / (ms_s / 1e3) / 1e6, "ms_per_step": ms_s / K},
             "speedup_vs_sequential": ms_s / ms_b}
-    print(json.dumps(line), flush=True)
     b.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def _sphere(lbmib, inputs, precision, shape, D, freq):
+    s = lbmib.Solver("D3Q19", precision, shape, mach=CASE["mach"], reynolds=CASE["reynolds"], ref_length=D,
+                     bc=[lbmib.BC_INLET, lbmib.BC_OUTLET] + [lbmib.BC_FARFIELD] * 4)
+    th = s.constants()["theta_inf"]
+    center = (shape[0] / 4.0, shape[1] / 2.0, shape[2] / 2.0)
+    s.set_geometry(inputs.icosphere(center, D, freq, tbc=0, t_value=1.1 * th))
+    return s
+
+
+def coefficient_history(s, steps, every):
+    """C_d and Nu of the body sampled every `every` steps."""
+    cd, nu = [], []
+    for _ in range(steps // every):
+        s.step(every)
+        d = s.wall_diagnostics(per_point=False)
+        cd.append(d["Cd"])
+        nu.append(d["Nu"])
+    s.check()
+    return np.array(cd), np.array(nu)
+
+
+def steady_summary(cd, nu, every, window):
+    """Running means over the last `window` steps and the first step from
+    which the trailing-window mean of C_d stays within 0.1% of that final
+    value (reading Q28: the criterion is judged on a running mean over at
+    least two shedding periods)."""
+    w = max(1, window // every)
+    cd_f, nu_f = float(cd[-w:].mean()), float(nu[-w:].mean())
+    run = np.convolve(cd, np.ones(w) / w, mode="valid")
+    ok = np.abs(run - cd_f) <= 1e-3 * abs(cd_f)
+    bad = np.nonzero(~ok)[0]
+    first = int(bad[-1] + 1) if bad.size else 0
+    steady = (first + w) * every if first < run.size else None
+    return dict(Cd=cd_f, Nu=nu_f, steps_to_steady=steady)
+
+
+def run_precision(args):
+    """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
+    isothermal wall): C_d and Nu as running means, and the steps until the
+    running mean of C_d settles within 0.1%, for FP32, FP16 and BF16 on the
+    full 256x192x192 grid (D = 48) and, with the FP64 path (which equals the
+    oracle to 1e-12), on the 64x48x48 downscale (D = 12)."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    out = {}
+    for name, shape, D, freq, steps, window, forms in (
+            ("downscale_64x48x48", (64, 48, 48), 12.0, 7, args.prec_steps_small, 2500, ("fp64", "fp32", "fp16", "bf16")),
+            ("full_256x192x192", SHAPE, 48.0, 27, args.prec_steps_full, 10000, ("fp32", "fp16", "bf16"))):
+        res = {}
+        for prec in forms:
+            s = _sphere(lbmib, inputs, prec, shape, D, freq)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cd, nu = coefficient_history(s, steps, 50)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            s.close()
+            r = steady_summary(cd, nu, 50, window)
+            r["wall_s"] = el
+            r["mlups"] = float(np.prod(shape)) * steps / el / 1e6
+            res[prec] = r
+        base = res["fp32"]
+        for prec, r in res.items():
+            r["Cd_rel_vs_fp32"] = r["Cd"] / base["Cd"] - 1.0
+            r["Nu_rel_vs_fp32"] = r["Nu"] / base["Nu"] - 1.0
+            if "fp64" in res:
+                r["Cd_rel_vs_fp64"] = r["Cd"] / res["fp64"]["Cd"] - 1.0
+                r["Nu_rel_vs_fp64"] = r["Nu"] / res["fp64"]["Nu"] - 1.0
+        out[name] = dict(steps=steps, window=window, forms=res)
+    line = {"metric": "C_d and Nu running means by storage form, 3D sphere (Ma 0.3, Re 300); steps to 0.1% drag",
+            "value": out["full_256x192x192"]["forms"]["fp16"]["Cd_rel_vs_fp32"], "unit": "relative C_d vs FP32 (FP16)",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32 / f16 / bf16 storage, f32 math", "data": "synthetic",
+            "config": {"workload": "3D sphere D3Q19, Ma 0.3, Re 300, isothermal wall 1.1 T_inf, uniform start"},
+            "cases": out}
+    print(json.dumps(line), flush=True)
 
 
 def run_warmstart(args):
@@ -291,6 +432,139 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def time_form(lbmib, inputs, precision, steps, warmup, N, peak):
+    """One storage form of the sphere case: device-timed MLUPS of the whole
+    step and the fused kernel's time from a profiled pass of the same steps."""
+    import torch
+    s, _ = build_case(lbmib, inputs, precision)
+    s.step(warmup)
+    s.check()
+    s.profile(True, True)
+    torch.cuda.synchronize()
+    s.step(steps)
+    torch.cuda.synchronize()
+    prof = s.get_profile()
+    s.profile(False, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    s.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.check()
+    s.close()
+    kern_ms = prof["step"][0] / steps
+    bpl = bytes_per_lu("D3Q19", precision)
+    return {"value": N * steps / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / steps,
+            "kernel_ms_per_step": kern_ms, "bytes_per_lu": bpl,
+            "roofline_frac": bpl * N / (kern_ms / 1e3) / 1e9 / peak}
+
+
+def other_forms(args, lbmib, inputs, N, peak):
+    """The reduced-precision storage forms of the same case and the 64-case
+    batch, measured on the same box as the headline (compact sub-records)."""
+    out = {}
+    for prec in ("fp16", "bf16"):
+        out[prec] = time_form(lbmib, inputs, prec, args.steps, args.warmup, N, peak)
+    b = run_batch(argparse.Namespace(steps=max(20, args.steps // 2), warmup=args.warmup), emit=False)
+    out["batch64"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "sequential", "speedup_vs_sequential")}
+    out["batch64"]["workload"] = b["config"]["workload"]
+    out["batch64"]["nodes"] = b["config"]["nodes"]
+    return out
+
+
+def run_slabs(args, rank, world, local, dist, lbmib, inputs):
+    """The partitioned case on N ranks: rank r owns planes [192 r, 192 r +
+    192) of a 256 x 192 x 192N channel whose sphere r (D = 48, 7292 points)
+    sits at z = 192 r + 96; ghost planes (10 per cut) are exchanged with NCCL
+    point-to-point transfers after every step; the wall loads are added over
+    ranks in rank order."""
+    import torch
+    from paper_2607_07432_b300 import slab
+    c = CASE
+    nz = SHAPE[2] * world
+    gshape = (SHAPE[0], SHAPE[1], nz)
+    halo = slab.MIN_HALO
+    p = slab.plan(nz, world, halo)[rank]
+    s = lbmib.Solver(c["lattice"], args.precision, gshape, mach=c["mach"], reynolds=c["reynolds"],
+                     ref_length=c["ref_length"], bc=[lbmib.BC_INLET, lbmib.BC_OUTLET] + [lbmib.BC_FARFIELD] * 4,
+                     slab=(p["z0"], p["z1"], halo))
+    th = s.constants()["theta_inf"]
+    center = (c["center"][0], c["center"][1], float(p["z0"]) + c["center"][2])
+    s.set_geometry(inputs.icosphere(center, c["diameter"], c["frequency"], tbc=0, t_value=1.1 * th))
+    bufs = slab.Buffers(s, "cuda")
+
+    def step(n):
+        for _ in range(n):
+            s.step(1)
+            slab.exchange_dist(s, bufs, rank, world, dist)
+
+    def barrier():
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    step(args.warmup)
+    s.check()
+    own = SHAPE[0] * SHAPE[1] * (p["z1"] - p["z0"])
+    total = int(np.prod(gshape))
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    l0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.begin()
+    e0.record()
+    step(args.steps)
+    e1.record()
+    barrier()
+    clocks.end()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    launches = s.launch_count() - l0
+    s.check()
+    # end to end: initial fields from pinned host memory, steps with the
+    # exchange, the body's loads gathered from every rank each step
+    Nloc = s.N
+    rho0 = torch.full((Nloc,), 1.0, dtype=torch.float64).pin_memory()
+    u0 = torch.zeros((3 * Nloc,), dtype=torch.float64)
+    u0[:Nloc] = s.constants()["u_mag"]
+    u0 = u0.pin_memory()
+    T0 = torch.full((Nloc,), th, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    s.set_fields(rho0.numpy(), u0.numpy(), T0.numpy())
+    for _ in range(args.steps):
+        step(1)
+        wl = s.wall_loads()
+        part = torch.tensor(list(wl["force"]) + [wl["heat"], wl["work"]], dtype=torch.float64, device="cuda")
+        gathered = [torch.empty_like(part) for _ in range(world)]
+        dist.all_gather(gathered, part)
+        slab.reduce_loads([dict(force=g[:3].cpu().numpy(), heat=float(g[3]), work=float(g[4])) for g in gathered])
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    if rank != 0:
+        s.close()
+        return
+    peak, _ = peaks()
+    line = {"metric": METRIC, "value": total * args.steps / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": "3D spheres D3Q19 256x192x(192 N), one D=48 sphere (7292 points) per 192 planes, "
+                                   "Ma 0.3, Re 300, isothermal walls, FODIBM-R",
+                       "precision": args.precision, "parallelism": "z slabs, %d ranks, halo %d" % (world, halo),
+                       "l2": "inputs larger than L2, no flush"},
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": total * args.steps / e2e_s / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": int(Nloc * 5 * 8 / args.steps), "d2h_bytes_per_step": 5 * 8 * world},
+            "gpu_launches": launches, "clocks": clk,
+            "exchange_bytes_per_step_per_rank": sum(bufs.send[k].numel() for k in (0, 1)
+                                                    if bufs.send[k] is not None)}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def max_over_ranks(x, dist, device):
     """The slowest rank's time (every rank gets it); x itself on one rank."""
     if dist is None:
@@ -315,7 +589,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart"])
+    ap.add_argument("--no-other-forms", action="store_true",
+                    help="skip the FP16 / BF16 storage and 64-case batch sub-records")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision"])
+    ap.add_argument("--prec-steps-small", type=int, default=20000)
+    ap.add_argument("--prec-steps-full", type=int, default=40000)
     ap.add_argument("--ws-cases", type=int, default=256)
     ap.add_argument("--ws-gen-steps", type=int, default=24000)
     ap.add_argument("--ws-train-steps", type=int, default=2000)
@@ -329,6 +607,8 @@ def main():
         return run_batch(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "precision":
+        return run_precision(args)
     args.warmup = max(args.warmup, 3)
     import torch
     torch.cuda.set_device(local)
@@ -337,6 +617,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2607_07432_b300 import inputs, lbmib
+    if world > 1:
+        return run_slabs(args, rank, world, local, dist, lbmib, inputs)
     s, geo = build_case(lbmib, inputs, args.precision)
     N = int(np.prod(SHAPE))
     s.step(args.warmup)
@@ -347,8 +629,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # device-timed region: K steps, inputs resident in HBM (state 1.5 GB,
-    # larger than L2, so no flush is needed between steps)
+    # device-timed region: K steps, inputs resident in HBM (each step reads
+    # about 1 GB of state, far more than L2, so no flush is needed)
     # per-kernel breakdown (roofline of the fused kernel): one pass of the
     # same K steps with CUDA events recorded around every launch
     s.profile(True, True)
@@ -400,7 +682,8 @@ def main():
     if rank != 0:
         return
     peak, peak_kind = peaks()
-    bpl = BYTES_PER_LU[(CASE["lattice"], args.precision)]
+    bpl = bytes_per_lu(CASE["lattice"], args.precision)
+    bpl_diag = bytes_per_lu(CASE["lattice"], args.precision, ndev=2)
     step_ms, step_n = prof["step"]
     other_ms, other_n = prof["other"]
     # dominant kernel: the fused collide-stream-energy step kernel
@@ -409,24 +692,30 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": kernel_traffic() if args.precision == "fp32" else None, "peak_kind": peak_kind,
             "bytes_per_lu": bpl,
+            "frac_at_diagonal_aC_bytes": bpl_diag * N / (kern_ms / 1e3) / 1e9 / peak,
+            "bytes_per_lu_diagonal_aC": bpl_diag,
             "kernel_ms_per_step": kern_ms,
             "breakdown_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    s.close()
+    others = None
+    if not args.no_other_forms and world == 1 and args.precision == "fp32":
+        others = other_forms(args, lbmib, inputs, N, peak)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        mlups, n, nodes, el = oracle_sample(15.0)
-        cpu = {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d steps of the 64x48x48 downscale (D=12, 492 points), %.1f s" % (n, el)}
+        cpu = cpu_baseline_record(15.0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
             "data": "synthetic",
             "config": {"workload": "3D sphere D3Q19 256x192x192, D=48, 7292 points, Ma 0.3, Re 300, "
                                    "isothermal wall, FODIBM-R",
-                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "state 1.5 GB > L2, no flush"},
+                       "precision": args.precision, "parallelism": "single",
+                       "l2": "inputs larger than L2: each step reads %.2f GB of state (126 MB L2), no flush"
+                             % (bpl * N / 2 / 1e9)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if others is not None:
+        line["other_forms"] = others
     print(json.dumps(line), flush=True)
-    s.close()
 
 
 if __name__ == "__main__":

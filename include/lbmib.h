@@ -84,7 +84,8 @@ typedef struct {
   int method;              /* IB_DIBM / IB_FODIBM / IB_FODIBM_R */
   int bc[6];               /* LBM_BC_* per face */
   int tau_mode;            /* LBM_TAU_LITERAL (default) or LBM_TAU_THETA */
-  int use_ac;              /* 1: include the a^C term of Eq. af2 (default) */
+  int use_ac;              /* a^C of Eq. af2: 2 = c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
+                              P = rho(1-theta) (default); 1 = the cubic part only; 0 = none */
   int device;              /* CUDA device ordinal */
   void* stream;            /* cudaStream_t, or NULL */
 } lbm_config;
@@ -108,7 +109,7 @@ typedef struct {
 } ib_geometry;
 
 /* Fill *cfg with defaults (D2Q9, FP32, Pr 0.71, gamma 1.4, sigma 0.98,
- * d_n 1.5, FODIBM-R, periodic faces, tau_LB = nu/c_s^2, a^C on). */
+ * d_n 1.5, FODIBM-R, periodic faces, tau_LB = nu/c_s^2, full a^C). */
 lbm_status lbm_config_default(lbm_config* cfg);
 
 /* Create a case (Sec. 2.2): validates *cfg, derives u_inf, mu, lambda,
@@ -198,6 +199,30 @@ lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, doub
  * rounding. */
 lbm_status lbm_get_wall_loads_noalloc(lbm_handle* h, double force[3], double* heat, double* work);
 
+/* Wall diagnostics of the current (updated) flow field (Sec. 3.1-3.2; the
+ * paper defines C_p and reads wall values with Eq. int1 at d = 2; the wall
+ * shear stress and heat-flux forms are this library's reading).
+ * coeffs (optional, host, 4 doubles), from the last step's FP64 loads:
+ *   [0] C_d = F . e_d / (q_inf A), e_d the inflow direction,
+ *   [1] C_l along e_d rotated by +90 degrees (2D) or the y axis made
+ *       orthogonal to e_d (3D), [2] C_l along e_d x e_l1 (3D; 0 in 2D),
+ *   [3] Nu = heat L / (lambda (T_w - T_inf) S), T_w the mean Dirichlet
+ *       temperature target (0 when every point is Neumann),
+ *   with q_inf = rho_inf u_inf^2 / 2, L = ref_length, A = L (2D, per unit
+ *   depth) or pi L^2 / 4 (3D), S = pi L (2D) or pi L^2 (3D): the frontal
+ *   area and surface of a circle or sphere of diameter L.
+ * per_point (optional, host, N_L rows of 2D + 3 doubles):
+ *   C_p = (p^s - p_inf) / q_inf with p^s by Eq. int1 (d = 2, nodes on both
+ *   sides of the wall) at X_l; tau_w[D] = mu ((u^P - u^B) - its normal
+ *   part) / d_n with u^P by Eq. int1 (d = 1) at the projection point;
+ *   u^s[D] and T^s by Eq. int1 (d = 2) at X_l; (dT/dn)^s = (T^P - T^s) / d_n.
+ * The boundary errors of Sec. 3.2 follow: eps_Dir = |u^s - u^Bt| / u_inf,
+ * eps_iso = |T^s - T^Bt| / T_inf, eps_Neu = |(dT/dn)^s - g| D / T_inf.
+ * LBM_ESTATE without a body, LBM_EGEOM if a diagnostic stencil leaves a
+ * non-periodic domain.  Allocates a device buffer of N_L (2D + 3) doubles
+ * for the call when per_point is given. */
+lbm_status lbm_get_wall_diagnostics(lbm_handle* h, double coeffs[4], double* per_point);
+
 /* Derived constants: out[0..7] = u_inf magnitude, mu, lambda, theta_inf,
  * C_v, C_p, rho_inf, gamma. */
 lbm_status lbm_get_constants(const lbm_handle* h, double out[8]);
@@ -223,6 +248,60 @@ lbm_status lbm_get_profile(lbm_handle* h, double ms[5], long long launches[5]);
 
 /* Number of kernels this handle has launched since creation. */
 long long lbm_launch_count(const lbm_handle* h);
+
+/* ---- one case split into z slabs (Sec. 2.5 step, partitioned) -----------
+ * A slab handle owns the planes [z0, z1) of the D3Q19 case *cfg describes
+ * (cfg->nz = the global nz; its z axis must not be periodic:
+ * LBM_EUNSUPPORTED), plus `halo` ghost planes on each side that borders
+ * another slab (none at a domain face).  It is created, initialised,
+ * stepped and read like any handle, on local arrays of nx x ny x
+ * (z1 - z0 + ghosts) nodes whose plane k is global plane k + zoff.  No
+ * boundary condition is applied on a ghost face.  After every step the
+ * ghost planes must be refreshed from the neighbours' owned planes: pack
+ * side 1 (high z) of slab s and unpack it into side 0 of slab s + 1, and
+ * pack side 0 of slab s + 1 into side 1 of slab s, before the next step
+ * (the caller moves the buffers: a device copy on one GPU, NCCL send and
+ * receive across GPUs).  With the exchange after every step and halo >= 10
+ * the owned planes evolve as the same planes of the unsplit case, bit for
+ * bit in FP64 (FP32 to rounding: the fused step's z chunks start at other
+ * planes).  ib_set_geometry on a slab takes the whole body in global
+ * coordinates and keeps the points whose stencils lie in its local planes
+ * (LBM_EGEOM if a point whose stencils leave the slab has its d = 2 stencil
+ * within 5 planes of the owned planes; 9 ghost planes always suffice);
+ * wall loads, diagnostics coefficients
+ * and their per-point arrays cover the points it keeps, the loads and
+ * coefficients only those it owns (z0 <= X_z < z1), so the case's loads
+ * are the sum over slabs (add them in slab order for a reproducible sum). */
+lbm_status lbm_create_slab(const lbm_config* cfg, int z0, int z1, int halo, lbm_handle** out);
+/* info[0..5] = z0, z1, ghost planes below, ghost planes above, zoff (global
+ * z of local plane 0), global nz.  LBM_ESTATE for a handle that is not a slab. */
+lbm_status lbm_slab_info(const lbm_handle* h, int info[6]);
+/* Bytes of the exchange buffer of one side (0 = low z, 1 = high z; 0 bytes
+ * at a domain face): the side's ghost-plane count x nx x ny x (Q storage
+ * elements + D + 3 + NDEV compute elements) -- populations, carried moments
+ * rho, rho u, rho E, rho(1-theta) and the a^F deviator of the previous
+ * step, component after component, planes in z order. */
+lbm_status lbm_slab_exchange_bytes(const lbm_handle* h, int side, size_t* bytes);
+/* Copy the owned planes next to `side` into dst (device, caller-owned,
+ * lbm_slab_exchange_bytes of that side), asynchronously on the handle's
+ * stream. */
+lbm_status lbm_slab_pack(lbm_handle* h, int side, void* dst);
+/* Copy src (device; the neighbour's pack of its facing side) into the
+ * ghost planes of `side`, asynchronously on the handle's stream. */
+lbm_status lbm_slab_unpack(lbm_handle* h, int side, const void* src);
+/* Number of Lagrangian points the slab keeps and (optional) their indices
+ * in the geometry given to ib_set_geometry. */
+lbm_status lbm_slab_points(const lbm_handle* h, int* n_points, int* global_index);
+/* Host-only planning (no device work, callable without a GPU):
+ * lbm_slab_plan writes, for each of n_slabs slabs of nz planes, out[4k..4k+3]
+ * = z0, z1, ghost planes below, ghost planes above (the first nz % n_slabs
+ * slabs get one plane more).  lbm_slab_keep applies the point rule of
+ * ib_set_geometry on a slab: keep[l] (the slab keeps point l) and owned[l]
+ * (z0 <= X_z < z1) for n_points points X, normals (host, n_points x 3);
+ * LBM_EGEOM when the halo is too narrow for the body. */
+lbm_status lbm_slab_plan(int nz, int n_slabs, int halo, int* out);
+lbm_status lbm_slab_keep(const lbm_config* cfg, int z0, int z1, int halo, int n_points, const double* X,
+                         const double* normals, int* keep, int* owned);
 
 /* ---- several cases advanced together ------------------------------------
  * A batch owns n cases (same lattice, precision and device; grids, bodies

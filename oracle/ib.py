@@ -80,9 +80,10 @@ def delta_tilde(r, d):
 # --------------------------------------------------------------------------
 # classification of Eulerian nodes (Omega' = strict interior)
 # --------------------------------------------------------------------------
-def classify(shape, grid_shape):
+def classify(shape, grid_shape, zoff=0):
     """Boolean mask over the grid (z, y, x order) of the nodes strictly inside
-    the body.  shape: dict with kind in {circle, sphere, ellipse, polygon, mask}."""
+    the body.  shape: dict with kind in {circle, sphere, ellipse, polygon, mask}.
+    zoff: global z of the grid's plane 0 (a z slab of a larger grid)."""
     nx = grid_shape[0]
     ny = grid_shape[1]
     D = len(grid_shape)
@@ -94,7 +95,7 @@ def classify(shape, grid_shape):
         coords = [x, y]
     else:
         nz = grid_shape[2]
-        z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+        z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64) + float(zoff), np.arange(ny, dtype=np.float64),
                               np.arange(nx, dtype=np.float64), indexing="ij")
         coords = [x, y, z]
     if kind in ("circle", "sphere"):
@@ -155,7 +156,10 @@ class Setup:
         self.uB = np.asarray(geometry.get("u_target", np.zeros((NL, D))), dtype=np.float64).reshape(NL, D)
         self.tB = np.asarray(geometry["t_value"], dtype=np.float64).reshape(NL)
         shape_n = prm.shape
-        self.inside = classify(geometry["shape"], shape_n)
+        # a z slab of a larger grid: node coordinates stay global, plane k of
+        # this grid is global plane k + zoff
+        self.zoff = zoff = getattr(prm, "zoff", 0)
+        self.inside = classify(geometry["shape"], shape_n, zoff)
         method = prm.method
         one_sided = method in (FODIBM, FODIBM_R)
         dims = list(shape_n)
@@ -172,7 +176,7 @@ class Setup:
         def linear(node, l, what):
             idx = []
             for a in range(D):
-                v = node[a]
+                v = node[a] - (zoff if a == 2 else 0)
                 if periodic[a]:
                     v = v % dims[a]
                 elif v < 0 or v >= dims[a]:
@@ -294,7 +298,7 @@ class Setup:
                     continue
                 idx = []
                 for a in range(D):
-                    v = node[a]
+                    v = node[a] - (self.zoff if a == 2 else 0)
                     if self.periodic[a]:
                         v = v % dims[a]
                     elif v < 0 or v >= dims[a]:

@@ -54,7 +54,7 @@ double theta_rule(double mach, double gamma, double re, double L, double pr, int
 void free_ib(lbm_handle* h) {
   void* ptrs[] = {h->inside, h->X, h->nrm, h->uB, h->tB, h->tbc, h->sten_node, h->psten_node, h->sten_w,
                   h->sten_x, h->psten_w, h->phi, h->W, h->Xstar, h->dBV, h->row_ptr, h->cell_id, h->col,
-                  h->slot_of_entry, h->wt, h->row_of_node, h->forced, h->G, h->FU, h->WQ, h->loads};
+                  h->slot_of_entry, h->wt, h->row_of_node, h->forced, h->G, h->FU, h->WQ, h->loads, h->owned};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->inside = nullptr;
@@ -67,6 +67,7 @@ void free_ib(lbm_handle* h) {
   h->row_of_node = nullptr;
   h->forced = nullptr;
   h->G = h->FU = h->WQ = h->loads = nullptr;
+  h->owned = nullptr;
   h->has_ib = false;
   h->NL = h->n_rows = h->nnz = 0;
 }
@@ -95,21 +96,33 @@ lbm_status lbm_config_default(lbm_config* c) {
   c->d_n = 1.5;
   c->method = IB_FODIBM_R;
   c->tau_mode = LBM_TAU_LITERAL;
-  c->use_ac = 1;
+  c->use_ac = 2;
   return LBM_OK;
 }
 
-lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
+}  // extern "C"
+
+namespace {
+
+// z slab of a larger case: global owned planes [z0, z1), ghost planes
+// below / above, global nz
+struct SlabSpec {
+  int z0, z1, ghost_lo, ghost_hi, nz_global;
+};
+
+lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle** out) {
   if (!cfg || !out || cfg->struct_size != sizeof(lbm_config)) return LBM_EINVAL;
   *out = nullptr;
   const int D = cfg->lattice == LBM_D3Q19 ? 3 : 2;
   if ((cfg->lattice != LBM_D2Q9 && cfg->lattice != LBM_D3Q19) || cfg->nx < 3 || cfg->ny < 3 ||
       (D == 3 && cfg->nz < 3) || (D == 2 && cfg->nz != 1) || cfg->mach <= 0 || cfg->reynolds <= 0 ||
       cfg->ref_length <= 0 || cfg->gamma <= 1.0 || cfg->prandtl <= 0 || cfg->precision < 0 ||
-      cfg->precision > LBM_BF16DEV || cfg->method < IB_DIBM || cfg->method > IB_FODIBM_R)
+      cfg->precision > LBM_BF16DEV || cfg->method < IB_DIBM || cfg->method > IB_FODIBM_R || cfg->use_ac < 0 ||
+      cfg->use_ac > 2)
     return LBM_EINVAL;
   for (int f = 0; f < 2 * D; ++f)
-    if (cfg->bc[f] < LBM_BC_PERIODIC || cfg->bc[f] > LBM_BC_FARFIELD) return LBM_EINVAL;
+    if ((cfg->bc[f] < LBM_BC_PERIODIC || cfg->bc[f] > LBM_BC_FARFIELD) && !(slab && cfg->bc[f] == kBCGhostFace))
+      return LBM_EINVAL;
   for (int a = 0; a < D; ++a)
     if ((cfg->bc[2 * a] == LBM_BC_PERIODIC) != (cfg->bc[2 * a + 1] == LBM_BC_PERIODIC)) return LBM_EINVAL;
   const Ops* ops = pick_ops(cfg->lattice, cfg->precision);
@@ -117,6 +130,15 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   lbm_handle* h = new lbm_handle();
   h->cfg = *cfg;
   h->ops = ops;
+  if (slab) {
+    h->slab = true;
+    h->slab_z0 = slab->z0;
+    h->slab_z1 = slab->z1;
+    h->ghost_lo = slab->ghost_lo;
+    h->ghost_hi = slab->ghost_hi;
+    h->nz_global = slab->nz_global;
+    h->g.zoff = slab->z0 - slab->ghost_lo;
+  }
   h->D = D;
   h->Q = D == 3 ? 19 : 9;
   h->NDEV = D == 3 ? 5 : 2;
@@ -137,6 +159,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
                                     : theta_rule(cfg->mach, cfg->gamma, cfg->reynolds, cfg->ref_length,
                                                  cfg->prandtl, D);
   h->rho_inf = 1.0;
+  h->g.thref = float(h->theta_inf);
   const double c_inf = std::sqrt(h->gamma * h->R * h->theta_inf);
   h->u_mag = cfg->mach * c_inf;
   double dn = 0.0;
@@ -152,7 +175,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   double k = 0.0;
   for (int a = 0; a < D; ++a) k += h->u_inf[a] * h->u_inf[a];
   h->E_inf = h->rho_inf * (0.5 * k + h->Cv * h->theta_inf);
-  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+  DeviceGuard dg(cfg->device);
+  if (dg.status() != cudaSuccess) {
     delete h;
     return LBM_ECUDA;
   }
@@ -166,27 +190,19 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
     }
   };
   {
-    const char* env = std::getenv("LBMIB_UNFUSED");
-    h->use_fused = (env && env[0] == '1') ? 0 : 1;
     const char* zc = std::getenv("LBMIB_ZCHUNK");
     if (zc) {
       h->zchunk = std::max(1, std::atoi(zc));
       h->zchunk_fixed = 1;
     }
-    const char* tr = std::getenv("LBMIB_TILE_ROWS");
-    if (tr) h->tile_rows = std::atoi(tr);
     const char* ng = std::getenv("LBMIB_NO_GRAPH");
     if (ng && ng[0] == '1') h->use_graph = 0;
     const char* bk = std::getenv("LBMIB_BC_SEPARATE");
     if (bk && bk[0] == '1') h->bc_in_kernel = 0;
   }
   alloc(&h->f, N * h->Q * h->ssize);
-  if (h->use_fused) {
-    alloc(&h->f2, N * h->Q * h->ssize);
-    alloc(&h->M2, N * (D + 2) * h->csize);
-  } else {
-    alloc(&h->fcol, N * h->Q * h->csize);
-  }
+  alloc(&h->f2, N * h->Q * h->ssize);
+  alloc(&h->M2, N * (D + 2) * h->csize);
   alloc(&h->M, N * (D + 3) * h->csize);
   alloc(&h->E, N * h->csize);
   for (int k2 = 0; k2 < 2; ++k2) {
@@ -205,17 +221,142 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) {
   return LBM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) { return create_impl(cfg, nullptr, out); }
+
+lbm_status lbm_create_slab(const lbm_config* cfg, int z0, int z1, int halo, lbm_handle** out) {
+  if (!cfg || !out || cfg->struct_size != sizeof(lbm_config)) return LBM_EINVAL;
+  *out = nullptr;
+  if (cfg->lattice != LBM_D3Q19) return LBM_EINVAL;
+  if (cfg->bc[4] == LBM_BC_PERIODIC) return LBM_EUNSUPPORTED;
+  const int nz = cfg->nz;
+  if (z0 < 0 || z1 > nz || z1 - z0 < 1 || halo < 1) return LBM_EINVAL;
+  SlabSpec sp;
+  sp.z0 = z0;
+  sp.z1 = z1;
+  sp.ghost_lo = z0 > 0 ? std::min(halo, z0) : 0;
+  sp.ghost_hi = z1 < nz ? std::min(halo, nz - z1) : 0;
+  sp.nz_global = nz;
+  lbm_config c = *cfg;
+  c.nz = (z1 - z0) + sp.ghost_lo + sp.ghost_hi;
+  if (c.nz < 3) return LBM_EINVAL;
+  if (sp.ghost_lo) c.bc[4] = kBCGhostFace;
+  if (sp.ghost_hi) c.bc[5] = kBCGhostFace;
+  return create_impl(&c, &sp, out);
+}
+
+lbm_status lbm_slab_info(const lbm_handle* h, int info[6]) {
+  if (!h || !info) return LBM_EINVAL;
+  if (!h->slab) return LBM_ESTATE;
+  info[0] = h->slab_z0;
+  info[1] = h->slab_z1;
+  info[2] = h->ghost_lo;
+  info[3] = h->ghost_hi;
+  info[4] = h->g.zoff;
+  info[5] = h->nz_global;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the stepping state of a slab as (device pointer, plane bytes, planes) per
+// component: populations (storage type), carried moments, rho(1-theta) of
+// the previous step, deviator of a^F of the previous step
+struct StateComp {
+  char* base;
+  size_t elem;
+};
+std::vector<StateComp> slab_components(lbm_handle* h) {
+  std::vector<StateComp> v;
+  const size_t N = (size_t)h->g.N;
+  for (int i = 0; i < h->Q; ++i) v.push_back({(char*)h->f + i * N * h->ssize, h->ssize});
+  for (int k = 0; k < h->D + 2; ++k) v.push_back({(char*)h->M + k * N * h->csize, h->csize});
+  v.push_back({(char*)h->P[h->cur], h->csize});
+  for (int k = 0; k < h->NDEV; ++k) v.push_back({(char*)h->A[h->cur] + k * N * h->csize, h->csize});
+  return v;
+}
+
+// planes of one side: the first plane and the count
+void slab_planes(const lbm_handle* h, int side, bool ghost, int* p0, int* cnt) {
+  const int nloc = h->g.n[2];
+  const int own = h->slab_z1 - h->slab_z0;
+  if (side == 0) {
+    *cnt = h->ghost_lo;
+    *p0 = ghost ? 0 : h->ghost_lo;
+  } else {
+    *cnt = h->ghost_hi;
+    *p0 = ghost ? nloc - h->ghost_hi : h->ghost_lo + own - h->ghost_hi;
+  }
+}
+
+lbm_status slab_copy(lbm_handle* h, int side, void* buf, bool pack) {
+  if (!h->slab) return fail(h, LBM_ESTATE, "not a slab handle");
+  if (side != 0 && side != 1) return fail(h, LBM_EINVAL, "side must be 0 (low z) or 1 (high z)");
+  int p0 = 0, cnt = 0;
+  slab_planes(h, side, !pack, &p0, &cnt);
+  if (!cnt) return LBM_OK;
+  if (pack && h->slab_z1 - h->slab_z0 < cnt) return fail(h, LBM_EINVAL, "slab thinner than its halo");
+  const size_t plane = (size_t)h->g.n[0] * h->g.n[1];
+  char* b = static_cast<char*>(buf);
+  for (const StateComp& c : slab_components(h)) {
+    const size_t bytes = (size_t)cnt * plane * c.elem;
+    char* field = c.base + (size_t)p0 * plane * c.elem;
+    const cudaError_t e = pack ? cudaMemcpyAsync(b, field, bytes, cudaMemcpyDeviceToDevice, h->st)
+                               : cudaMemcpyAsync(field, b, bytes, cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, LBM_ECUDA, std::string("slab exchange copy: ") + cudaGetErrorString(e));
+    }
+    b += bytes;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_slab_exchange_bytes(const lbm_handle* h, int side, size_t* bytes) {
+  if (!h || !bytes || (side != 0 && side != 1)) return LBM_EINVAL;
+  if (!h->slab) return LBM_ESTATE;
+  const int cnt = side == 0 ? h->ghost_lo : h->ghost_hi;
+  const size_t plane = (size_t)h->g.n[0] * h->g.n[1];
+  *bytes = (size_t)cnt * plane * (h->Q * h->ssize + (h->D + 3 + h->NDEV) * h->csize);
+  return LBM_OK;
+}
+
+lbm_status lbm_slab_pack(lbm_handle* h, int side, void* dst) {
+  if (!h || !dst) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
+  return slab_copy(h, side, dst, true);
+}
+
+lbm_status lbm_slab_unpack(lbm_handle* h, int side, const void* src) {
+  if (!h || !src) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
+  lbm_status s = slab_copy(h, side, const_cast<void*>(src), false);
+  // the ghost planes changed: a captured step graph stays valid (same
+  // buffers), the stream orders the copies before the next step
+  return s;
+}
+
 namespace {
 void drop_step_graph(lbm_handle* h);
 }
 
 void lbm_destroy(lbm_handle* h) {
   if (!h) return;
+  DeviceGuard dg(h->cfg.device);
   cudaStreamSynchronize(h->st);
   drop_step_graph(h);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   free_ib(h);
-  void* ptrs[] = {h->f, h->f2, h->fcol, h->M, h->M2, h->E, h->P[0], h->P[1], h->A[0], h->A[1], h->feq_inf, h->d_bad};
+  void* ptrs[] = {h->f, h->f2, h->M, h->M2, h->E, h->P[0], h->P[1], h->A[0], h->A[1], h->feq_inf, h->d_bad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : h->ev_pool) cudaEventDestroy(e);
@@ -228,7 +369,64 @@ void lbm_destroy(lbm_handle* h) {
 
 const char* lbm_last_error(const lbm_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
-lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
+// Points of a z slab (host only, no device work): keep[l] = 1 when the
+// point's interpolation (d = 2) and projection (d = 1) stencils lie in the
+// local planes [zlo, zhi) (global z), owned[l] = 1 when z0 <= X_z < z1 (each
+// point has one owner).  The owned planes read the carried moments up to two
+// planes beyond them; those take forcing from points whose d = 2 stencils
+// reach them (within three more planes), whose Lagrangian weights (Eq.
+// weight) need every point sharing one of their nodes (three more).  So a
+// point may only be dropped when its d = 2 stencil stays more than four
+// planes beyond the owned planes; returns 1 when a dropped point comes
+// closer (the halo is too narrow there; 9 ghost planes always suffice).
+static int slab_keep_points(int D, double d_n, int zlo, int zhi, int ghost_lo, int ghost_hi, int z0, int z1, int NL,
+                            const double* X, const double* nrm, int* keep, int* owned) {
+  for (int l = 0; l < NL; ++l) {
+    const double xz = X[l * D + 2];
+    const double fz = std::floor(xz);
+    const int s_lo = int(fz) - 1, s_hi = int(fz) + (xz > fz ? 2 : 1);
+    const double pz = xz + d_n * nrm[l * D + 2];
+    const double fp = std::floor(pz);
+    const int p_lo = int(fp), p_hi = int(fp) + (pz > fp ? 1 : 0);
+    const int f_lo = std::min(s_lo, p_lo), f_hi = std::max(s_hi, p_hi);
+    const bool out_lo = f_lo < zlo && ghost_lo > 0;
+    const bool out_hi = f_hi >= zhi && ghost_hi > 0;
+    keep[l] = (!out_lo && !out_hi) ? 1 : 0;
+    owned[l] = (xz >= double(z0) && xz < double(z1)) ? 1 : 0;
+    if ((out_lo && s_hi >= zlo + ghost_lo - 5) || (out_hi && s_lo < zhi - ghost_hi + 5)) return 1;
+  }
+  return 0;
+}
+
+// z ranges of n slabs of nz planes: owned [z0, z1), ghost planes below and
+// above (halo, none at the domain faces)
+static void slab_ranges(int nz, int n, int halo, int k, int* z0, int* z1, int* glo, int* ghi) {
+  const int base = nz / n, extra = nz % n;
+  *z0 = k * base + std::min(k, extra);
+  *z1 = *z0 + base + (k < extra ? 1 : 0);
+  *glo = *z0 > 0 ? std::min(halo, *z0) : 0;
+  *ghi = *z1 < nz ? std::min(halo, nz - *z1) : 0;
+}
+
+lbm_status lbm_slab_plan(int nz, int n_slabs, int halo, int* out) {
+  if (nz < 1 || n_slabs < 1 || n_slabs > nz || halo < 1 || !out) return LBM_EINVAL;
+  for (int k = 0; k < n_slabs; ++k) slab_ranges(nz, n_slabs, halo, k, out + 4 * k, out + 4 * k + 1, out + 4 * k + 2,
+                                                 out + 4 * k + 3);
+  return LBM_OK;
+}
+
+lbm_status lbm_slab_keep(const lbm_config* cfg, int z0, int z1, int halo, int n_points, const double* X,
+                         const double* normals, int* keep, int* owned) {
+  if (!cfg || cfg->lattice != LBM_D3Q19 || !X || !normals || !keep || !owned || n_points < 0 || z0 < 0 ||
+      z1 > cfg->nz || z1 <= z0 || halo < 1)
+    return LBM_EINVAL;
+  const int glo = z0 > 0 ? std::min(halo, z0) : 0, ghi = z1 < cfg->nz ? std::min(halo, cfg->nz - z1) : 0;
+  return slab_keep_points(3, cfg->d_n, z0 - glo, z1 + ghi, glo, ghi, z0, z1, n_points, X, normals, keep, owned)
+             ? LBM_EGEOM
+             : LBM_OK;
+}
+
+static lbm_status set_geometry_impl(lbm_handle* h, const ib_geometry* gm) {
   if (!h || !gm || gm->struct_size != sizeof(ib_geometry) || gm->n_points <= 0 || !gm->X || !gm->normals ||
       !gm->t_value)
     return fail(h, LBM_EINVAL, "invalid geometry arguments");
@@ -237,6 +435,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     return fail(h, LBM_EINVAL, "invalid polygon");
   if (gm->shape == IB_SHAPE_ELLIPSE && h->D != 2) return fail(h, LBM_EINVAL, "ellipse is 2D only");
   if (gm->shape == IB_SHAPE_MASK && !gm->mask) return fail(h, LBM_EINVAL, "mask missing");
+  DeviceGuard dg(h->cfg.device);
   CK(cudaStreamSynchronize(h->st));
   free_ib(h);
   const int D = h->D, NL = gm->n_points;
@@ -289,6 +488,16 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
   alloc((void**)&count, 4);
   if (s) goto done;
   {
+// a CUDA error from here on releases the temporaries and the partial setup
+#define GCK(call)                                                                                     \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
+      cudaGetLastError();                                                                             \
+      s = fail(h, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+      goto done;                                                                                      \
+    }                                                                                                 \
+  } while (0)
     std::vector<double> zeros((size_t)NL * D, 0.0);
     std::vector<int> tb(NL, 0);
     if (gm->tbc)
@@ -299,6 +508,17 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     up(h->tB, gm->t_value, NL * 8);
     up(h->tbc, tb.data(), NL * 4);
     if (s) goto done;
+    {
+      double tsum = 0.0;
+      int nd = 0;
+      for (int l = 0; l < NL; ++l)
+        if (tb[l] == IB_T_DIRICHLET) {
+          tsum += gm->t_value[l];
+          ++nd;
+        }
+      h->has_dirichlet = nd > 0;
+      h->T_wall = nd > 0 ? tsum / nd : 0.0;
+    }
     ShapeDev sd{};
     sd.kind = gm->shape;
     for (int a = 0; a < 3; ++a) sd.c[a] = gm->center[a];
@@ -319,10 +539,10 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
       sd.mask = dmask;
     }
     if (s) goto done;
-    CK(cudaMemsetAsync(derr, 0, 4, h->st));
-    CK(cudaMemsetAsync(count, 0, 4, h->st));
-    CK(cudaMemsetAsync(h->row_of_node, 0xff, N * 4, h->st));
-    CK(cudaMemsetAsync(h->forced, 0, N, h->st));
+    GCK(cudaMemsetAsync(derr, 0, 4, h->st));
+    GCK(cudaMemsetAsync(count, 0, 4, h->st));
+    GCK(cudaMemsetAsync(h->row_of_node, 0xff, N * 4, h->st));
+    GCK(cudaMemsetAsync(h->forced, 0, N, h->st));
     if ((s = launch(h, kProfOther, [&] { k_classify<<<nblk(N, 256), 256, 0, h->st>>>(h->g, D, sd, h->inside); })))
       goto done;
     IBSetupDev sdv;
@@ -346,9 +566,9 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
          })))
       goto done;
     int herr = 0, hcount = 0;
-    CK(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(&hcount, count, 4, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    GCK(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, h->st));
+    GCK(cudaMemcpyAsync(&hcount, count, 4, cudaMemcpyDeviceToHost, h->st));
+    GCK(cudaStreamSynchronize(h->st));
     if (herr) {
       s = fail(h, LBM_EGEOM, herr == 1 ? "an immersed-boundary stencil leaves the domain"
                                        : "a Lagrangian point has no interior node in its support");
@@ -363,7 +583,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     alloc((void**)&head, (size_t)nnz * 4);
     alloc((void**)&head_scan, (size_t)nnz * 4);
     if (s) goto done;
-    CK(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, keys, keys_sorted, nnz, 0, bits, h->st));
+    GCK(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, keys, keys_sorted, nnz, 0, bits, h->st));
     const int NLKS = NL * KS;
     if ((s = launch(h, kProfOther, [&] {
            k_csr_heads<<<nblk(nnz, 256), 256, 0, h->st>>>(nnz, NLKS, keys_sorted, head);
@@ -372,17 +592,17 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     size_t tmp2 = 0;
     cub::DeviceScan::InclusiveSum(nullptr, tmp2, head, head_scan, nnz, h->st);
     if (tmp2 > tmp_bytes) {
-      CK(cudaStreamSynchronize(h->st));
+      GCK(cudaStreamSynchronize(h->st));
       cudaFree(tmp);
       tmp = nullptr;
       tmp_bytes = tmp2;
       alloc(&tmp, tmp_bytes);
       if (s) goto done;
     }
-    CK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, head, head_scan, nnz, h->st));
+    GCK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, head, head_scan, nnz, h->st));
     int nrows = 0;
-    CK(cudaMemcpyAsync(&nrows, head_scan + (nnz - 1), 4, cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    GCK(cudaMemcpyAsync(&nrows, head_scan + (nnz - 1), 4, cudaMemcpyDeviceToHost, h->st));
+    GCK(cudaStreamSynchronize(h->st));
     h->n_rows = nrows;
     alloc((void**)&h->row_ptr, (size_t)(nrows + 1) * 4);
     alloc((void**)&h->cell_id, (size_t)nrows * 4);
@@ -393,7 +613,7 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
     alloc((void**)&h->FU, (size_t)nrows * D * 8);
     alloc((void**)&h->WQ, (size_t)nrows * 8);
     if (s) goto done;
-    CK(cudaMemcpyAsync(h->row_ptr + nrows, &h->nnz, 4, cudaMemcpyHostToDevice, h->st));
+    GCK(cudaMemcpyAsync(h->row_ptr + nrows, &h->nnz, 4, cudaMemcpyHostToDevice, h->st));
     if ((s = launch(h, kProfOther, [&] {
            k_csr_fill<<<nblk(nnz, 256), 256, 0, h->st>>>(nnz, NLKS, KS, keys_sorted, head_scan, h->row_ptr,
                                                           h->cell_id, h->col, h->slot_of_entry);
@@ -419,10 +639,10 @@ lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
            k_row_map<<<nblk(nrows, 256), 256, 0, h->st>>>(nrows, h->cell_id, h->row_of_node, h->forced);
          })))
       goto done;
-    CK(cudaMemsetAsync(h->G, 0, NL * (D + 2) * 8, h->st));
-    CK(cudaMemsetAsync(h->FU, 0, (size_t)nrows * D * 8, h->st));
-    CK(cudaMemsetAsync(h->WQ, 0, (size_t)nrows * 8, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    GCK(cudaMemsetAsync(h->G, 0, NL * (D + 2) * 8, h->st));
+    GCK(cudaMemsetAsync(h->FU, 0, (size_t)nrows * D * 8, h->st));
+    GCK(cudaMemsetAsync(h->WQ, 0, (size_t)nrows * 8, h->st));
+    GCK(cudaStreamSynchronize(h->st));
     h->has_ib = true;
     h->geom_version++;
   }
@@ -433,6 +653,75 @@ done:
     if (p) cudaFree(p);
   if (s) free_ib(h);
   return s;
+#undef GCK
+}
+
+lbm_status ib_set_geometry(lbm_handle* h, const ib_geometry* gm) {
+  if (!h || !gm || gm->struct_size != sizeof(ib_geometry) || gm->n_points <= 0 || !gm->X || !gm->normals ||
+      !gm->t_value)
+    return fail(h, LBM_EINVAL, "invalid geometry arguments");
+  if (!h->slab) return set_geometry_impl(h, gm);
+  // A z slab keeps the points whose interpolation (d = 2) and projection
+  // (d = 1) stencils lie in its local planes (slab_keep_points); the
+  // geometry stays in global coordinates.
+  const int D = h->D, NL = gm->n_points;
+  std::vector<int> kflag(NL), oflag(NL);
+  if (slab_keep_points(D, h->cfg.d_n, h->g.zoff, h->g.zoff + h->g.n[2], h->ghost_lo, h->ghost_hi, h->slab_z0,
+                       h->slab_z1, NL, gm->X, gm->normals, kflag.data(), oflag.data()))
+    return fail(h, LBM_EGEOM, "slab halo too narrow for the immersed body at a slab boundary");
+  std::vector<int> keep;
+  for (int l = 0; l < NL; ++l)
+    if (kflag[l]) keep.push_back(l);
+  DeviceGuard dg(h->cfg.device);
+  if (keep.empty()) {
+    CK(cudaStreamSynchronize(h->st));
+    free_ib(h);
+    h->slab_points.clear();
+    h->geom_version++;
+    return LBM_OK;
+  }
+  const int n = (int)keep.size();
+  std::vector<double> X((size_t)n * D), nrm((size_t)n * D), ut((size_t)n * D), tv(n);
+  std::vector<int> tb(n, 0);
+  for (int k = 0; k < n; ++k) {
+    const int l = keep[k];
+    for (int a = 0; a < D; ++a) {
+      X[k * D + a] = gm->X[l * D + a];
+      nrm[k * D + a] = gm->normals[l * D + a];
+      ut[k * D + a] = gm->u_target ? gm->u_target[l * D + a] : 0.0;
+    }
+    tv[k] = gm->t_value[l];
+    if (gm->tbc) tb[k] = gm->tbc[l];
+  }
+  ib_geometry g2 = *gm;
+  g2.n_points = n;
+  g2.X = X.data();
+  g2.normals = nrm.data();
+  g2.u_target = ut.data();
+  g2.t_value = tv.data();
+  g2.tbc = tb.data();
+  if (gm->shape == IB_SHAPE_MASK) g2.mask = gm->mask + (size_t)h->g.zoff * h->g.n[0] * h->g.n[1];
+  lbm_status s = set_geometry_impl(h, &g2);
+  if (s) return s;
+  h->slab_points = keep;
+  std::vector<unsigned char> own(n);
+  for (int k = 0; k < n; ++k) own[k] = (unsigned char)oflag[keep[k]];
+  if (cudaMalloc((void**)&h->owned, n) != cudaSuccess) {
+    cudaGetLastError();
+    free_ib(h);
+    return fail(h, LBM_ENOMEM, "device allocation failed");
+  }
+  CK(cudaMemcpy(h->owned, own.data(), n, cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+lbm_status lbm_slab_points(const lbm_handle* h, int* n_points, int* global_index) {
+  if (!h || !n_points) return LBM_EINVAL;
+  if (!h->slab) return LBM_ESTATE;
+  *n_points = (int)h->slab_points.size();
+  if (global_index)
+    for (size_t k = 0; k < h->slab_points.size(); ++k) global_index[k] = h->slab_points[k];
+  return LBM_OK;
 }
 
 namespace {
@@ -490,10 +779,11 @@ lbm_status capture_step_graph(lbm_handle* h) {
 
 lbm_status lbm_step(lbm_handle* h, int n_steps) {
   if (!h || n_steps < 0) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   if (h->sticky) return (lbm_status)h->sticky;
   // pairs of steps replay a captured graph (fewer host launches for small
-  // grids); profiling runs, the unfused form and odd remainders step eagerly
-  const bool graphs = h->use_graph && h->use_fused && !h->prof;
+  // grids); profiling runs and odd remainders step eagerly
+  const bool graphs = h->use_graph && !h->prof;
   int k = 0;
   while (k < n_steps) {
     if (graphs && h->stepped && n_steps - k >= 2) {
@@ -516,6 +806,7 @@ lbm_status lbm_step(lbm_handle* h, int n_steps) {
 
 lbm_status lbm_check(lbm_handle* h) {
   if (!h) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   CK(cudaMemsetAsync(h->d_bad, 0, sizeof(unsigned long long), h->st));
   lbm_status s = h->ops->health(h, h->d_bad);
   if (s) return s;
@@ -531,6 +822,7 @@ lbm_status lbm_check(lbm_handle* h) {
 
 lbm_status lbm_get_fields(lbm_handle* h, int dst_is_device, double* rho, double* u, double* T, double* p) {
   if (!h) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   const long long N = h->g.N;
   if (dst_is_device) {
     lbm_status s = h->ops->fields(h, rho, u, T, p);
@@ -555,6 +847,7 @@ lbm_status lbm_get_fields(lbm_handle* h, int dst_is_device, double* rho, double*
 
 lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* E) {
   if (!h || !f || !E) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   const long long N = h->g.N;
   if (dst_is_device) {
     lbm_status s = h->ops->get_state(h, f, E);
@@ -576,6 +869,7 @@ lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* E)
 
 lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, const double* E) {
   if (!h || !f || !E) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   const long long N = h->g.N;
   if (src_is_device) {
     lbm_status s = h->ops->set_state(h, f, E);
@@ -609,13 +903,8 @@ int state_arrays(lbm_handle* h, void** ptr, size_t* bytes) {
   int k = 0;
   ptr[k] = h->f;
   bytes[k++] = N * h->Q * h->ssize;
-  if (h->use_fused) {
-    ptr[k] = h->M;
-    bytes[k++] = N * (h->D + 2) * h->csize;
-  } else {
-    ptr[k] = h->E;
-    bytes[k++] = N * h->csize;
-  }
+  ptr[k] = h->M;
+  bytes[k++] = N * (h->D + 2) * h->csize;
   ptr[k] = h->P[h->cur];
   bytes[k++] = N * h->csize;
   ptr[k] = h->A[h->cur];
@@ -633,7 +922,7 @@ StateHeader state_header(lbm_handle* h) {
   hd.nx = h->g.n[0];
   hd.ny = h->g.n[1];
   hd.nz = h->g.n[2];
-  hd.fused = h->use_fused;
+  hd.fused = 1;
   hd.N = h->g.N;
   return hd;
 }
@@ -642,6 +931,7 @@ StateHeader state_header(lbm_handle* h) {
 
 lbm_status lbm_save_state(lbm_handle* h, const char* path) {
   if (!h || !path) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   void* ptr[4];
   size_t bytes[4];
   const int n = state_arrays(h, ptr, bytes);
@@ -666,6 +956,7 @@ lbm_status lbm_save_state(lbm_handle* h, const char* path) {
 
 lbm_status lbm_load_state(lbm_handle* h, const char* path) {
   if (!h || !path) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   void* ptr[4];
   size_t bytes[4];
   const int n = state_arrays(h, ptr, bytes);
@@ -697,6 +988,7 @@ lbm_status lbm_load_state(lbm_handle* h, const char* path) {
 lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho, const double* u,
                           const double* T) {
   if (!h || !rho || !u || !T) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   const long long N = h->g.N;
   if (src_is_device) {
     lbm_status s = h->ops->set_fields(h, rho, u, T);
@@ -719,8 +1011,17 @@ lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho, c
 
 lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, double* work, double* per_point) {
   if (!h) return LBM_EINVAL;
+  if (h->slab && !h->has_ib) {
+    // a slab the body does not reach contributes nothing
+    if (force)
+      for (int a = 0; a < 3; ++a) force[a] = 0.0;
+    if (heat) *heat = 0.0;
+    if (work) *work = 0.0;
+    return LBM_OK;
+  }
+  DeviceGuard dg(h->cfg.device);
   if (!h->has_ib) return fail(h, LBM_ESTATE, "no immersed body");
-  lbm_status s = launch(h, kProfOther, [&] { k_wall_loads<<<1, 256, 0, h->st>>>(h->D, h->NL, h->G, h->W, h->loads); });
+  lbm_status s = launch(h, kProfOther, [&] { k_wall_loads<<<1, 256, 0, h->st>>>(h->D, h->NL, h->G, h->W, h->owned, h->loads); });
   if (s) return s;
   double out[5];
   CK(cudaMemcpyAsync(out, h->loads, 5 * 8, cudaMemcpyDeviceToHost, h->st));
@@ -730,6 +1031,72 @@ lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, doub
     for (int a = 0; a < 3; ++a) force[a] = out[a];
   if (heat) *heat = out[3];
   if (work) *work = out[4];
+  return LBM_OK;
+}
+
+lbm_status lbm_get_wall_diagnostics(lbm_handle* h, double coeffs[4], double* per_point) {
+  if (!h) return LBM_EINVAL;
+  if (!h->has_ib) return fail(h, LBM_ESTATE, "no immersed body");
+  DeviceGuard dg(h->cfg.device);
+  const int D = h->D;
+  if (coeffs) {
+    double force[3], heat = 0.0;
+    lbm_status s = lbm_get_wall_loads(h, force, &heat, nullptr, nullptr);
+    if (s) return s;
+    // drag along the inflow direction, lift along the perpendicular axes
+    double ed[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0}, nd = 0.0;
+    for (int a = 0; a < D; ++a) nd += h->cfg.inflow_dir[a] * h->cfg.inflow_dir[a];
+    nd = std::sqrt(nd);
+    for (int a = 0; a < D; ++a) ed[a] = h->cfg.inflow_dir[a] / nd;
+    if (D == 2) {
+      e1[0] = -ed[1];
+      e1[1] = ed[0];
+    } else {
+      e1[0] = -ed[1] * ed[0];
+      e1[1] = 1.0 - ed[1] * ed[1];
+      e1[2] = -ed[1] * ed[2];
+      const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+      for (int a = 0; a < 3; ++a) e1[a] /= n1;
+      e2[0] = ed[1] * e1[2] - ed[2] * e1[1];
+      e2[1] = ed[2] * e1[0] - ed[0] * e1[2];
+      e2[2] = ed[0] * e1[1] - ed[1] * e1[0];
+    }
+    const double Lr = h->cfg.ref_length;
+    const double q = 0.5 * h->rho_inf * h->u_mag * h->u_mag;
+    const double A = D == 2 ? Lr : M_PI * Lr * Lr / 4.0;
+    const double S = D == 2 ? M_PI * Lr : M_PI * Lr * Lr;
+    double fd = 0.0, f1 = 0.0, f2 = 0.0;
+    for (int a = 0; a < D; ++a) {
+      fd += force[a] * ed[a];
+      f1 += force[a] * e1[a];
+      f2 += force[a] * e2[a];
+    }
+    coeffs[0] = fd / (q * A);
+    coeffs[1] = f1 / (q * A);
+    coeffs[2] = D == 3 ? f2 / (q * A) : 0.0;
+    coeffs[3] = (h->has_dirichlet && h->T_wall != h->theta_inf)
+                    ? heat * Lr / (h->lam * (h->T_wall - h->theta_inf) * S)
+                    : 0.0;
+  }
+  if (per_point) {
+    const size_t bytes = (size_t)h->NL * (2 * D + 3) * 8;
+    double* buf = nullptr;
+    int* derr = nullptr;
+    CK(cudaMalloc(&buf, bytes + 16));
+    derr = reinterpret_cast<int*>(reinterpret_cast<char*>(buf) + bytes);
+    lbm_status s = LBM_OK;
+    if (cudaMemsetAsync(derr, 0, 4, h->st) != cudaSuccess) s = fail(h, LBM_ECUDA, "diagnostics memset");
+    if (!s) s = h->ops->wall_diag(h, buf, derr);
+    int herr = 0;
+    if (!s && (cudaMemcpyAsync(per_point, buf, bytes, cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+               cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+               cudaStreamSynchronize(h->st) != cudaSuccess))
+      s = fail(h, LBM_ECUDA, "diagnostics copy");
+    cudaStreamSynchronize(h->st);
+    cudaFree(buf);
+    if (!s && herr) s = fail(h, LBM_EGEOM, "a diagnostic stencil leaves the domain");
+    if (s) return s;
+  }
   return LBM_OK;
 }
 
@@ -757,6 +1124,7 @@ lbm_status ib_get_sizes(const lbm_handle* h, int* n_rows, int* nnz, int* n_point
 lbm_status ib_get_setup(lbm_handle* h, double* phi, double* W, double* Xstar, double* dBV, uint8_t* inside,
                         int* row_ptr, int* cell_id, int* col, double* wt) {
   if (!h) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   if (!h->has_ib) return fail(h, LBM_ESTATE, "no immersed body");
   const int NL = h->NL, D = h->D;
   if (phi) CK(cudaMemcpyAsync(phi, h->phi, NL * 8, cudaMemcpyDeviceToHost, h->st));
@@ -774,6 +1142,7 @@ lbm_status ib_get_setup(lbm_handle* h, double* phi, double* W, double* Xstar, do
 
 lbm_status lbm_profile(lbm_handle* h, int enable, int reset) {
   if (!h) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   CK(cudaStreamSynchronize(h->st));
   if (reset) {
     for (auto& e : h->ev_used) {
@@ -792,6 +1161,7 @@ lbm_status lbm_profile(lbm_handle* h, int enable, int reset) {
 
 lbm_status lbm_get_profile(lbm_handle* h, double ms[5], long long launches[5]) {
   if (!h) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
   CK(cudaStreamSynchronize(h->st));
   for (auto& e : h->ev_used) {
     float t = 0.f;

@@ -96,9 +96,9 @@ lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_batch** out) {
     if (cfgs[k].lattice != cfgs[0].lattice || cfgs[k].precision != cfgs[0].precision ||
         cfgs[k].device != cfgs[0].device)
       return LBM_EINVAL;
+  DeviceGuard dg(cfgs[0].device);
   lbm_batch* b = new lbm_batch();
-  if (cudaSetDevice(cfgs[0].device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+  if (dg.status() != cudaSuccess || cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
     delete b;
     return LBM_ECUDA;
   }
@@ -121,6 +121,7 @@ lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_batch** out) {
 
 void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
+  DeviceGuard dg(b->plan.cases.empty() ? 0 : b->plan.cases[0]->cfg.device);
   drop_graph(b);
   for (lbm_handle* h : b->plan.cases) lbm_destroy(h);
   BatchPlan& pl = b->plan;
@@ -159,6 +160,7 @@ lbm_status lbm_batch_get_plan(const lbm_batch* b, int* tile_rows, int* schedule)
 
 lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
   if (!b || n_steps < 0) return LBM_EINVAL;
+  DeviceGuard dg(b->plan.cases[0]->cfg.device);
   int done = 0;
   while (done < n_steps) {
     if (!plan_current(b)) {
@@ -198,6 +200,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
 
 lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps) {
   if (!b || n_steps < 0) return LBM_EINVAL;
+  DeviceGuard dg(b->plan.cases[0]->cfg.device);
   for (lbm_handle* h : b->plan.cases) {
     lbm_status s = lbm_step(h, n_steps);
     if (s) return bfail(b, s, h->err);
@@ -207,6 +210,7 @@ lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps) {
 
 lbm_status lbm_batch_sync(lbm_batch* b) {
   if (!b) return LBM_EINVAL;
+  DeviceGuard dg(b->plan.cases[0]->cfg.device);
   return cudaStreamSynchronize(b->st) == cudaSuccess ? LBM_OK : bfail(b, LBM_ECUDA, "sync");
 }
 
@@ -216,6 +220,7 @@ lbm_status lbm_batch_sync(lbm_batch* b) {
 // from / appended to that text file ("key tile_rows schedule" lines).
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, double* best_ms) {
   if (!b || steps <= 0) return LBM_EINVAL;
+  DeviceGuard dg(b->plan.cases[0]->cfg.device);
   BatchPlan& p = b->plan;
   std::ostringstream key;
   key << p.cases.size() << ":" << p.cases[0]->cfg.lattice << ":" << p.cases[0]->cfg.precision;

@@ -10,8 +10,8 @@
 #include "handle.cuh"
 #include "ib.cuh"
 #include "physics.cuh"
+#include "state.cuh"
 #include "step_fused.cuh"
-#include "step_v1.cuh"
 
 namespace lbmib_host {
 
@@ -29,21 +29,6 @@ struct Engine {
     p.use_ac = h->cfg.use_ac;
     return p;
   }
-  static StepBufs<S, C> bufs(lbm_handle* h) {
-    StepBufs<S, C> b;
-    b.f = (S*)h->f;
-    b.fcol = (C*)h->fcol;
-    b.M = (C*)h->M;
-    b.E = (C*)h->E;
-    b.Pp = (const C*)h->P[h->cur];
-    b.Pn = (C*)h->P[1 - h->cur];
-    b.Ap = (const C*)h->A[h->cur];
-    b.An = (C*)h->A[1 - h->cur];
-    b.row_of_node = h->has_ib ? h->row_of_node : nullptr;
-    b.FU = h->FU;
-    b.WQ = h->WQ;
-    return b;
-  }
   static lbm_status reset_aux(lbm_handle* h) {
     lbm_handle* hh = h;
     return launch(hh, kProfOther, [&] {
@@ -55,7 +40,7 @@ struct Engine {
   // collision planes, and the last wave of CTAs runs partly empty, so take
   // the chunk that minimises (waves of CTAs) x (planes a CTA collides).
   static void choose_zchunk(lbm_handle* h) {
-    if (L::D != 3 || !h->use_fused || h->zchunk_fixed) return;
+    if (L::D != 3 || h->zchunk_fixed) return;
     using Lay = FusedLayout<L, S, C, 0>;
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->cfg.device) != cudaSuccess ||
@@ -153,44 +138,17 @@ struct Engine {
   static lbm_status ib_force(lbm_handle* h) {
     const IBStepDev s = ib_step_dev(h);
     lbm_status st = launch(h, kProfIBForce, [&] {
-      k_ib_force<L, S, C><<<nblk(h->NL, kIBPointsPerWarp * kIBWarps), 32 * kIBWarps, 0, h->st>>>(
-          h->g, s, (const S*)h->f, (const C*)h->E, h->use_fused ? (const C*)h->M : nullptr);
+      k_ib_force<L, S, C><<<nblk(h->NL, kIBPointsPerWarp * kIBWarps), 32 * kIBWarps, 0, h->st>>>(h->g, s,
+                                                                                              (const C*)h->M);
     });
     if (st) return st;
-    if (h->use_fused)
-      return launch(h, kProfIBSpread, [&] {
-        k_ib_spread_apply<C><<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->g.N, h->n_rows, h->row_ptr, h->col,
-                                                                      h->wt, h->G, h->cell_id, h->FU, h->WQ,
-                                                                      (C*)h->M);
-      });
     return launch(h, kProfIBSpread, [&] {
-      k_ib_spread<<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->n_rows, h->row_ptr, h->col, h->wt, h->G,
-                                                          h->FU, h->WQ);
+      k_ib_spread_apply<C><<<nblk(h->n_rows, 128), 128, 0, h->st>>>(L::D, h->g.N, h->n_rows, h->row_ptr, h->col,
+                                                                    h->wt, h->G, h->cell_id, h->FU, h->WQ,
+                                                                    (C*)h->M);
     });
   }
   static lbm_status bc(lbm_handle* h) {
-    if (h->use_fused) return bc_fused(h);
-    for (int face = 0; face < 2 * L::D; ++face) {
-      if (h->cfg.bc[face] != LBM_BC_OUTLET) continue;
-      FacePlane fp{face / 2, face % 2};
-      lbm_status s = launch(h, kProfBC, [&] {
-        k_bc_outlet<L, S, C><<<nblk(fp.count(h->g), 128), 128, 0, h->st>>>(h->g, (S*)h->f, (C*)h->E, fp);
-      });
-      if (s) return s;
-    }
-    for (int face = 0; face < 2 * L::D; ++face) {
-      const int t = h->cfg.bc[face];
-      if (t != LBM_BC_INLET && t != LBM_BC_FARFIELD) continue;
-      FacePlane fp{face / 2, face % 2};
-      lbm_status s = launch(h, kProfBC, [&] {
-        k_bc_equilibrium<L, S, C><<<nblk(fp.count(h->g), 128), 128, 0, h->st>>>(
-            h->g, (S*)h->f, (C*)h->E, fp, (const C*)h->feq_inf, C(h->E_inf));
-      });
-      if (s) return s;
-    }
-    return LBM_OK;
-  }
-  static lbm_status bc_fused(lbm_handle* h) {
     BCFaces bf;
     int maxplane = 0;
     const int skip_x = bc_in_kernel(h) ? 1 : 0;
@@ -207,21 +165,40 @@ struct Engine {
           h->g, (S*)h->f, (C*)h->M, bf, (const C*)h->feq_inf, C(h->E_inf), skip_x);
     });
   }
-  // fused form: predicted moments from the populations and rho E
+  // predicted moments from the populations and rho E
   static lbm_status refresh_moments(lbm_handle* h) {
-    if (!h->use_fused) return LBM_OK;
     return launch(h, kProfOther, [&] {
       k_moments<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, (const S*)h->f, (const C*)h->E, (C*)h->M);
     });
   }
-  // fused form: rho E lives in the moment buffer; copy it out for readback
+  // rho E lives in the moment buffer; copy it out for readback
   static lbm_status sync_energy(lbm_handle* h) {
-    if (!h->use_fused) return LBM_OK;
     CK(cudaMemcpyAsync(h->E, (const C*)h->M + (size_t)(L::D + 1) * h->g.N, h->g.N * sizeof(C),
                        cudaMemcpyDeviceToDevice, h->st));
     return LBM_OK;
   }
   static lbm_status ib_part(lbm_handle* h) { return h->has_ib ? ib_force(h) : LBM_OK; }
+  static lbm_status wall_diag(lbm_handle* h, double* out, int* err) {
+    DiagDev d;
+    d.NL = h->NL;
+    d.D = L::D;
+    d.R = h->R;
+    d.Cv = h->Cv;
+    d.mu = h->mu;
+    d.d_n = h->cfg.d_n;
+    d.p_inf = h->rho_inf * h->R * h->theta_inf;
+    d.q_inf = 0.5 * h->rho_inf * h->u_mag * h->u_mag;
+    d.X = h->X;
+    d.nrm = h->nrm;
+    d.uB = h->uB;
+    d.psten_node = h->psten_node;
+    d.psten_w = h->psten_w;
+    d.out = out;
+    d.err = err;
+    return launch(h, kProfOther, [&] {
+      k_wall_diag<L, C><<<nblk(h->NL, 128), 128, 0, h->st>>>(h->g, d, (const C*)h->M);
+    });
+  }
   static lbm_status bc_part(lbm_handle* h) { return bc(h); }
   static FusedArgs<S, C> fused_args(lbm_handle* h, int parity) {
     // parity 0: the handle's current buffers; parity 1: the swapped ones
@@ -253,7 +230,7 @@ struct Engine {
   // neighbour, and no outlet face on y or z (whose copies would read x-face
   // nodes before the kernel's equilibrium wins on the edges)
   static bool bc_in_kernel(lbm_handle* h) {
-    if (!h->use_fused || !h->bc_in_kernel || h->g.n[0] < 4) return false;
+    if (!h->bc_in_kernel || h->g.n[0] < 4) return false;
     if (h->cfg.bc[0] == LBM_BC_PERIODIC || h->cfg.bc[1] == LBM_BC_PERIODIC) return false;
     if (h->cfg.bc[1] == LBM_BC_OUTLET && (h->g.n[0] - 1) % FusedTile<L, C>::TX == 0) return false;
     for (int f = 2; f < 2 * L::D; ++f)
@@ -273,10 +250,6 @@ struct Engine {
     std::vector<int> tx(n), ty(n), tz(n);
     for (int k = 0; k < n; ++k) {
       lbm_handle* h = b->cases[k];
-      if (!h->use_fused) {
-        b->err = "batched stepping needs the fused step";
-        return LBM_EUNSUPPORTED;
-      }
       for (int p = 0; p < 2; ++p) {
         CaseDesc<S, C>& d = p ? d1[k] : d0[k];
         d.g = h->g;
@@ -361,8 +334,6 @@ struct Engine {
         IBCaseDesc<S, C> d;
         d.g = h->g;
         d.s = ib_step_dev(h);
-        d.f = (const S*)(p ? h->f2 : h->f);
-        d.E = (const C*)h->E;
         d.M = (const C*)(p ? h->M2 : h->M);
         ib[p].push_back(d);
         SpreadCaseDesc<C> q;
@@ -474,19 +445,7 @@ struct Engine {
   static lbm_status step(lbm_handle* h) {
     lbm_status s;
     if (h->has_ib && (s = ib_force(h))) return s;
-    const Phys<C> ph = phys(h);
-    if (h->use_fused) {
-      s = fused_step(h, ph);
-    } else {
-      StepBufs<S, C> b = bufs(h);
-      if ((s = launch(h, kProfOther, [&] { k_macro<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, b, ph); })))
-        return s;
-      if ((s = launch(h, kProfStep, [&] { k_collide<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, b, ph); })))
-        return s;
-      s = launch(h, kProfStep,
-                 [&] { k_stream_energy<L, S, C><<<nblk(h->g.N, 256), 256, 0, h->st>>>(h->g, b, ph); });
-    }
-    if (s) return s;
+    if ((s = fused_step(h, phys(h)))) return s;
     if ((s = bc(h))) return s;
     h->cur = 1 - h->cur;
     return LBM_OK;
@@ -523,8 +482,9 @@ struct Engine {
     });
   }
   static const Ops* ops() {
-    static const Ops o = {&init,   &step,        &fields,      &get_state, &set_state, &set_fields_api,
-                          &health, &batch_build, &batch_fused, &batch_aux, &ib_part,   &bc_part};
+    static const Ops o = {&init,        &step,        &fields,    &get_state, &set_state,
+                          &set_fields_api, &health, &batch_build, &batch_fused, &batch_aux,
+                          &ib_part,     &bc_part,     &wall_diag};
     return &o;
   }
 };
@@ -532,7 +492,7 @@ struct Engine {
 template <class L, class S, class C>
 inline lbm_status Engine<L, S, C>::fused_step(lbm_handle* h, const Phys<C>& ph) {
   const FusedArgs<S, C> a = fused_args(h, 0);
-  lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st, h->zchunk, h->tile_rows); });
+  lbm_status s = launch(h, kProfStep, [&] { launch_fused<L, S, C>(h->g, a, ph, h->st, h->zchunk, 0); });
   if (s) return s;
   std::swap(h->f, h->f2);
   std::swap(h->M, h->M2);

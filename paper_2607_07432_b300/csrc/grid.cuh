@@ -6,12 +6,19 @@
 
 namespace lbmib {
 
+// A face of a z slab that borders a neighbour slab (boundary type next to
+// the LBM_BC_* values): no boundary condition there; its ghost planes are
+// refreshed by the slab exchange.
+constexpr int kBCGhostFace = 4;
+
 // Domain extent and per-axis periodicity.  Non-periodic axes clamp
 // out-of-range stencil reads to the edge node (zero-gradient).
 struct Grid {
   int n[3];
   int per[3];
   long long N;
+  int zoff;  // global z of local plane 0 (a z slab of a larger case; 0 otherwise)
+  float thref;  // reference temperature of 16-bit population storage (see pop_offset)
   __host__ __device__ __forceinline__ int wrap(int a, int v) const {
     if (per[a]) {
       v = v % n[a];
@@ -57,20 +64,37 @@ struct Store<__nv_bfloat16> {
   __device__ __forceinline__ static __nv_bfloat16 save(float v) { return __float2bfloat16_rn(v); }
 };
 
+// Reference value subtracted from population i before it is stored: w_i for
+// FP32 storage; for FP16 / BF16 storage the rest equilibrium at the run's
+// free-stream temperature, f^eq_i(rho = 1, u = 0, theta = thr) =
+// w_i thr + delta_0i (1 - thr) (Eq. feq), so that at theta_inf != 1 the
+// stored deviations near a wall at rest stay small and lose little to the
+// 16-bit rounding (at thr = 1 this is w_i)
 template <class L, class S, class C>
-__device__ __forceinline__ C load_pop(const S* f, int i, long long N, long long n) {
+__device__ __forceinline__ C pop_offset(int i, C thr) {
+  if constexpr (sizeof(S) == 2) {
+    return C(L::w(i)) * thr + (i == 0 ? C(1) - thr : C(0));
+  } else {
+    return C(L::w(i));
+  }
+}
+template <class L, class S, class C>
+__device__ __forceinline__ C load_pop(const S* f, int i, long long N, long long n, C thr) {
   const C v = C(Store<S>::load(f[(long long)i * N + n]));
-  return Store<S>::dev ? v + C(L::w(i)) : v;
+  return Store<S>::dev ? v + pop_offset<L, S, C>(i, thr) : v;
 }
 // the value a population takes after a store and a reload
 template <class L, class S, class C>
-__device__ __forceinline__ C roundtrip_pop(int i, C v) {
-  if (Store<S>::dev) return C(Store<S>::load(Store<S>::save(v - C(L::w(i))))) + C(L::w(i));
+__device__ __forceinline__ C roundtrip_pop(int i, C v, C thr) {
+  if (Store<S>::dev) {
+    const C o = pop_offset<L, S, C>(i, thr);
+    return C(Store<S>::load(Store<S>::save(v - o))) + o;
+  }
   return C(Store<S>::load(Store<S>::save(v)));
 }
 template <class L, class S, class C>
-__device__ __forceinline__ void store_pop(S* f, int i, long long N, long long n, C v) {
-  f[(long long)i * N + n] = Store<S>::save(Store<S>::dev ? v - C(L::w(i)) : v);
+__device__ __forceinline__ void store_pop(S* f, int i, long long N, long long n, C v, C thr) {
+  f[(long long)i * N + n] = Store<S>::save(Store<S>::dev ? v - pop_offset<L, S, C>(i, thr) : v);
 }
 
 }  // namespace lbmib

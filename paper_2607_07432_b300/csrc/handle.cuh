@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/lbmib.h"
+#include "devguard.cuh"
 #include "grid.cuh"
 
 namespace lbmib_host {
@@ -30,20 +31,17 @@ struct lbm_handle {
   size_t csize = 8, ssize = 8;  // compute / storage element sizes
   // device state
   void* f = nullptr;
-  void* fcol = nullptr;
   void* M = nullptr;
   void* E = nullptr;
   void* P[2] = {nullptr, nullptr};
   void* A[2] = {nullptr, nullptr};
   void* feq_inf = nullptr;
   int cur = 0;
-  int use_fused = 1;         // fused shared-memory step (0: unfused global-memory form)
   int zchunk = 16;           // planes per CTA along z in the fused step
   int zchunk_fixed = 0;      // set by the environment: keep it
   int bc_in_kernel = 1;  // far-field boundaries inside the fused kernel when the faces allow it
-  int tile_rows = 0;         // tile height of the 3D FP32 fused step (0 = default)
-  void* f2 = nullptr;        // second population buffer (fused form)
-  void* M2 = nullptr;        // second predicted-moment buffer (fused form)
+  void* f2 = nullptr;        // second population buffer (the fused step reads one, writes the other)
+  void* M2 = nullptr;        // second predicted-moment buffer
   unsigned long long* d_bad = nullptr;
   // immersed boundary
   bool has_ib = false;
@@ -59,6 +57,15 @@ struct lbm_handle {
   int* row_of_node = nullptr;
   unsigned char* forced = nullptr;
   double *G = nullptr, *FU = nullptr, *WQ = nullptr, *loads = nullptr;
+  double T_wall = 0.0;       // mean Dirichlet temperature target (Nusselt number)
+  bool has_dirichlet = false;
+  // z slab of a larger case (lbm_create_slab): global owned planes
+  // [z0, z1), ghost planes below / above, global nz; the Lagrangian points
+  // kept by the slab (global indices) and which of them it owns
+  bool slab = false;
+  int slab_z0 = 0, slab_z1 = 0, ghost_lo = 0, ghost_hi = 0, nz_global = 0;
+  std::vector<int> slab_points;
+  unsigned char* owned = nullptr;
   // bookkeeping
   std::string err;
   long long launches = 0;
@@ -147,6 +154,8 @@ struct Ops {
   // per-case parts of a step around the fused kernel
   lbm_status (*ib_part)(lbm_handle*);
   lbm_status (*bc_part)(lbm_handle*);
+  // wall diagnostics of the current state into a device array (NL rows)
+  lbm_status (*wall_diag)(lbm_handle*, double* out, int* err);
 };
 
 // A set of cases advanced together (lbm_batch_*): one fused launch covers

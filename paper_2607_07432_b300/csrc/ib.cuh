@@ -41,7 +41,7 @@ static __global__ void k_classify(Grid g, int D, ShapeDev s, unsigned char* insi
   const int x = int(n % g.n[0]);
   const int y = int((n / g.n[0]) % g.n[1]);
   const int z = int(n / ((long long)g.n[0] * g.n[1]));
-  const double p[3] = {double(x), double(y), double(z)};
+  const double p[3] = {double(x), double(y), double(z + g.zoff)};
   bool in = false;
   if (s.kind == kShapeMask) {
     in = s.mask[n] != 0;
@@ -193,7 +193,7 @@ static __global__ void k_stencils(Grid g, IBSetupDev s) {
         int idx[3] = {0, 0, 0};
         bool ok = true;
         for (int a = 0; a < D; ++a) {
-          int v = node[a];
+          int v = node[a] - (a == 2 ? g.zoff : 0);
           if (g.per[a]) {
             v = v % g.n[a];
             if (v < 0) v += g.n[a];
@@ -241,7 +241,7 @@ static __global__ void k_stencils(Grid g, IBSetupDev s) {
         int idx[3] = {0, 0, 0};
         bool ok = true;
         for (int a = 0; a < D; ++a) {
-          int v = node[a];
+          int v = node[a] - (a == 2 ? g.zoff : 0);
           if (g.per[a]) {
             v = v % g.n[a];
             if (v < 0) v += g.n[a];
@@ -391,33 +391,18 @@ static __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// predicted moments of one node (Sec. 2.2): from the stored moments
-// rho, rho u, rho E when M is given, else from the post-stream populations.
-// Evaluated in the compute type C (the precision of the stored state) and
-// widened to FP64 for the Lagrangian sums.
-template <class L, class S, class C>
-__device__ __forceinline__ void node_pred_c(const S* f, const C* E, const C* M, long long N, long long n,
-                                            C& rho_o, C* j_o, C* u_o, C& T_o, C Cv) {
+// predicted moments of one node (Sec. 2.2) from the carried moments rho,
+// rho u, rho E, evaluated in the compute type C (the precision of the
+// stored state) and widened to FP64 for the Lagrangian sums.
+template <class L, class C>
+__device__ __forceinline__ void node_pred_c(const C* M, long long N, long long n, C& rho_o, C* j_o, C* u_o,
+                                            C& T_o, C Cv) {
   constexpr int D = L::D;
   C rho, j[3], En;
-  if (M) {
-    rho = M[n];
+  rho = M[n];
 #pragma unroll
-    for (int a = 0; a < D; ++a) j[a] = M[(1 + a) * N + n];
-    En = M[(1 + D) * N + n];
-  } else {
-    rho = C(0);
-    for (int a = 0; a < 3; ++a) j[a] = C(0);
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      const C v = load_pop<L, S, C>(f, i, N, n);
-      rho += v;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
-    }
-    En = E[n];
-  }
+  for (int a = 0; a < D; ++a) j[a] = M[(1 + a) * N + n];
+  En = M[(1 + D) * N + n];
   C uu = C(0), u[3], T;
   if constexpr (sizeof(C) == 8) {
 #pragma unroll
@@ -444,11 +429,11 @@ __device__ __forceinline__ void node_pred_c(const S* f, const C* E, const C* M, 
   T_o = T;
 }
 
-template <class L, class S, class C>
-__device__ __forceinline__ void node_pred(const S* f, const C* E, const C* M, long long N, long long n,
-                                          double& rho_o, double* j_o, double* u_o, double& T_o, C Cv) {
+template <class L, class C>
+__device__ __forceinline__ void node_pred(const C* M, long long N, long long n, double& rho_o, double* j_o,
+                                          double* u_o, double& T_o, C Cv) {
   C rho, j[3], u[3], T;
-  node_pred_c<L, S, C>(f, E, M, N, n, rho, j, u, T, Cv);
+  node_pred_c<L, C>(M, N, n, rho, j, u, T, Cv);
   rho_o = double(rho);
 #pragma unroll
   for (int a = 0; a < L::D; ++a) {
@@ -467,8 +452,7 @@ constexpr int kIBWarps = 2;
 // Body of the IB force step for block blk (kIBWarps warps of
 // kIBPointsPerWarp Lagrangian points each) of one case.
 template <class L, class S, class C>
-__device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s, const S* f, const C* E,
-                                              const C* M, int blk) {
+__device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s, const C* M, int blk) {
   constexpr int D = L::D;
   constexpr int KS = D == 2 ? 16 : 64;
   constexpr int KP = D == 2 ? 4 : 8;
@@ -500,7 +484,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
           if constexpr (sizeof(C) == 8) {
             const double w = s.sten_w[l * KS + k];
             double rho, j[3], u[3], T;
-            node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
+            node_pred<L, C>(M, g.N, n, rho, j, u, T, C(s.Cv));
             v[0] = rho * w;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -512,7 +496,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
             // FP32 state: the slot products in FP32, their sums in FP64
             const C w = C(s.sten_w[l * KS + k]);
             C rho, j[3], u[3], T;
-            node_pred_c<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
+            node_pred_c<L, C>(M, g.N, n, rho, j, u, T, C(s.Cv));
             v[0] = double(rho * w);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -540,7 +524,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
       if (n >= 0) {
         const double w = s.psten_w[l * KP + k];
         double rho, j[3], u[3], T;
-        node_pred<L, S, C>(f, E, M, g.N, n, rho, j, u, T, C(s.Cv));
+        node_pred<L, C>(M, g.N, n, rho, j, u, T, C(s.Cv));
 #pragma unroll
         for (int a = 0; a < D; ++a) pv[a] = u[a] * w;
         pv[D] = T * w;
@@ -620,9 +604,8 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
 }
 
 template <class L, class S, class C>
-static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBStepDev s, const S* f, const C* E,
-                                                                   const C* M) {
-  ib_force_body<L, S, C>(g, s, f, E, M, blockIdx.x);
+static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force(Grid g, IBStepDev s, const C* M) {
+  ib_force_body<L, S, C>(g, s, M, blockIdx.x);
 }
 
 // Several cases in one launch: work item = (case, block of the case).
@@ -630,8 +613,6 @@ template <class S, class C>
 struct IBCaseDesc {
   Grid g;
   IBStepDev s;
-  const S* f;
-  const C* E;
   const C* M;
 };
 
@@ -640,7 +621,7 @@ static __global__ void __launch_bounds__(32 * kIBWarps) k_ib_force_batched(const
                                                                            const int2* work) {
   const int2 w = work[blockIdx.x];
   const IBCaseDesc<S, C>& c = d[w.x];
-  ib_force_body<L, S, C>(c.g, c.s, c.f, c.E, c.M, w.y);
+  ib_force_body<L, S, C>(c.g, c.s, c.M, w.y);
 }
 
 // Eq. spr2 as an Eulerian-side gather: f_u, w + q of each forced node.
@@ -682,18 +663,6 @@ __device__ __forceinline__ void spread_row(int D, int r, const int* row_ptr, con
   }
 }
 
-static __global__ void k_ib_spread(int D, int n_rows, const int* row_ptr, const int* col, const double* wt,
-                                   const double* G, double* FU, double* WQ) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_rows) return;
-  double acc[4];
-  spread_row(D, r, row_ptr, col, wt, G, acc);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-    if (a < D) FU[(long long)r * D + a] = acc[a];
-  WQ[r] = acc[3];
-}
-
 // Spreading and its application to the moments, several cases in one
 // launch: the same sums and updates as k_ib_spread_apply, one row per
 // thread.
@@ -733,7 +702,7 @@ static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const 
   c.M[(1 + D) * N + n] = c.M[(1 + D) * N + n] + C(acc[3]);
 }
 
-// One case: spreading (the sums of k_ib_spread) and its application to the
+// One case: spreading (Eq. spr2, the sums of spread_row) and its application to the
 // predicted moments in place, rho u += f_u / 2 and rho E += w + q on the
 // row's node (Sec. 2.2, reading Q15), one thread per row.
 template <class C>
@@ -755,12 +724,107 @@ static __global__ void k_ib_spread_apply(int D, long long N, int n_rows, const i
   M[(1 + D) * N + n] = M[(1 + D) * N + n] + C(acc[3]);
 }
 
+// Wall diagnostics of the updated field (Sec. 3.1-3.2, reading Q26), one
+// thread per Lagrangian point: p, u, T at X_l by Eq. int1 with d = 2 over
+// Omega (nodes on both sides of the wall), u and T at the projection point
+// P_l by Eq. int1 with d = 1 (the per-step stencils), then per point
+//   C_p = (p^s - p_inf) / q_inf, tau_w = mu [(u^P - u^B) - normal part] / d_n,
+//   u^s, T^s, (dT/dn)^s = (T^P - T^s) / d_n
+// in out[l * (2D + 3) + ...] (C_p, tau_w[D], u^s[D], T^s, (dT/dn)^s).
+struct DiagDev {
+  int NL, D;
+  double R, Cv, mu, d_n, p_inf, q_inf;
+  const double* X;
+  const double* nrm;
+  const double* uB;
+  const int* psten_node;
+  const double* psten_w;
+  double* out;
+  int* err;
+};
+
+template <class L, class C>
+static __global__ void k_wall_diag(Grid g, DiagDev d, const C* M) {
+  constexpr int D = L::D;
+  constexpr int KP = D == 2 ? 4 : 8;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= d.NL) return;
+  double X[3] = {0, 0, 0};
+  int base[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) {
+    X[a] = d.X[l * D + a];
+    base[a] = int(floor(X[a])) - 1;
+  }
+  double ps = 0.0, us[3] = {0, 0, 0}, Ts = 0.0;
+  for (int oz = 0; oz < (D == 3 ? 4 : 1); ++oz)
+    for (int oy = 0; oy < 4; ++oy)
+      for (int ox = 0; ox < 4; ++ox) {
+        const int node[3] = {base[0] + ox, base[1] + oy, D == 3 ? base[2] + oz : 0};
+        double r[3];
+        bool inbox = true;
+        for (int a = 0; a < D; ++a) {
+          r[a] = double(node[a]) - X[a];
+          if (fabs(r[a]) >= 2.0) inbox = false;
+        }
+        if (!inbox) continue;
+        int idx[3] = {0, 0, 0};
+        bool ok = true;
+        for (int a = 0; a < D; ++a) {
+          int v = node[a] - (a == 2 ? g.zoff : 0);
+          if (g.per[a]) {
+            v = v % g.n[a];
+            if (v < 0) v += g.n[a];
+          } else if (v < 0 || v >= g.n[a]) {
+            ok = false;
+          }
+          idx[a] = v;
+        }
+        if (!ok) {
+          atomicExch(d.err, 1);
+          continue;
+        }
+        double wt = 1.0;
+        for (int a = 0; a < D; ++a) wt = wt * delta_tilde(r[a], 2.0);
+        double rho, j[3], u[3], T;
+        node_pred<L, C>(M, g.N, g.lin(idx[0], idx[1], idx[2]), rho, j, u, T, C(d.Cv));
+        ps = ps + ((rho * d.R) * T) * wt;
+        for (int a = 0; a < D; ++a) us[a] = us[a] + u[a] * wt;
+        Ts = Ts + T * wt;
+      }
+  double uP[3] = {0, 0, 0}, TP = 0.0;
+  for (int k = 0; k < KP; ++k) {
+    const int n = d.psten_node[l * KP + k];
+    if (n < 0) continue;
+    const double w = d.psten_w[l * KP + k];
+    double rho, j[3], u[3], T;
+    node_pred<L, C>(M, g.N, n, rho, j, u, T, C(d.Cv));
+    for (int a = 0; a < D; ++a) uP[a] = uP[a] + u[a] * w;
+    TP = TP + T * w;
+  }
+  double du[3], dn = 0.0;
+  for (int a = 0; a < D; ++a) {
+    du[a] = uP[a] - (d.uB ? d.uB[l * D + a] : 0.0);
+    dn = dn + du[a] * d.nrm[l * D + a];
+  }
+  double* o = d.out + (long long)l * (2 * D + 3);
+  o[0] = (ps - d.p_inf) / d.q_inf;
+  for (int a = 0; a < D; ++a) {
+    o[1 + a] = d.mu * (du[a] - dn * d.nrm[l * D + a]) / d.d_n;
+    o[1 + D + a] = us[a];
+  }
+  o[1 + 2 * D] = Ts;
+  o[2 + 2 * D] = (TP - Ts) / d.d_n;
+}
+
 // wall loads: fixed-order block reduction (deterministic)
-static __global__ void k_wall_loads(int D, int NL, const double* G, const double* W, double* out) {
+// owned (optional, slabs): only points with owned[l] != 0 are summed
+static __global__ void k_wall_loads(int D, int NL, const double* G, const double* W, const unsigned char* owned,
+                                    double* out) {
   __shared__ double sh[256][5];
   const int t = threadIdx.x;
   double acc[5] = {0, 0, 0, 0, 0};
   for (int l = t; l < NL; l += 256) {
+    if (owned && !owned[l]) continue;
     const double w = W[l];
     for (int a = 0; a < D; ++a) acc[a] += G[l * (D + 2) + a] * w;
     acc[3] += G[l * (D + 2) + D + 1] * w;  // Q

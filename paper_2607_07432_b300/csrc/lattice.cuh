@@ -100,18 +100,34 @@ __host__ __device__ constexpr double H3r(int k, int i) {
     v += L::h3sign(k, t) * H3<L>(i, L::h3idx(k, t, 0), L::h3idx(k, t, 1), L::h3idx(k, t, 2));
   return v;
 }
-// lattice norm N_k = sum_i w_i H3r_k,i^2 (orthogonal projection, 1/N_k)
-template <class L>
-__host__ __device__ constexpr double N3r(int k) {
-  double s = 0.0;
-  for (int i = 0; i < L::Q; ++i) s += L::w(i) * H3r<L>(k, i) * H3r<L>(k, i);
-  return s;
-}
 template <class L>
 __host__ __device__ constexpr int c2(int i) {
   int s = 0;
   for (int a = 0; a < L::D; ++a) s += L::c(i, a) * L::c(i, a);
   return s;
+}
+// lattice norm N_k = sum_i w_i H3r_k,i^2 (orthogonal projection, 1/N_k),
+// evaluated exactly and rounded once: 36 w_i and 3 H3r_k,i are integers,
+// so N_k = (sum_i 36 w_i (3 H3r_k,i)^2) / 324
+template <class L>
+__host__ __device__ constexpr int w36(int i) {
+  return c2<L>(i) == 0 ? (L::D == 3 ? 12 : 16) : (c2<L>(i) == 1 ? (L::D == 3 ? 2 : 4) : 1);
+}
+template <class L>
+__host__ __device__ constexpr int H3x3(int i, int a, int b, int g) {
+  return 3 * L::c(i, a) * L::c(i, b) * L::c(i, g) -
+         ((a == b ? L::c(i, g) : 0) + (b == g ? L::c(i, a) : 0) + (a == g ? L::c(i, b) : 0));
+}
+template <class L>
+__host__ __device__ constexpr double N3r(int k) {
+  long long s = 0;
+  for (int i = 0; i < L::Q; ++i) {
+    long long h = 0;
+    for (int t = 0; t < L::h3terms(k); ++t)
+      h += L::h3sign(k, t) * H3x3<L>(i, L::h3idx(k, t, 0), L::h3idx(k, t, 1), L::h3idx(k, t, 2));
+    s += w36<L>(i) * h * h;
+  }
+  return double(s) / 324.0;
 }
 // number of nonzero transverse components of c_i with respect to axis a
 template <class L>

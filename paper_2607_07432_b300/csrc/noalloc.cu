@@ -37,12 +37,14 @@ double* g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
 // pass 1: block b sums points [256 b, 256 b + 256) in a fixed tree order
-__global__ void k_wall_partials(int D, int NL, const double* G, const double* W, double* scratch) {
+// (on a z slab only the points it owns, owned != nullptr)
+__global__ void k_wall_partials(int D, int NL, const double* G, const double* W, const unsigned char* owned,
+                                double* scratch) {
   __shared__ double sh[kNoallocThreads][5];
   const int t = threadIdx.x;
   const int l = blockIdx.x * kNoallocThreads + t;
   double acc[5] = {0, 0, 0, 0, 0};
-  if (l < NL) {
+  if (l < NL && (!owned || owned[l])) {
     const double w = W[l];
     for (int a = 0; a < D; ++a) acc[a] = G[l * (D + 2) + a] * w;
     acc[3] = G[l * (D + 2) + D + 1] * w;  // Q
@@ -81,7 +83,8 @@ extern "C" lbm_status lbm_get_wall_loads_noalloc(lbm_handle* h, double force[3],
                 "lbm_get_wall_loads_noalloc supports at most 65536 Lagrangian points (static scratch)");
   const int dev = h->cfg.device;
   if (dev < 0 || dev >= kMaxDevices) return fail(h, LBM_EINVAL, "device ordinal out of range");
-  if (cudaSetDevice(dev) != cudaSuccess) return fail(h, LBM_ECUDA, "cudaSetDevice failed");
+  DeviceGuard dg(dev);
+  if (dg.status() != cudaSuccess) return fail(h, LBM_ECUDA, "cudaSetDevice failed");
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -94,12 +97,13 @@ extern "C" lbm_status lbm_get_wall_loads_noalloc(lbm_handle* h, double force[3],
     scratch = g_scratch_addr[dev];
   }
   const int nblocks = (h->NL + kNoallocThreads - 1) / kNoallocThreads;
-  k_wall_partials<<<nblocks, kNoallocThreads, 0, h->st>>>(h->D, h->NL, h->G, h->W, scratch);
-  h->launches++;
-  k_wall_final<<<1, 32, 0, h->st>>>(h->D, nblocks, scratch);
-  h->launches++;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(h, LBM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  lbm_status s = launch(h, kProfOther, [&] {
+    k_wall_partials<<<nblocks, kNoallocThreads, 0, h->st>>>(h->D, h->NL, h->G, h->W, h->owned, scratch);
+  });
+  if (s) return s;
+  s = launch(h, kProfOther, [&] { k_wall_final<<<1, 32, 0, h->st>>>(h->D, nblocks, scratch); });
+  if (s) return s;
+  cudaError_t e;
   double out[5];
   e = cudaMemcpyAsync(out, scratch + kNoallocMaxBlocks * kNoallocSlot, 5 * sizeof(double), cudaMemcpyDeviceToHost,
                       h->st);

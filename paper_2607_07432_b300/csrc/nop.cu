@@ -14,6 +14,7 @@
 #include "nop_kernels.cuh"
 
 using namespace lbmib::nop;
+using lbmib_host::DeviceGuard;
 
 namespace {
 
@@ -304,10 +305,8 @@ lbm_status nop_create(const nop_config* cfg, nop_net** out) {
     return LBM_EINVAL;
   for (int l = 0; l < 4; ++l)
     if (cfg->channels[l] < 16 || cfg->channels[l] > 256 || cfg->channels[l] % 16) return LBM_EINVAL;
-  if (cudaSetDevice(cfg->device) != cudaSuccess) {
-    cudaGetLastError();
-    return LBM_ECUDA;
-  }
+  DeviceGuard dg(cfg->device);
+  if (dg.status() != cudaSuccess) return LBM_ECUDA;
   nop_net* net = new nop_net();
   net->cfg = *cfg;
   if (cfg->stream) {
@@ -369,7 +368,7 @@ lbm_status nop_create(const nop_config* cfg, nop_net** out) {
 
 void nop_destroy(nop_net* net) {
   if (!net) return;
-  cudaSetDevice(net->cfg.device);
+  DeviceGuard dg(net->cfg.device);
   if (net->st) cudaStreamSynchronize(net->st);
   for (void* p : net->allocs) cudaFree(p);
   if (net->own_stream && net->st) cudaStreamDestroy(net->st);
@@ -382,7 +381,8 @@ long long nop_param_count(const nop_net* net) { return net ? net->n_params : 0; 
 
 lbm_status nop_init_params(nop_net* net, unsigned long long seed) {
   if (!net) return LBM_EINVAL;
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   for (const Layer& l : net->L)
     k_init_layer<<<blocks(l.size()), 256, 0, net->st>>>(net->master + l.offset, l.cin, l.cout, seed, l.offset);
   NCK(cudaMemsetAsync(net->adam_m, 0, net->n_params * sizeof(float), net->st));
@@ -395,7 +395,8 @@ lbm_status nop_init_params(nop_net* net, unsigned long long seed) {
 
 lbm_status nop_set_params(nop_net* net, int is_device, const float* params) {
   if (!net || !params) return LBM_EINVAL;
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   NCK(cudaMemcpyAsync(net->master, params, net->n_params * sizeof(float),
                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, net->st));
   NCK(cudaMemsetAsync(net->adam_m, 0, net->n_params * sizeof(float), net->st));
@@ -409,7 +410,8 @@ lbm_status nop_set_params(nop_net* net, int is_device, const float* params) {
 lbm_status nop_get_params(const nop_net* cnet, int is_device, float* params) {
   nop_net* net = const_cast<nop_net*>(cnet);
   if (!net || !params) return LBM_EINVAL;
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   NCK(cudaMemcpyAsync(params, net->master, net->n_params * sizeof(float),
                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, net->st));
   NCK(cudaStreamSynchronize(net->st));
@@ -420,7 +422,8 @@ lbm_status nop_forward(nop_net* net, int batch, const float* x, float* y) {
   if (!net || !x || !y) return LBM_EINVAL;
   lbm_status s = check_batch(net, batch);
   if (s) return s;
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   if ((s = load_input(net, batch, x)) || (s = forward(net, batch))) return s;
   const Tensor& t = net->T[net->y_t];
   const long long P = pixels(net, 0, batch);
@@ -433,7 +436,8 @@ lbm_status nop_backward(nop_net* net, int batch, const float* x, const float* dy
   if (!net || !x || !dy) return LBM_EINVAL;
   lbm_status s = check_batch(net, batch);
   if (s) return s;
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   if ((s = load_input(net, batch, x)) || (s = forward(net, batch))) return s;
   const Tensor& t = net->T[net->y_t];
   const long long P = pixels(net, 0, batch);
@@ -454,7 +458,8 @@ lbm_status nop_train_step(nop_net* net, int batch, const float* x, const float* 
   if (!net || !x || !target || !(lr >= 0.f)) return LBM_EINVAL;
   lbm_status s = check_batch(net, batch);
   if (s) return s;
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   if ((s = load_input(net, batch, x)) || (s = forward(net, batch))) return s;
   const Tensor& t = net->T[net->y_t];
   const long long P = pixels(net, 0, batch);
@@ -481,7 +486,8 @@ lbm_status nop_infer_into(nop_net* net, lbm_handle* h, const float* x, const dou
   if (!net || !h || !x || !off || !scale) return LBM_EINVAL;
   if (h->D != 2 || h->g.n[0] != net->cfg.width || h->g.n[1] != net->cfg.height || net->cfg.out_channels != 4)
     return fail(net, LBM_EINVAL, "solver must be D2Q9 of the network's grid, network with 4 outputs");
-  NCK(cudaSetDevice(net->cfg.device));
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
   lbm_status s;
   if ((s = load_input(net, 1, x)) || (s = forward(net, 1))) return s;
   const long long N = (long long)net->cfg.height * net->cfg.width;

@@ -66,13 +66,17 @@ __device__ __forceinline__ C feq_i(C rho, const C* u, C th) {
 }
 
 // Velocity gradient du[a][b] = d u_a / d x_b and a^C, the lattice-dependent
-// part of Eq. af2 (only cited by the paper): a^C_ab = -d_ab d_a(rho u_a^3),
-// the divergence of the diagonal third-order equilibrium moment that the
-// lattice cannot carry.  Central differences; MacroAt(dx,dy,dz) returns the
-// neighbour's Macro.
+// part of Eq. af2 (only cited by the paper), read from the Chapman-Enskog
+// expansion of the lattice's third moment:
+//   a^C_ab = c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
+// P = rho(1-theta) (use_ac = 2; use_ac = 1 keeps the cubic part only,
+// 0 none).  Central differences; MacroAt(dx,dy,dz) returns the neighbour's
+// Macro, uc is the node's own velocity.  In FP64 the operations follow the
+// oracle's order.
 template <class L, class C, class MacroAt>
-__device__ __forceinline__ void gradients(const MacroAt& M, C du[3][3], C aC[3][3], int use_ac) {
+__device__ __forceinline__ void gradients(const MacroAt& M, const C* uc, C du[3][3], C aC[3][3], int use_ac) {
   constexpr int D = L::D;
+  C dP[3];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     const Macro<C> p = M(b == 0 ? 1 : 0, b == 1 ? 1 : 0, b == 2 ? 1 : 0);
@@ -84,6 +88,13 @@ __device__ __forceinline__ void gradients(const MacroAt& M, C du[3][3], C aC[3][
     }
     if (use_ac)
       aC[b][b] = -((p.rho * (p.u[b] * p.u[b] * p.u[b]) - m.rho * (m.u[b] * m.u[b] * m.u[b])) * C(0.5));
+    dP[b] = (p.rho * (C(1) - p.th) - m.rho * (C(1) - m.th)) * C(0.5);
+  }
+  if (use_ac == 2) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) aC[a][b] = aC[a][b] + C(kCs2) * (uc[a] * dP[b] + uc[b] * dP[a]);
   }
 }
 
@@ -260,17 +271,32 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
   const C fd = (C(1) - ph.sigma) * m.rho * cs2 * th_m * tau_bar;
   C Fp[3][3];
   dev_expand<L, C>(dAFp, Fp);
-  // raw second moments of f-bar
+  // raw second moments of f-bar from the even parts f_i + f_opp(i) of the
+  // opposite pairs (c_a c_b is even in c, so each pair enters once)
+  C ev[Q];
+  sfor<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int o = opposite<L>(i);
+    if constexpr (i < o) ev[i] = fbar[i] + fbar[o];
+  });
   C S2[3][3];
   sfor<0, D>([&](auto A) {
     sfor<decltype(A)::value, D>([&](auto B) {
       constexpr int a = decltype(A)::value, b = decltype(B)::value;
       C s = C(0);
-      sfor<0, Q>([&](auto I) {
+      bool first = true;
+      sfor<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
+        constexpr int o = opposite<L>(i);
         constexpr int cc = L::c(i, a) * L::c(i, b);
-        if constexpr (cc == 1) s += fbar[i];
-        if constexpr (cc == -1) s -= fbar[i];
+        if constexpr (i < o && cc == 1) {
+          s = first ? ev[i] : s + ev[i];
+          first = false;
+        }
+        if constexpr (i < o && cc == -1) {
+          s = first ? -ev[i] : s - ev[i];
+          first = false;
+        }
       });
       S2[a][b] = s;
     });

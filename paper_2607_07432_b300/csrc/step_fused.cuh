@@ -73,17 +73,14 @@ struct FusedLayout {
   // so its slot takes plane z+2
   static constexpr int RM = D == 3 ? 4 : 1;
   static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
-  static constexpr int NMF = D + 3;           // rho, u (D), theta, E'
-  // 3D FP32: the next plane's inputs are staged in shared memory with
-  // asynchronous copies while the current plane is finished
-  static constexpr bool stage = D == 3 && sizeof(S) == 4 && sizeof(C) == 4 && HY1 == 12;
-  // resident CTAs per SM the tile is sized for
-  static constexpr int min_blocks = (D == 3 && sizeof(C) == 4 && HY1 <= 8) ? 2 : 1;
-  static constexpr size_t ring_bytes =
+  // corrected macros of a plane: rho, u (3 slots), theta, E' per node, kept
+  // as vectors so that one shared-memory load reads several fields
+  // (FP32: a float4 (rho, u) and a float2 (theta, E') array; FP64: three
+  // double2 arrays (rho, u_x), (u_y, u_z), (theta, E')), 6 values per node
+  static constexpr int NMF = 6;
+  static constexpr int min_blocks = 1;
+  static constexpr size_t bytes =
       sizeof(C) * ((size_t)RM * NMF * NH2 + (size_t)RF * L::Q * NH1 + 4 * (size_t)NH1);
-  static constexpr size_t stage_bytes =
-      stage ? 4 * ((size_t)(D + 2) * NH2 + (size_t)(L::Q + 1 + L::NDEV) * NH1) : 0;
-  static constexpr size_t bytes = ring_bytes + stage_bytes;
 };
 
 __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int node) {
@@ -98,14 +95,6 @@ __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int 
   return -1;
 }
 
-// 4-byte asynchronous global -> shared copy (sm_80+ LDGSTS) and its fences
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
 // body of the fused step for the tile (bx, by) and z-chunk bz of one case
 template <class L, class S, class C, int HY>
 __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, int zchunk,
@@ -115,16 +104,12 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   constexpr int TX = Lay::TX, TY = Lay::TY, NT = Lay::NT;
   constexpr int HX2 = Lay::HX2, NH2 = Lay::NH2, HX1 = Lay::HX1, NH1 = Lay::NH1;
   constexpr int RM = Lay::RM, RF = Lay::RF, NMF = Lay::NMF;
-  constexpr bool STG = Lay::stage;
   constexpr bool exact = std::is_same<C, double>::value;  // FP64: operations as in the oracle
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* mr = reinterpret_cast<C*>(smem_raw);        // [RM][NMF][NH2]
+  C* mr = reinterpret_cast<C*>(smem_raw);        // [RM][6 NH2] vector arrays (see FusedLayout)
   C* fr = mr + (size_t)RM * NMF * NH2;           // [RF][Q][NH1]
   C* Fx = fr + (size_t)RF * Q * NH1;             // [2][NH1] +x face fluxes (plane parity)
   C* Fy = Fx + 2 * NH1;                          // [2][NH1] +y face fluxes
-  C* stM = Fy + 2 * NH1;                         // staged moments [(D+2)][NH2]
-  S* stF = reinterpret_cast<S*>(stM + (size_t)(D + 2) * NH2);  // staged populations [Q][NH1]
-  C* stA = reinterpret_cast<C*>(stF + (size_t)Q * NH1);        // staged P_prev, dAF [1+NDEV][NH1]
   const int t = threadIdx.x;
   const int cx = t % HX1, cy = t / HX1;          // halo-1 coordinates of this thread's node
   const int hx = cx + 1, hy = cy + 1;            // halo-2 coordinates
@@ -146,8 +131,8 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   };
 
   // corrected macros (rho, u, theta, rho E') of plane z over the halo-2 region,
-  // from the moments rho, rho u, rho E (staged copy or global memory)
-  constexpr bool RPM = D == 3 && !STG && !exact && NH2 <= 2 * NT;
+  // from the moments rho, rho u, rho E
+  constexpr bool RPM = D == 3 && !exact && NH2 <= 2 * NT;
   C rm[RPM ? 2 : 1][RPM ? D + 2 : 1];
   auto prefetch_moments = [&](int z) {
     if constexpr (RPM) {
@@ -185,15 +170,19 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       }
       th = (E * ir - C(0.5) * uu) * (C(1) / ph.Cv);
     }
-    dst[0 * NH2 + k] = rho;
-#pragma unroll
-    for (int d = 0; d < D; ++d) dst[(1 + d) * NH2 + k] = u[d];
-    dst[(1 + D) * NH2 + k] = th;
-    dst[(2 + D) * NH2 + k] = E;
+    const C u2 = D == 3 ? u[D - 1] : C(0);
+    if constexpr (sizeof(C) == 4) {
+      reinterpret_cast<float4*>(dst)[k] = make_float4(rho, u[0], u[1], u2);
+      reinterpret_cast<float2*>(dst + 4 * NH2)[k] = make_float2(th, E);
+    } else {
+      reinterpret_cast<double2*>(dst)[k] = make_double2(rho, u[0]);
+      reinterpret_cast<double2*>(dst + 2 * NH2)[k] = make_double2(u[1], u2);
+      reinterpret_cast<double2*>(dst + 4 * NH2)[k] = make_double2(th, E);
+    }
   };
   // corrected macros of plane z over the halo-2 region, from the moments in
-  // registers (prefetched), the staged copy, or global memory
-  auto load_macros = [&](int z, bool staged, bool regs = false) {
+  // registers (prefetched) or global memory
+  auto load_macros = [&](int z, bool regs = false) {
     C* dst = mr + (size_t)mslot(z) * NMF * NH2;
     if constexpr (RPM) {
       if (regs) {
@@ -212,49 +201,38 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     const int gz = g.wrap(2, z);
     for (int k = t; k < NH2; k += NT) {
       C rho, jm[3], E;
-      if (STG && staged) {
-        rho = stM[k];
+      const long long n = halo2_node(k, gz);
+      rho = a.M_in[n];
 #pragma unroll
-        for (int d = 0; d < D; ++d) jm[d] = stM[(1 + d) * NH2 + k];
-        E = stM[(1 + D) * NH2 + k];
-      } else {
-        const long long n = halo2_node(k, gz);
-        rho = a.M_in[n];
-#pragma unroll
-        for (int d = 0; d < D; ++d) jm[d] = a.M_in[(1 + d) * N + n];
-        E = a.M_in[(1 + D) * N + n];
-      }
+      for (int d = 0; d < D; ++d) jm[d] = a.M_in[(1 + d) * N + n];
+      E = a.M_in[(1 + D) * N + n];
       put_macro(dst, k, rho, jm, E);
-    }
-  };
-  // asynchronous copies of the inputs of plane zm (moments, halo 2) and of
-  // this thread's node of plane zf (populations, previous-step auxiliaries)
-  auto prefetch = [&](int zm, int zf) {
-    if constexpr (STG) {
-      const int gzm = g.wrap(2, zm);
-      for (int k = t; k < NH2; k += NT) {
-        const long long n = halo2_node(k, gzm);
-#pragma unroll
-        for (int q = 0; q < D + 2; ++q) cp_async4(&stM[q * NH2 + k], &a.M_in[q * N + n]);
-      }
-      const long long nf = g.lin(wx, wy, g.wrap(2, zf));
-#pragma unroll
-      for (int i = 0; i < Q; ++i) cp_async4(&stF[i * NH1 + t], &a.f_in[(long long)i * N + nf]);
-      cp_async4(&stA[t], &a.Pp[nf]);
-#pragma unroll
-      for (int q = 0; q < L::NDEV; ++q) cp_async4(&stA[(1 + q) * NH1 + t], &a.Ap[q * N + nf]);
-      cp_async_commit();
     }
   };
   auto macro_at = [&](int z, int kx, int ky) {
     const C* src = mr + (size_t)mslot(z) * NMF * NH2;
     const int k = ky * HX2 + kx;
     Macro<C> m;
-    m.rho = src[k];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) m.u[d] = d < D ? src[(1 + d) * NH2 + k] : C(0);
-    m.th = src[(1 + D) * NH2 + k];
-    m.E = src[(2 + D) * NH2 + k];
+    if constexpr (sizeof(C) == 4) {
+      const float4 a4 = reinterpret_cast<const float4*>(src)[k];
+      const float2 a2 = reinterpret_cast<const float2*>(src + 4 * NH2)[k];
+      m.rho = a4.x;
+      m.u[0] = a4.y;
+      m.u[1] = a4.z;
+      m.u[2] = a4.w;
+      m.th = a2.x;
+      m.E = a2.y;
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(src)[k];
+      const double2 b = reinterpret_cast<const double2*>(src + 2 * NH2)[k];
+      const double2 c = reinterpret_cast<const double2*>(src + 4 * NH2)[k];
+      m.rho = a.x;
+      m.u[0] = a.y;
+      m.u[1] = b.x;
+      m.u[2] = b.y;
+      m.th = c.x;
+      m.E = c.y;
+    }
     return m;
   };
   // 3D FP32 arithmetic (FP32, FP16 or BF16 storage): the populations and
@@ -265,7 +243,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   // auxiliaries with the last): a warp whose load queue is full stalls, so
   // one group goes out before the pull stream, one after it and one after
   // the x face flux, where the arithmetic gives the queue time to drain.
-  constexpr bool RP = D == 3 && !STG && !exact;
+  constexpr bool RP = D == 3 && !exact;
   constexpr int QA = (Q + 2) / 3, QB = (2 * Q + 1) / 3;  // population groups [0,QA) [QA,QB) [QB,Q)
   S rf[RP ? Q : 1];
   C rP = C(0);
@@ -285,13 +263,13 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     }
   };
   // collision of this thread's node of plane z (halo-1 region, one node per thread)
-  auto collide_plane = [&](int z, bool staged, bool regs) {
+  auto collide_plane = [&](int z, bool regs) {
     C* dst = fr + (size_t)fslot(z) * Q * NH1;
     const long long n = g.lin(wx, wy, g.wrap(2, z));
     auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
-    C du[3][3], aC[3][3];
-    gradients<L, C>(MA, du, aC, ph.use_ac);
     const Macro<C> m = macro_at(z, hx, hy);
+    C du[3][3], aC[3][3];
+    gradients<L, C>(MA, m.u, du, aC, ph.use_ac);
     C fbar[Q];
     C dAFp[L::NDEV];
     C Pp;
@@ -300,25 +278,15 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const C v = C(Store<S>::load(rf[RP ? i : 0]));
-        fbar[i] = Store<S>::dev ? v + C(L::w(i)) : v;
+        fbar[i] = Store<S>::dev ? v + pop_offset<L, S, C>(i, C(g.thref)) : v;
       }
       Pp = rP;
 #pragma unroll
       for (int q = 0; q < L::NDEV; ++q) dAFp[q] = rA[RP ? q : 0];
       is_forced = rfl != 0;
-    } else if (STG && staged) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const C v = C(Store<S>::load(stF[i * NH1 + t]));
-        fbar[i] = Store<S>::dev ? v + C(L::w(i)) : v;
-      }
-      Pp = stA[t];
-#pragma unroll
-      for (int q = 0; q < L::NDEV; ++q) dAFp[q] = stA[(1 + q) * NH1 + t];
-      is_forced = a.forced && a.forced[n];
     } else {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n);
+      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n, C(g.thref));
       Pp = a.Pp[n];
 #pragma unroll
       for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
@@ -376,11 +344,10 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
 
   // prologue: macros of planes z0-2..z0+1, collisions of planes z0-1 and z0
   if constexpr (D == 3) {
-    for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z, false);
+    for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z);
     __syncthreads();
-    collide_plane(z0 - 1, false, false);
-    collide_plane(z0, false, false);
-    prefetch(z0 + 2, z0 + 1);
+    collide_plane(z0 - 1, false);
+    collide_plane(z0, false);
     prefetch_regs(z0 + 1, std::integral_constant<int, 0>{}, std::integral_constant<int, Q>{}, true);
     prefetch_moments(z0 + 2);
     __syncthreads();
@@ -412,21 +379,19 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     }
   };
   for (int z = z0; z < z1; ++z) {
-    if constexpr (STG) cp_async_wait_all();
     __syncthreads();
     if (z > z0) finish(z - 1);
     if constexpr (D == 3) {
-      load_macros(z + 2, true, true);
+      load_macros(z + 2, true);
       __syncthreads();
-      collide_plane(z + 1, true, true);
+      collide_plane(z + 1, true);
       __syncthreads();
-      prefetch(z + 3, z + 2);
       prefetch_regs(z + 2, std::integral_constant<int, 0>{}, std::integral_constant<int, QA>{}, false);
       prefetch_moments(z + 3);
     } else {
-      load_macros(0, false);
+      load_macros(0);
       __syncthreads();
-      collide_plane(0, false, false);
+      collide_plane(0, false);
       __syncthreads();
     }
     C rho = C(0), j[3] = {C(0), C(0), C(0)};
@@ -437,7 +402,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       sfor<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const C v = fcol_at(i, z - L::c(i, 2), sx - L::c(i, 0), cy - L::c(i, 1));
-        store_pop<L, S, C>(a.f_out, i, N, n, v);
+        store_pop<L, S, C>(a.f_out, i, N, n, v, C(g.thref));
         rho += v;
         sfor<0, D>([&](auto A) {
           constexpr int d = decltype(A)::value;
@@ -450,8 +415,8 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         j[0] = j[1] = j[2] = C(0);
         sfor<0, Q>([&](auto I) {
           constexpr int i = decltype(I)::value;
-          store_pop<L, S, C>(a.f_out, i, N, n, a.feq_inf[i]);
-          const C v = roundtrip_pop<L, S, C>(i, a.feq_inf[i]);
+          store_pop<L, S, C>(a.f_out, i, N, n, a.feq_inf[i], C(g.thref));
+          const C v = roundtrip_pop<L, S, C>(i, a.feq_inf[i], C(g.thref));
           rho += v;
           sfor<0, D>([&](auto A) {
             constexpr int d = decltype(A)::value;
@@ -482,7 +447,6 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   }
   __syncthreads();
   finish(z1 - 1);
-  if constexpr (STG) cp_async_wait_all();
 }
 
 template <class L, class S, class C, int HY>
@@ -524,15 +488,11 @@ inline void launch_fused_tile(const Grid& g, const FusedArgs<S, C>& a, const Phy
 }
 
 // zchunk: planes per CTA along z (3D); tile_rows selects the halo-1 tile
-// height: 3D FP32 8 (two CTAs per SM), 12 (staged inputs), 0 = 16 (one CTA
-// per SM); 2D FP32 0 = 8, 16 or 32 (1024 threads)
+// height of the 2D FP32 step: 0 = 8, 16 or 32 (1024 threads); other forms
+// have one tile
 template <class L, class S, class C>
 inline void launch_fused(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
                          int zchunk, int tile_rows) {
-  if constexpr (L::D == 3 && sizeof(C) == 4) {
-    if (tile_rows == 8) return launch_fused_tile<L, S, C, 8>(g, a, ph, st, zchunk);
-    if (tile_rows == 12) return launch_fused_tile<L, S, C, 12>(g, a, ph, st, zchunk);
-  }
   if constexpr (L::D == 2 && sizeof(C) == 4) {
     if (tile_rows == 16) return launch_fused_tile<L, S, C, 16>(g, a, ph, st, zchunk);
     if (tile_rows == 32) return launch_fused_tile<L, S, C, 32>(g, a, ph, st, zchunk);
@@ -549,7 +509,7 @@ __global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
   C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const C v = load_pop<L, S, C>(f, i, g.N, n);
+    const C v = load_pop<L, S, C>(f, i, g.N, n, C(g.thref));
     r += v;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -567,7 +527,7 @@ __global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
 // equilibrium face copies its inner neighbour along the outlet axis.  This is
 // the outlet-copy-then-equilibrium order with the edges resolved up front.
 struct BCFaces {
-  int type[6];  // LBM_BC_* per face: 0 periodic, 1 inlet, 2 outlet, 3 far field
+  int type[6];  // LBM_BC_* per face: 0 periodic, 1 inlet, 2 outlet, 3 far field, 4 slab ghost face
 };
 
 // boundary node t of face `face` (see k_bc_all_m)
@@ -577,7 +537,7 @@ __device__ __forceinline__ void bc_node(const Grid& g, S* f, C* M, const BCFaces
   constexpr int D = L::D;
   const int axis = face / 2, side = face % 2;
   const int ft = bf.type[face];
-  if (ft == 0 || (skip_x && axis == 0)) return;
+  if (ft == 0 || ft == kBCGhostFace || (skip_x && axis == 0)) return;
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
   if (t >= g.n[a1] * g.n[a2]) return;
   int c[3];
@@ -599,8 +559,8 @@ __device__ __forceinline__ void bc_node(const Grid& g, S* f, C* M, const BCFaces
     C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i]);
-      const C v = roundtrip_pop<L, S, C>(i, feq_inf[i]);
+      store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i], C(g.thref));
+      const C v = roundtrip_pop<L, S, C>(i, feq_inf[i], C(g.thref));
       r += v;
 #pragma unroll
       for (int a = 0; a < D; ++a)

@@ -26,11 +26,13 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
 
 EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", "ib_set_geometry",
            "lbm_step", "lbm_check", "lbm_get_fields", "lbm_get_state", "lbm_set_state", "lbm_set_fields",
-           "lbm_get_wall_loads", "lbm_get_constants", "ib_get_sizes", "ib_get_setup", "lbm_profile",
+           "lbm_get_wall_loads", "lbm_get_wall_diagnostics", "lbm_get_constants", "ib_get_sizes", "ib_get_setup", "lbm_profile",
            "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_case", "lbm_batch_step",
            "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
-           "lbm_batch_autotune", "lbm_save_state", "lbm_load_state"]
+           "lbm_batch_autotune", "lbm_save_state", "lbm_load_state", "lbm_create_slab", "lbm_slab_info",
+           "lbm_slab_exchange_bytes", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_points",
+           "lbm_slab_plan", "lbm_slab_keep"]
 
 
 class Config(ct.Structure):
@@ -58,6 +60,10 @@ def load():
     lib.lbm_last_error.restype = ct.c_char_p
     lib.lbm_launch_count.restype = ct.c_longlong
     lib.lbm_create.argtypes = [ct.POINTER(Config), ct.POINTER(ct.c_void_p)]
+    lib.lbm_create_slab.argtypes = [ct.POINTER(Config), ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_void_p)]
+    lib.lbm_slab_pack.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+    lib.lbm_slab_unpack.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+    lib.lbm_slab_exchange_bytes.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_size_t)]
     lib.lbm_save_state.argtypes = [ct.c_void_p, ct.c_char_p]
     lib.lbm_load_state.argtypes = [ct.c_void_p, ct.c_char_p]
     lib.lbm_batch_last_error.restype = ct.c_char_p
@@ -103,8 +109,10 @@ class Solver:
 
     def __init__(self, lattice="D2Q9", precision="fp32", shape=(64, 64), mach=0.1, reynolds=100.0,
                  ref_length=10.0, prandtl=0.71, gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0),
-                 sigma=0.98, d_n=1.5, method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=True,
-                 device=0, stream=None):
+                 sigma=0.98, d_n=1.5, method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=2,
+                 device=0, stream=None, slab=None):
+        """slab = (z0, z1, halo): a z slab of the case (lbm_create_slab); shape
+        is then the global grid."""
         L = lib()
         cfg = Config()
         L.lbm_config_default(ct.byref(cfg))
@@ -122,18 +130,31 @@ class Solver:
         bc = list(bc) if bc is not None else [BC_PERIODIC] * (2 * self.D)
         for k in range(6):
             cfg.bc[k] = int(bc[k]) if k < len(bc) else BC_PERIODIC
-        cfg.tau_mode, cfg.use_ac, cfg.device = int(tau_mode), int(bool(use_ac)), int(device)
+        cfg.tau_mode, cfg.use_ac, cfg.device = int(tau_mode), int(use_ac), int(device)
         cfg.stream = ct.c_void_p(stream) if stream else None
         self.cfg = cfg
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
         self.zyx = tuple(reversed(self.shape))
         h = ct.c_void_p()
-        st = L.lbm_create(ct.byref(cfg), ct.byref(h))
+        if slab is None:
+            st = L.lbm_create(ct.byref(cfg), ct.byref(h))
+        else:
+            st = L.lbm_create_slab(ct.byref(cfg), int(slab[0]), int(slab[1]), int(slab[2]), ct.byref(h))
         if st:
             raise LBMError(st, "lbm_create failed")
         self.h = h
         self.NL = 0
+        self.slab = None
+        if slab is not None:
+            info = (ct.c_int * 6)()
+            self._check(L.lbm_slab_info(h, info))
+            self.slab = dict(z0=info[0], z1=info[1], ghost_lo=info[2], ghost_hi=info[3], zoff=info[4],
+                             nz_global=info[5])
+            nloc = info[1] - info[0] + info[2] + info[3]
+            self.shape = (self.shape[0], self.shape[1], nloc)
+            self.N = int(np.prod(self.shape))
+            self.zyx = tuple(reversed(self.shape))
 
     def _check(self, st):
         if st:
@@ -190,6 +211,13 @@ class Solver:
             raise ValueError(kind)
         self._check(lib().ib_set_geometry(self.h, ct.byref(g)))
         self.NL = NL
+        if getattr(self, "slab", None) is not None:
+            n = ct.c_int()
+            self._check(lib().lbm_slab_points(self.h, ct.byref(n), None))
+            idx = np.empty(n.value, dtype=np.int32)
+            self._check(lib().lbm_slab_points(self.h, ct.byref(n), _ptr(idx)))
+            self.NL = n.value
+            self.slab_points = idx
 
     # -- time stepping -----------------------------------------------------
     def step(self, n=1):
@@ -246,6 +274,35 @@ class Solver:
             out.update(F=pp[:, :self.D].copy(), W=pp[:, self.D].copy(), Q=pp[:, self.D + 1].copy())
         return out
 
+    # -- z slabs ------------------------------------------------------------
+    def exchange_bytes(self, side):
+        n = ct.c_size_t()
+        self._check(lib().lbm_slab_exchange_bytes(self.h, int(side), ct.byref(n)))
+        return n.value
+
+    def slab_pack(self, side, dst):
+        """Pack the owned planes next to `side` into dst (a torch CUDA uint8
+        tensor of exchange_bytes(side) bytes)."""
+        self._check(lib().lbm_slab_pack(self.h, int(side), _ptr(dst)))
+
+    def slab_unpack(self, side, src):
+        self._check(lib().lbm_slab_unpack(self.h, int(side), _ptr(src)))
+
+    def wall_diagnostics(self, per_point=True):
+        """lbm_get_wall_diagnostics: C_d, C_l (C_l2 in 3D), Nu and, per
+        Lagrangian point, C_p, tau_w, u^s, T^s and (dT/dn)^s of the current
+        field."""
+        D = self.D
+        co = (ct.c_double * 4)()
+        pp = np.empty(self.NL * (2 * D + 3)) if per_point else None
+        self._check(lib().lbm_get_wall_diagnostics(self.h, co, _ptr(pp)))
+        out = dict(Cd=co[0], Cl=co[1], Cl2=co[2], Nu=co[3])
+        if per_point:
+            pp = pp.reshape(self.NL, 2 * D + 3)
+            out.update(Cp=pp[:, 0].copy(), tau_w=pp[:, 1:1 + D].copy(), u_s=pp[:, 1 + D:1 + 2 * D].copy(),
+                       T_s=pp[:, 1 + 2 * D].copy(), dTdn=pp[:, 2 + 2 * D].copy())
+        return out
+
     def wall_loads_noalloc(self):
         """lbm_get_wall_loads_noalloc: the same loads with no device allocation
         (static scratch, at most 65536 points)."""
@@ -300,6 +357,7 @@ class CaseView(Solver):
         self.N = int(np.prod(self.shape))
         self.zyx = tuple(reversed(self.shape))
         self.NL = 0
+        self.slab = None
 
     def close(self):
         self.h = None

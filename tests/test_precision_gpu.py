@@ -8,19 +8,21 @@ from tests import _cases as C
 
 pytestmark = pytest.mark.gpu
 
-STEPS = 2000
+STEPS = 6000
 
 
 @pytest.fixture(scope="module")
 def cylinder_runs():
+    """The 2D cylinder case (Re 40, a steady wake) in each storage form: drag
+    and wall heat as running means over the last 2000 of 6000 steps."""
+    import bench
     case = C.cylinder_c1()
     _, geo = C.make_oracle(case)
     out = {}
     for p in ("fp32", "fp16", "bf16"):
         g = C.make_gpu(case, p, geo)
-        g.step(STEPS)
-        g.check()
-        out[p] = g.wall_loads()
+        cd, nu = bench.coefficient_history(g, STEPS, 50)
+        out[p] = bench.steady_summary(cd, nu, 50, 2000)
         g.close()
     return out
 
@@ -30,18 +32,19 @@ def _rel(a, b):
 
 
 def test_fp16_drag_and_heat_within_0p1_percent(cylinder_runs):
-    """FP16 deviation storage: drag and wall heat flux within 0.1% of FP32."""
+    """FP16 deviation storage: steady drag and Nusselt number within 0.1% of
+    FP32."""
     r32, r16 = cylinder_runs["fp32"], cylinder_runs["fp16"]
-    assert _rel(r16["force"][0], r32["force"][0]) < 1e-3
-    assert _rel(r16["heat"], r32["heat"]) < 1e-3
+    assert _rel(r16["Cd"], r32["Cd"]) < 1e-3
+    assert _rel(r16["Nu"], r32["Nu"]) < 1e-3
 
 
 def test_bf16_drag_and_heat_within_1_percent(cylinder_runs):
-    """BF16 (8-bit mantissa) storage: within 1% of FP32; it does not reach
-    the 0.1% drag bar on this case (about 0.4%)."""
+    """BF16 (8-bit mantissa) storage: within 1% of FP32 (its rounding of the
+    populations, 2^-9 relative, is above the 0.1% bar's budget)."""
     r32, rb = cylinder_runs["fp32"], cylinder_runs["bf16"]
-    assert _rel(rb["force"][0], r32["force"][0]) < 1e-2
-    assert _rel(rb["heat"], r32["heat"]) < 1e-2
+    assert _rel(rb["Cd"], r32["Cd"]) < 1e-2
+    assert _rel(rb["Nu"], r32["Nu"]) < 1e-2
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
@@ -60,3 +63,41 @@ def test_sphere_case_stays_finite(precision):
     w = s.wall_loads()
     assert np.isfinite(w["force"]).all() and w["force"][0] > 0
     s.close()
+
+
+@pytest.fixture(scope="module")
+def sphere_means():
+    """A 48x32x32 downscale of the sphere case (D = 8, 252 points, Ma 0.3,
+    Re 100 so that the flow settles, isothermal wall) run 4000 steps in each
+    storage form; C_d and Nu are running means over the last 1000 steps."""
+    import bench
+    from paper_2607_07432_b300 import inputs, lbmib
+    out = {}
+    for prec in ("fp64", "fp32", "fp16", "bf16"):
+        s = lbmib.Solver("D3Q19", prec, (48, 32, 32), mach=0.3, reynolds=100.0, ref_length=8.0,
+                         bc=[lbmib.BC_INLET, lbmib.BC_OUTLET] + [lbmib.BC_FARFIELD] * 4)
+        th = s.constants()["theta_inf"]
+        s.set_geometry(inputs.icosphere((12.0, 16.0, 16.0), 8.0, 5, tbc=0, t_value=1.1 * th))
+        cd, nu = bench.coefficient_history(s, 4000, 50)
+        s.close()
+        out[prec] = bench.steady_summary(cd, nu, 50, 1000)
+    return out
+
+
+def test_sphere_fp32_and_fp16_means_within_0p1_percent_of_fp64(sphere_means):
+    """Drag and Nusselt running means of the FP32 path within 0.01% and of
+    FP16 storage within 0.1% of the FP64 path (the FP64 path equals the
+    oracle to 1e-12)."""
+    m = sphere_means
+    assert _rel(m["fp32"]["Cd"], m["fp64"]["Cd"]) < 1e-4
+    assert _rel(m["fp32"]["Nu"], m["fp64"]["Nu"]) < 1e-4
+    assert _rel(m["fp16"]["Cd"], m["fp64"]["Cd"]) < 1e-3
+    assert _rel(m["fp16"]["Nu"], m["fp64"]["Nu"]) < 1e-3
+    assert m["fp64"]["Cd"] > 0 and m["fp64"]["Nu"] > 0
+
+
+def test_sphere_bf16_means_within_1_percent_of_fp64(sphere_means):
+    """BF16 storage: drag and Nusselt running means within 1% of FP64."""
+    m = sphere_means
+    assert _rel(m["bf16"]["Cd"], m["fp64"]["Cd"]) < 1e-2
+    assert _rel(m["bf16"]["Nu"], m["fp64"]["Nu"]) < 1e-2
