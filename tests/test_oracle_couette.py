@@ -85,3 +85,33 @@ def test_steady_profile_is_linear():
     assert np.abs(np.polyval(c, YS[INNER]) - u[INNER]).max() < 0.005 * U
     # and its slope is U over a channel within a cell of the nominal height
     assert abs(U / c[0] - H) < 1.0
+
+
+@pytest.mark.timeout(300)
+def test_viscous_heating_profile():
+    """Couette flow with viscous heating (both walls isothermal at T_w, the
+    upper one moving at Ma 0.3): the steady temperature is the parabola
+    T_w + (mu U^2 / 2 lambda) eta (1 - eta).  Checked locally, where the
+    diffuse walls do not enter: the interior profile is a parabola (fit
+    residual below 1e-4 of the rise) whose curvature balances the viscous
+    work, lambda T'' = -mu (du/dy)^2, with the measured shear rate (within
+    0.5%; measured 3e-5); the peak rise is mu U^2 / (8 lambda) within 10%
+    (the effective walls sit about half a cell inside the points, which
+    raises the shear rate by 6%).  This pins the viscous work carried into
+    the energy equation by the LB momentum fluxes of Eq. energy and the
+    conductivity lambda = mu C_p / Pr."""
+    mach = 0.3
+    U = mach * np.sqrt(1.4 / 3.0 * THETA)
+    prm = lbm.Params("D2Q9", (NX, NY), method=IB.FODIBM_R, mach=mach, reynolds=U * H / MU, ref_length=H,
+                     theta_inf=THETA)
+    sim = lbm.Sim(prm, geometry(prm.u_mag, prm.theta_inf))
+    sim.run(4000)
+    _, u, T, _ = sim.fields()
+    ux, Ty = u[0][:, 1], T[:, 1]
+    Y = YS[INNER]
+    cu = np.polyfit(Y, ux[INNER], 1)
+    cT = np.polyfit(Y, Ty[INNER], 2)
+    rise = Ty[INNER].max() - THETA
+    assert np.abs(np.polyval(cT, Y) - Ty[INNER]).max() < 1e-4 * rise
+    assert abs(2 * cT[0] / (-prm.mu * cu[0] ** 2 / prm.lam) - 1.0) < 5e-3
+    assert abs(rise / (prm.mu * prm.u_mag ** 2 / (8 * prm.lam)) - 1.0) < 0.10
