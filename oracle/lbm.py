@@ -71,7 +71,7 @@ from . import ib as IB
 
 CS2 = L.CS2
 
-BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_GHOST = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_GHOST, BC_CHAR = 0, 1, 2, 3, 4, 5
 TAU_THETA, TAU_LITERAL = 0, 1
 # a^C readings (Q6): off, the diagonal cubic defect only, full (default)
 AC_OFF, AC_CUBIC, AC_FULL = 0, 1, 2
@@ -407,13 +407,73 @@ def freestream(prm, shape_zyx):
     return f, E
 
 
+def characteristic_face(prm, f, E, a, side):
+    """Characteristic far field on the face (axis a, side) (SURVEY NEXT item;
+    the paper cites characteristic boundaries without giving them): the face
+    nodes take the equilibrium of the state built from the linearized
+    one-dimensional Riemann invariants normal to the face,
+        W+ = p + rho c u_n, W- = p - rho c u_n, W0 = rho - p / c^2, u_t,
+    each taken from the interior neighbour when its characteristic leaves
+    the domain (speed u_n + c, u_n - c, u_n, u_n > 0 with u_n along the
+    outward normal) and from the free stream when it enters; rho c and c^2
+    are the neighbour's.  Returns the face populations and rho E."""
+    lat = prm.lat
+    D = lat.D
+    zyx = f.shape[1:]
+    ax = len(zyx) - 1 - a
+    n = zyx[ax]
+    sl = [slice(None)] * len(zyx)
+    sl[ax] = 1 if side == 0 else n - 2
+    fi = f[(slice(None),) + tuple(sl)]
+    Ei = E[tuple(sl)]
+    c = lat.c.astype(np.float64)
+    rho = np.zeros(fi.shape[1:])
+    j = np.zeros((D,) + fi.shape[1:])
+    for i in range(lat.Q):
+        rho = rho + fi[i]
+        for b in range(D):
+            if c[i, b] != 0:
+                j[b] = j[b] + c[i, b] * fi[i]
+    u = j / rho
+    th = (Ei / rho - 0.5 * (u * u).sum(axis=0)) / prm.Cv
+    p = rho * prm.R * th
+    cs = np.sqrt(prm.gamma * prm.R * th)
+    sgn = -1.0 if side == 0 else 1.0
+    un = sgn * u[a]
+    un_inf = sgn * prm.u_inf[a]
+    p_inf = prm.rho_inf * prm.R * prm.theta_inf
+    rc = rho * cs
+    c2 = cs * cs
+    Wp = np.where(un + cs > 0.0, p + rc * un, p_inf + rc * un_inf)
+    Wm = np.where(un - cs < 0.0, p_inf - rc * un_inf, p - rc * un)
+    out = un > 0.0
+    W0 = np.where(out, rho - p / c2, prm.rho_inf - p_inf / c2)
+    pb = 0.5 * (Wp + Wm)
+    unb = (Wp - Wm) / (2.0 * rc)
+    rb = W0 + pb / c2
+    ub = np.empty_like(u)
+    for b in range(D):
+        ub[b] = sgn * unb if b == a else np.where(out, u[b], prm.u_inf[b])
+    thb = pb / (rb * prm.R)
+    fb = equilibrium(lat, rb, ub, thb)
+    Eb = rb * (0.5 * (ub * ub).sum(axis=0) + prm.Cv * thb)
+    return fb, Eb
+
+
 def apply_bc(prm, f, E):
     """Q24 far field on the outermost nodes of non-periodic axes: outlet faces
-    copy the neighbouring inner plane first, then inlet / far-field faces are
-    set to the free-stream equilibrium (so edges and corners are free-stream)."""
+    copy the neighbouring inner plane first, then characteristic faces take
+    the state of their Riemann invariants (computed from the state before
+    any face is set), then inlet / far-field faces are set to the free-stream
+    equilibrium (so edges and corners with them are free-stream); a node on
+    two or more characteristic faces (an edge between them) is set to the
+    free-stream equilibrium too."""
     D = prm.lat.D
     zyx = f.shape[1:]
     feq1, E1 = freestream(prm, ())
+    chars = [(a, side) for a in range(D) for side in (0, 1) if prm.bc[2 * a + side] == BC_CHAR]
+    assert not (chars and BC_OUTLET in prm.bc[:2 * D]), "characteristic faces are not combined with outlets"
+    cvals = [characteristic_face(prm, f, E, a, side) for (a, side) in chars]
     for a in range(D):
         ax = len(zyx) - 1 - a
         for side in (0, 1):
@@ -426,6 +486,24 @@ def apply_bc(prm, f, E):
             sl_s[ax] = 1 if side == 0 else n - 2
             f[(slice(None),) + tuple(sl_d)] = f[(slice(None),) + tuple(sl_s)]
             E[tuple(sl_d)] = E[tuple(sl_s)]
+    for (a, side), (fb, Eb) in zip(chars, cvals):
+        ax = len(zyx) - 1 - a
+        sl = [slice(None)] * len(zyx)
+        sl[ax] = 0 if side == 0 else zyx[ax] - 1
+        f[(slice(None),) + tuple(sl)] = fb
+        E[tuple(sl)] = Eb
+    if len(chars) > 1:
+        # edges between characteristic faces
+        count = np.zeros(zyx, dtype=int)
+        for (a, side) in chars:
+            ax = len(zyx) - 1 - a
+            sl = [slice(None)] * len(zyx)
+            sl[ax] = 0 if side == 0 else zyx[ax] - 1
+            count[tuple(sl)] += 1
+        edge = count >= 2
+        for i in range(prm.lat.Q):
+            f[i][edge] = feq1[i]
+        E[edge] = E1
     for a in range(D):
         ax = len(zyx) - 1 - a
         for side in (0, 1):
