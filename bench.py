@@ -390,6 +390,67 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def run_convergence(args):
+    """Grid convergence of the wall pressure coefficient (paper Sec. 3.1: L2
+    error of C_p against the finest mesh at identical wall locations), read
+    at X_l (Eq. int1, d = 2, nodes on both sides of the wall) and at the
+    projection points (d = 1, fluid nodes), and of C_d: the
+    2D cylinder case (Ma 0.2, Re 40, isothermal wall 1.1 T_inf, FODIBM-R and
+    FODIBM) at D = 20, 40, 80 on 10D x 5D grids, against D = 160; 64 D / 20
+    Lagrangian points so that every coarse point is also a fine point; FP32;
+    each run to a steady C_d (running mean settled within 0.01%)."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    Ds = (20, 40, 80, 160)
+    res = {}
+    for method in (lbmib.FODIBM_R, lbmib.FODIBM):
+        cps = {}
+        for D in Ds:
+            nx, ny = 10 * D, 5 * D
+            s = lbmib.Solver("D2Q9", "fp32", (nx, ny), mach=0.2, reynolds=40.0, ref_length=float(D),
+                             method=method, bc=[lbmib.BC_INLET, lbmib.BC_OUTLET, lbmib.BC_FARFIELD, lbmib.BC_FARFIELD])
+            c = s.constants()
+            th = c["theta_inf"]
+            s.set_geometry(inputs.cylinder((3.0 * D, 2.5 * D), float(D), 64 * D // 20, tbc=0, t_value=1.1 * th))
+            chunk = int(2 * D / c["u_mag"])
+            prev, steps = None, 0
+            t0 = time.perf_counter()
+            while True:
+                s.step(chunk)
+                steps += chunk
+                cd = s.wall_diagnostics(per_point=False)["Cd"]
+                if prev is not None and abs(cd - prev) < 1e-4 * abs(cd) and steps > 20 * chunk:
+                    break
+                prev = cd
+                if steps > 400 * chunk:
+                    break
+            s.check()
+            d = s.wall_diagnostics()
+            cps[D] = dict(Cp=d["Cp"], CpP=d["CpP"], Cd=d["Cd"], steps=steps, theta_inf=th,
+                          wall_s=time.perf_counter() - t0)
+            s.close()
+        out = {}
+        for key in ("Cp", "CpP"):
+            ref = cps[Ds[-1]][key]
+            err = {}
+            for D in Ds[:-1]:
+                r = ref[::Ds[-1] // D]
+                err[D] = float(np.sqrt(((cps[D][key] - r) ** 2).sum() / (r ** 2).sum()))
+            orders = [float(np.log(err[Ds[k]] / err[Ds[k + 1]]) / np.log(2.0)) for k in range(len(Ds) - 2)]
+            out[key] = dict(L2_error=err, observed_order=orders)
+        cds = [cps[D]["Cd"] for D in Ds]
+        out["Cd_order"] = [float(np.log(abs(cds[k] - cds[k + 1]) / abs(cds[k + 1] - cds[k + 2])) / np.log(2.0))
+                           for k in range(len(Ds) - 2)]
+        out["runs"] = {D: dict(Cd=v["Cd"], steps=v["steps"], theta_inf=v["theta_inf"], wall_s=v["wall_s"])
+                       for D, v in cps.items()}
+        res["FODIBM-R" if method == lbmib.FODIBM_R else "FODIBM"] = out
+    line = {"metric": "L2 error of C_p against D = 160 and observed order (2D cylinder, Ma 0.2, Re 40)",
+            "value": res["FODIBM-R"]["CpP"]["observed_order"][-1], "unit": "order", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": "2D cylinder, 10D x 5D, D = 20/40/80/160"},
+            "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args):
     """Learned warm start on 512x256 two-body cases (a circle and an
     ellipse, diameters 10-40 cells, Ma 0.1-0.3, Re 20-45 so that every case
@@ -591,7 +652,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-forms", action="store_true",
                     help="skip the FP16 / BF16 storage and 64-case batch sub-records")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
+                                                                    "convergence"])
     ap.add_argument("--prec-steps-small", type=int, default=20000)
     ap.add_argument("--prec-steps-full", type=int, default=40000)
     ap.add_argument("--ws-cases", type=int, default=256)
@@ -609,6 +671,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "convergence":
+        return run_convergence(args)
     args.warmup = max(args.warmup, 3)
     import torch
     torch.cuda.set_device(local)

@@ -56,8 +56,14 @@ enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16DEV = 2, LBM_BF16DEV = 3 };
 /* immersed boundary method (Sec. 2.3, 2.4, Table 1) */
 enum { IB_DIBM = 0, IB_FODIBM = 1, IB_FODIBM_R = 2 };
 /* per-face domain boundary: periodic; free-stream equilibrium (inlet or far
- * field); zero-gradient outlet.  Faces: x-, x+, y-, y+, z-, z+. */
-enum { LBM_BC_PERIODIC = 0, LBM_BC_INLET = 1, LBM_BC_OUTLET = 2, LBM_BC_FARFIELD = 3 };
+ * field); zero-gradient outlet; characteristic far field (the equilibrium of
+ * the state whose linearized one-dimensional Riemann invariants normal to the
+ * face, p +- rho c u_n, rho - p/c^2 and u_t, come from the interior neighbour
+ * when they leave the domain and from the free stream when they enter; an
+ * edge between two characteristic faces takes the free stream; not combined
+ * with an outlet face, LBM_EINVAL).  Faces: x-, x+, y-, y+, z-, z+. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_INLET = 1, LBM_BC_OUTLET = 2, LBM_BC_FARFIELD = 3,
+       LBM_BC_CHARACTERISTIC = 5 };
 /* relaxation time: tau_LB = mu/(rho c_s^2 theta), or tau_LB = nu/c_s^2 = mu/(rho c_s^2)
  * as written in Eq. LB (the default; the theta-scaled variant is not stable for
  * theta < 1 and gives a shear viscosity mu/theta) */
@@ -211,15 +217,17 @@ lbm_status lbm_get_wall_loads_noalloc(lbm_handle* h, double force[3], double* he
  *   with q_inf = rho_inf u_inf^2 / 2, L = ref_length, A = L (2D, per unit
  *   depth) or pi L^2 / 4 (3D), S = pi L (2D) or pi L^2 (3D): the frontal
  *   area and surface of a circle or sphere of diameter L.
- * per_point (optional, host, N_L rows of 2D + 3 doubles):
+ * per_point (optional, host, N_L rows of 2D + 4 doubles):
  *   C_p = (p^s - p_inf) / q_inf with p^s by Eq. int1 (d = 2, nodes on both
  *   sides of the wall) at X_l; tau_w[D] = mu ((u^P - u^B) - its normal
  *   part) / d_n with u^P by Eq. int1 (d = 1) at the projection point;
- *   u^s[D] and T^s by Eq. int1 (d = 2) at X_l; (dT/dn)^s = (T^P - T^s) / d_n.
+ *   u^s[D] and T^s by Eq. int1 (d = 2) at X_l; (dT/dn)^s = (T^P - T^s) / d_n;
+ *   C_p^P, the pressure coefficient at the projection point (d = 1: fluid
+ *   nodes only, d_n cells off the wall).
  * The boundary errors of Sec. 3.2 follow: eps_Dir = |u^s - u^Bt| / u_inf,
  * eps_iso = |T^s - T^Bt| / T_inf, eps_Neu = |(dT/dn)^s - g| D / T_inf.
  * LBM_ESTATE without a body, LBM_EGEOM if a diagnostic stencil leaves a
- * non-periodic domain.  Allocates a device buffer of N_L (2D + 3) doubles
+ * non-periodic domain.  Allocates a device buffer of N_L (2D + 4) doubles
  * for the call when per_point is given. */
 lbm_status lbm_get_wall_diagnostics(lbm_handle* h, double coeffs[4], double* per_point);
 

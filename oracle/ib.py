@@ -29,7 +29,9 @@ Readings (paper silent or ambiguous):
   Q26 wall diagnostics (the paper defines C_p and the boundary errors, not
       the discrete wall shear or heat flux): tau_w = mu [(u^P - u^B) minus
       its normal part] / d_n, (dT/dn)^s = (T^P - T^s) / d_n, with u^P, T^P
-      by Eq. int1 at d = 1 and T^s by Eq. int1 at d = 2.
+      by Eq. int1 at d = 1 and T^s by Eq. int1 at d = 2; besides C_p at X_l
+      (d = 2, nodes on both sides of the wall) also C_p at P_l (d = 1, fluid
+      nodes only).
 """
 import functools
 import math
@@ -317,7 +319,8 @@ class Setup:
     def diagnostics(self, rho, u, T):
         """Wall quantities of the updated field (grid-shaped rho, u (D, grid),
         T): per point C_p (Sec. 3.1), the wall shear stress vector tau_w,
-        u^s and T^s at X_l and (dT/dn)^s (reading Q26)."""
+        u^s and T^s at X_l, (dT/dn)^s, and C_p at the projection point P_l
+        (Eq. int1, d = 1: fluid nodes only) (reading Q26)."""
         prm = self.prm
         D = self.D
         NL = self.NL
@@ -329,6 +332,7 @@ class Setup:
         T_s = self.interp(T.ravel(), nodes, wts, ones)
         uP = np.stack([self.interp(u[a].ravel(), self.P_nodes, self.P_w, ones) for a in range(D)], axis=1)
         TP = self.interp(T.ravel(), self.P_nodes, self.P_w, ones)
+        pP = self.interp(p.ravel(), self.P_nodes, self.P_w, ones)
         p_inf = prm.rho_inf * prm.R * prm.theta_inf
         q_inf = 0.5 * prm.rho_inf * prm.u_mag * prm.u_mag
         Cp = (p_s - p_inf) / q_inf
@@ -336,7 +340,7 @@ class Setup:
         dn_comp = (du * self.nrm).sum(axis=1)
         tau = prm.mu * (du - dn_comp[:, None] * self.nrm) / prm.d_n
         dTdn = (TP - T_s) / prm.d_n
-        return dict(Cp=Cp, tau_w=tau, u_s=u_s, T_s=T_s, dTdn=dTdn, p_s=p_s)
+        return dict(Cp=Cp, tau_w=tau, u_s=u_s, T_s=T_s, dTdn=dTdn, p_s=p_s, CpP=(pP - p_inf) / q_inf)
 
     def interp(self, field_flat, nodes, wts, scale):
         return np.array([scale[l] * sum(field_flat[n] * w for n, w in zip(nodes[l], wts[l]))

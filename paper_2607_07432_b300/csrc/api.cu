@@ -120,9 +120,15 @@ lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle**
       cfg->precision > LBM_BF16DEV || cfg->method < IB_DIBM || cfg->method > IB_FODIBM_R || cfg->use_ac < 0 ||
       cfg->use_ac > 2)
     return LBM_EINVAL;
-  for (int f = 0; f < 2 * D; ++f)
-    if ((cfg->bc[f] < LBM_BC_PERIODIC || cfg->bc[f] > LBM_BC_FARFIELD) && !(slab && cfg->bc[f] == kBCGhostFace))
+  bool has_char = false, has_outlet = false;
+  for (int f = 0; f < 2 * D; ++f) {
+    const int t = cfg->bc[f];
+    if ((t < LBM_BC_PERIODIC || t > LBM_BC_FARFIELD) && t != LBM_BC_CHARACTERISTIC && !(slab && t == kBCGhostFace))
       return LBM_EINVAL;
+    has_char = has_char || t == LBM_BC_CHARACTERISTIC;
+    has_outlet = has_outlet || t == LBM_BC_OUTLET;
+  }
+  if (has_char && has_outlet) return LBM_EINVAL;  // a characteristic face is the outflow face
   for (int a = 0; a < D; ++a)
     if ((cfg->bc[2 * a] == LBM_BC_PERIODIC) != (cfg->bc[2 * a + 1] == LBM_BC_PERIODIC)) return LBM_EINVAL;
   const Ops* ops = pick_ops(cfg->lattice, cfg->precision);
@@ -1079,7 +1085,7 @@ lbm_status lbm_get_wall_diagnostics(lbm_handle* h, double coeffs[4], double* per
                     : 0.0;
   }
   if (per_point) {
-    const size_t bytes = (size_t)h->NL * (2 * D + 3) * 8;
+    const size_t bytes = (size_t)h->NL * (2 * D + 4) * 8;
     double* buf = nullptr;
     int* derr = nullptr;
     CK(cudaMalloc(&buf, bytes + 16));

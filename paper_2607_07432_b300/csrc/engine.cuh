@@ -133,6 +133,12 @@ struct Engine {
   static BCFaces bc_faces(lbm_handle* h) {
     BCFaces bf;
     for (int face = 0; face < 6; ++face) bf.type[face] = face < 2 * L::D ? h->cfg.bc[face] : 0;
+    bf.rho_inf = h->rho_inf;
+    for (int a = 0; a < 3; ++a) bf.u_inf[a] = h->u_inf[a];
+    bf.p_inf = h->rho_inf * h->R * h->theta_inf;
+    bf.gamma = h->gamma;
+    bf.R = h->R;
+    bf.Cv = h->Cv;
     return bf;
   }
   static lbm_status ib_force(lbm_handle* h) {
@@ -149,11 +155,10 @@ struct Engine {
     });
   }
   static lbm_status bc(lbm_handle* h) {
-    BCFaces bf;
+    BCFaces bf = bc_faces(h);
     int maxplane = 0;
     const int skip_x = bc_in_kernel(h) ? 1 : 0;
     for (int face = 0; face < 6; ++face) {
-      bf.type[face] = face < 2 * L::D ? h->cfg.bc[face] : 0;
       if (face < 2 * L::D && bf.type[face] && !(skip_x && face < 2)) {
         FacePlane fp{face / 2, face % 2};
         maxplane = std::max(maxplane, fp.count(h->g));
@@ -231,6 +236,8 @@ struct Engine {
   // nodes before the kernel's equilibrium wins on the edges)
   static bool bc_in_kernel(lbm_handle* h) {
     if (!h->bc_in_kernel || h->g.n[0] < 4) return false;
+    for (int f = 0; f < 2 * L::D; ++f)
+      if (h->cfg.bc[f] == kBCChar) return false;
     if (h->cfg.bc[0] == LBM_BC_PERIODIC || h->cfg.bc[1] == LBM_BC_PERIODIC) return false;
     if (h->cfg.bc[1] == LBM_BC_OUTLET && (h->g.n[0] - 1) % FusedTile<L, C>::TX == 0) return false;
     for (int f = 2; f < 2 * L::D; ++f)

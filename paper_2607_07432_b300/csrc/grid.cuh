@@ -10,6 +10,8 @@ namespace lbmib {
 // the LBM_BC_* values): no boundary condition there; its ghost planes are
 // refreshed by the slab exchange.
 constexpr int kBCGhostFace = 4;
+// characteristic far field (LBM_BC_CHARACTERISTIC)
+constexpr int kBCChar = 5;
 
 // Domain extent and per-axis periodicity.  Non-periodic axes clamp
 // out-of-range stencil reads to the edge node (zero-gradient).

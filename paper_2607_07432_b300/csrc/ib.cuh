@@ -729,8 +729,9 @@ static __global__ void k_ib_spread_apply(int D, long long N, int n_rows, const i
 // Omega (nodes on both sides of the wall), u and T at the projection point
 // P_l by Eq. int1 with d = 1 (the per-step stencils), then per point
 //   C_p = (p^s - p_inf) / q_inf, tau_w = mu [(u^P - u^B) - normal part] / d_n,
-//   u^s, T^s, (dT/dn)^s = (T^P - T^s) / d_n
-// in out[l * (2D + 3) + ...] (C_p, tau_w[D], u^s[D], T^s, (dT/dn)^s).
+//   u^s, T^s, (dT/dn)^s = (T^P - T^s) / d_n, and C_p at P_l (d = 1, fluid
+//   nodes only)
+// in out[l * (2D + 4) + ...] (C_p, tau_w[D], u^s[D], T^s, (dT/dn)^s, C_p^P).
 struct DiagDev {
   int NL, D;
   double R, Cv, mu, d_n, p_inf, q_inf;
@@ -791,7 +792,7 @@ static __global__ void k_wall_diag(Grid g, DiagDev d, const C* M) {
         for (int a = 0; a < D; ++a) us[a] = us[a] + u[a] * wt;
         Ts = Ts + T * wt;
       }
-  double uP[3] = {0, 0, 0}, TP = 0.0;
+  double uP[3] = {0, 0, 0}, TP = 0.0, pP = 0.0;
   for (int k = 0; k < KP; ++k) {
     const int n = d.psten_node[l * KP + k];
     if (n < 0) continue;
@@ -800,13 +801,14 @@ static __global__ void k_wall_diag(Grid g, DiagDev d, const C* M) {
     node_pred<L, C>(M, g.N, n, rho, j, u, T, C(d.Cv));
     for (int a = 0; a < D; ++a) uP[a] = uP[a] + u[a] * w;
     TP = TP + T * w;
+    pP = pP + ((rho * d.R) * T) * w;
   }
   double du[3], dn = 0.0;
   for (int a = 0; a < D; ++a) {
     du[a] = uP[a] - (d.uB ? d.uB[l * D + a] : 0.0);
     dn = dn + du[a] * d.nrm[l * D + a];
   }
-  double* o = d.out + (long long)l * (2 * D + 3);
+  double* o = d.out + (long long)l * (2 * D + 4);
   o[0] = (ps - d.p_inf) / d.q_inf;
   for (int a = 0; a < D; ++a) {
     o[1 + a] = d.mu * (du[a] - dn * d.nrm[l * D + a]) / d.d_n;
@@ -814,6 +816,7 @@ static __global__ void k_wall_diag(Grid g, DiagDev d, const C* M) {
   }
   o[1 + 2 * D] = Ts;
   o[2 + 2 * D] = (TP - Ts) / d.d_n;
+  o[3 + 2 * D] = (pP - d.p_inf) / d.q_inf;
 }
 
 // wall loads: fixed-order block reduction (deterministic)

@@ -527,7 +527,10 @@ __global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
 // equilibrium face copies its inner neighbour along the outlet axis.  This is
 // the outlet-copy-then-equilibrium order with the edges resolved up front.
 struct BCFaces {
-  int type[6];  // LBM_BC_* per face: 0 periodic, 1 inlet, 2 outlet, 3 far field, 4 slab ghost face
+  int type[6];  // LBM_BC_* per face: 0 periodic, 1 inlet, 2 outlet, 3 far field, 4 slab ghost face,
+                // 5 characteristic far field
+  // free stream and gas constants of the characteristic faces
+  double rho_inf, u_inf[3], p_inf, gamma, R, Cv;
 };
 
 // boundary node t of face `face` (see k_bc_all_m)
@@ -570,6 +573,81 @@ __device__ __forceinline__ void bc_node(const Grid& g, S* f, C* M, const BCFaces
 #pragma unroll
     for (int a = 0; a < D; ++a) M[(1 + a) * g.N + dst] = j[a];
     M[(1 + D) * g.N + dst] = E_inf;
+    return;
+  }
+  // free-stream equilibrium at dst with its moments, as stored
+  auto put_state = [&](auto feq_of, C E) {
+    C r = C(0), j[3] = {C(0), C(0), C(0)};
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const C fe = feq_of(I);
+      store_pop<L, S, C>(f, i, g.N, dst, fe, C(g.thref));
+      const C v = roundtrip_pop<L, S, C>(i, fe, C(g.thref));
+      r += v;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        if (L::c(i, a) != 0) j[a] += C(L::c(i, a)) * v;
+    });
+    M[dst] = r;
+#pragma unroll
+    for (int a = 0; a < D; ++a) M[(1 + a) * g.N + dst] = j[a];
+    M[(1 + D) * g.N + dst] = E;
+  };
+  if (ft == kBCChar) {
+    // a node on two or more characteristic faces (an edge between them)
+    // takes the free stream, written by the first of those faces
+    int nchar = 0, first = -1;
+    for (int b = 0; b < D; ++b)
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (bf.type[2 * b + s2] == kBCChar && c[b] == (s2 ? g.n[b] - 1 : 0)) {
+          ++nchar;
+          if (first < 0) first = 2 * b + s2;
+        }
+    if (nchar >= 2) {
+      if (face == first) put_state([&](auto I) { return feq_inf[decltype(I)::value]; }, E_inf);
+      return;
+    }
+    // the state of the linearized one-dimensional Riemann invariants normal
+    // to the face: W+ = p + rho c u_n, W- = p - rho c u_n, W0 = rho - p/c^2
+    // and u_t, each from the interior neighbour when its characteristic
+    // leaves the domain and from the free stream when it enters (the
+    // neighbour's carried moments are this step's streamed values)
+    int ci[3] = {c[0], c[1], c[2]};
+    ci[axis] = side ? g.n[axis] - 2 : 1;
+    const long long src = g.lin(ci[0], ci[1], ci[2]);
+    const C rho = M[src];
+    C u[3] = {C(0), C(0), C(0)}, uu = C(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      u[b] = M[(1 + b) * g.N + src] / rho;
+      uu = uu + u[b] * u[b];
+    }
+    const C Rg = C(bf.R), Cv = C(bf.Cv);
+    const C th = (M[(1 + D) * g.N + src] / rho - C(0.5) * uu) / Cv;
+    const C p = rho * Rg * th;
+    const C cs = sqrt(C(bf.gamma) * Rg * th);
+    const C sgn = side ? C(1) : C(-1);
+    const C un = sgn * u[axis];
+    const C un_inf = sgn * C(bf.u_inf[axis]);
+    const C p_inf = C(bf.p_inf);
+    const C rc = rho * cs;
+    const C c2 = cs * cs;
+    const C Wp = (un + cs > C(0)) ? p + rc * un : p_inf + rc * un_inf;
+    const C Wm = (un - cs < C(0)) ? p_inf - rc * un_inf : p - rc * un;
+    const bool out = un > C(0);
+    const C W0 = out ? rho - p / c2 : C(bf.rho_inf) - p_inf / c2;
+    const C pb = C(0.5) * (Wp + Wm);
+    const C unb = (Wp - Wm) / (C(2) * rc);
+    const C rb = W0 + pb / c2;
+    C ub[3] = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int b = 0; b < D; ++b) ub[b] = b == axis ? sgn * unb : (out ? u[b] : C(bf.u_inf[b]));
+    const C thb = pb / (rb * Rg);
+    C kb = C(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) kb = kb + ub[b] * ub[b];
+    const C Eb = rb * (C(0.5) * kb + Cv * thb);
+    put_state([&](auto I) { return feq_i<L, C, decltype(I)::value>(rb, ub, thb); }, Eb);
     return;
   }
   if (ft != 2) return;

@@ -17,7 +17,7 @@ LIBPATH = os.path.join(HERE, "liblbmib.so")
 D2Q9, D3Q19 = 0, 1
 FP64, FP32, FP16DEV, BF16DEV = 0, 1, 2, 3
 DIBM, FODIBM, FODIBM_R = 0, 1, 2
-BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD = 0, 1, 2, 3
+BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_CHAR = 0, 1, 2, 3, 5
 TAU_THETA, TAU_LITERAL = 0, 1
 SHAPE_SPHERE, SHAPE_ELLIPSE, SHAPE_POLYGON, SHAPE_MASK = 0, 1, 2, 3
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EGEOM",
@@ -290,17 +290,17 @@ class Solver:
 
     def wall_diagnostics(self, per_point=True):
         """lbm_get_wall_diagnostics: C_d, C_l (C_l2 in 3D), Nu and, per
-        Lagrangian point, C_p, tau_w, u^s, T^s and (dT/dn)^s of the current
-        field."""
+        Lagrangian point, C_p, tau_w, u^s, T^s, (dT/dn)^s and C_p at the
+        projection point of the current field."""
         D = self.D
         co = (ct.c_double * 4)()
-        pp = np.empty(self.NL * (2 * D + 3)) if per_point else None
+        pp = np.empty(self.NL * (2 * D + 4)) if per_point else None
         self._check(lib().lbm_get_wall_diagnostics(self.h, co, _ptr(pp)))
         out = dict(Cd=co[0], Cl=co[1], Cl2=co[2], Nu=co[3])
         if per_point:
-            pp = pp.reshape(self.NL, 2 * D + 3)
+            pp = pp.reshape(self.NL, 2 * D + 4)
             out.update(Cp=pp[:, 0].copy(), tau_w=pp[:, 1:1 + D].copy(), u_s=pp[:, 1 + D:1 + 2 * D].copy(),
-                       T_s=pp[:, 1 + 2 * D].copy(), dTdn=pp[:, 2 + 2 * D].copy())
+                       T_s=pp[:, 1 + 2 * D].copy(), dTdn=pp[:, 2 + 2 * D].copy(), CpP=pp[:, 3 + 2 * D].copy())
         return out
 
     def wall_loads_noalloc(self):

@@ -9,7 +9,7 @@ from tests import _cases as C
 
 pytestmark = pytest.mark.gpu
 
-KEYS = ("Cp", "tau_w", "u_s", "T_s", "dTdn")
+KEYS = ("Cp", "tau_w", "u_s", "T_s", "dTdn", "CpP")
 
 
 def _check(gd, coeffs, per, atol):

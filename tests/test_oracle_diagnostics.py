@@ -45,6 +45,7 @@ def test_uniform_field_is_read_exactly():
     q_inf = 0.5 * prm.rho_inf * prm.u_mag ** 2
     d2 = S.diagnostics(rho * 1.01, u, T)
     assert np.allclose(d2["Cp"], 0.01 * prm.R * prm.theta_inf / q_inf, rtol=1e-12)
+    assert np.allclose(d2["CpP"], 0.01 * prm.R * prm.theta_inf / q_inf, rtol=1e-12)
 
 
 def test_linear_field_error_is_the_kernel_first_moment():
