@@ -114,3 +114,34 @@ def test_batched_3d_equals_individual():
         assert np.array_equal(fa, fb) and np.array_equal(Ea, Eb)
         s.close()
     b.close()
+
+
+def test_batched_full_grid_range_equals_individual():
+    """The two ends of the sweep's grid range in one batch, 256x128 and
+    1024x512 (FP32, characteristic far field on the outflow and lateral
+    faces as well as the equilibrium far field), bit for bit against each
+    case stepped alone."""
+    from paper_2607_07432_b300 import lbmib
+    specs = inputs.batch_cases(2, seed=20260001)
+    cases = [dict(shape=(256, 128), mach=0.3, reynolds=80.0, ref_length=20.0, bc=BC),
+             dict(shape=(1024, 512), mach=0.2, reynolds=150.0, ref_length=60.0, bc=[1, 5, 5, 5])]
+    b = lbmib.Batch("D2Q9", "fp32", cases)
+    solo = []
+    for k, c in enumerate(cases):
+        s = lbmib.Solver("D2Q9", "fp32", c["shape"], mach=c["mach"], reynolds=c["reynolds"],
+                         ref_length=c["ref_length"], bc=c["bc"])
+        th = s.constants()["theta_inf"]
+        geo = _geometry(c, specs[k], th)
+        s.set_geometry(geo)
+        b.case(k).set_geometry(geo)
+        solo.append(s)
+    b.step(6)
+    for s in solo:
+        s.step(6)
+    b.sync()
+    for k, s in enumerate(solo):
+        fa, Ea = b.case(k).state()
+        fb, Eb = s.state()
+        assert np.array_equal(fa, fb) and np.array_equal(Ea, Eb)
+        s.close()
+    b.close()
