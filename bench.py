@@ -479,12 +479,16 @@ def run_warmstart(args):
     t_train = time.perf_counter() - t0
     res = [ws.compare(net, c, run_steps, 100) for c in test_cases]
     net.close()
-    ok = [r for r in res if r["steps_uniform"] and r["steps_warm"]]
+    # the uniform run's drag at the end of the run is the reference answer;
+    # it is trusted only where that run has stayed in the band for the last
+    # 10000 steps ("settled"); the other cases are counted, not averaged
+    settled = [r for r in res if r["steps_uniform"] and r["steps_uniform"] <= run_steps - 10000]
+    ok = [r for r in settled if r["steps_warm"]]
     su = float(np.mean([r["steps_uniform"] for r in ok])) if ok else None
     sw = float(np.mean([r["steps_warm"] for r in ok])) if ok else None
     mu = float(np.mean([r["ms_uniform"] for r in ok])) if ok else None
     mw = float(np.mean([r["ms_warm"] for r in ok])) if ok else None
-    line = {"metric": "steps to the 0.1% drag band, warm start vs uniform start (mean over held-out cases)",
+    line = {"metric": "steps to the 0.1% drag band, warm start vs uniform start (mean over settled held-out cases)",
             "value": sw, "unit": "steps", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 solver, bf16 x bf16 -> f32 network", "data": "synthetic",
             "config": {"workload": "2D two-body cases 512x256 (circle + ellipse, D 10-40, Ma 0.1-%.2f, Re 20-45)"
@@ -492,6 +496,9 @@ def run_warmstart(args):
                        "train_cases": n_train, "gen_steps": gen_steps, "train_steps": train_steps, "batch": 8,
                        "held_out": n_test},
             "uniform_steps": su, "warm_ms": mw, "uniform_ms": mu, "step_ratio": (sw / su) if ok else None,
+            "settled_cases": len(settled), "warm_missed_band": len(settled) - len(ok),
+            "warm_faster": sum(r["steps_warm"] < r["steps_uniform"] for r in ok),
+            "unsettled_reference": len(res) - len(settled),
             "gen_s": t_gen, "train_s": t_train, "final_loss": float(losses[-50:].mean()),
             "cases": res}
     print(json.dumps(line), flush=True)
@@ -730,22 +737,29 @@ def main():
     s.check()
 
     # end-to-end through the public API with host buffers: the job uploads
-    # its initial fields from pinned host memory, steps, and reads the wall
-    # loads back every step; all copies are inside the timed region
+    # its initial fields from pinned host memory, steps, and copies the wall
+    # loads of every step into its own row of a pinned host array (queued
+    # behind the step, no per-step wait); after the last step it waits once
+    # and reads them all.  Every copy is inside the timed region.
     c = s.constants()
     rho0 = torch.full((N,), 1.0, dtype=torch.float64).pin_memory()
     u0 = torch.zeros((3 * N,), dtype=torch.float64)
     u0[:N] = c["u_mag"]
     u0 = u0.pin_memory()
     T0 = torch.full((N,), c["theta_inf"], dtype=torch.float64).pin_memory()
+    loads_h = torch.zeros((args.steps, 5), dtype=torch.float64).pin_memory()
     barrier()
     t0 = time.perf_counter()
     s.set_fields(rho0.numpy(), u0.numpy(), T0.numpy())
-    for _ in range(args.steps):
+    for k in range(args.steps):
         s.step(1)
-        s.wall_loads()
+        s.wall_loads_async(loads_h[k])
+    s.sync()
+    drag_hist = loads_h[:, 0].numpy().copy()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    if not np.all(np.isfinite(drag_hist)):
+        raise RuntimeError("non-finite wall loads in the end-to-end run")
     e2e = {"value": job_mlups(world, N, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(N * 5 * 8 / args.steps), "d2h_bytes_per_step": 5 * 8}
 

@@ -157,7 +157,11 @@ lbm_status lbm_get_fields(lbm_handle* h, int dst_is_device, double* rho, double*
 lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* rhoE);
 
 /* Replace the state: populations (Q*N) and rho E (N).  The stored
- * previous-step auxiliaries are reset as for a fresh start. */
+ * previous-step auxiliaries are reset as for a fresh start.  Host arrays in
+ * page-locked memory that the device can address (cudaHostAlloc /
+ * cudaMallocHost under unified addressing, cudaHostRegister with mapping)
+ * are read by the upload kernel in place; other host memory goes through a
+ * device buffer allocated for the call.  Returns after the upload. */
 lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, const double* rhoE);
 
 /* Checkpoint: write the complete time-stepping state of the handle to a
@@ -177,7 +181,8 @@ lbm_status lbm_save_state(lbm_handle* h, const char* path);
 lbm_status lbm_load_state(lbm_handle* h, const char* path);
 
 /* Set the state to the equilibrium of given fields (warm start): rho (N),
- * u (D*N), T (N). */
+ * u (D*N), T (N).  Host arrays are read as by lbm_set_state (in place when
+ * page-locked and device-addressable). */
 lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho,
                           const double* u, const double* T);
 
@@ -204,6 +209,21 @@ lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, doub
  * blocks in order), deterministic, equal to lbm_get_wall_loads up to
  * rounding. */
 lbm_status lbm_get_wall_loads_noalloc(lbm_handle* h, double force[3], double* heat, double* work);
+
+/* Wall loads of the last step (the sums of lbm_get_wall_loads) queued for
+ * the host without waiting: the reduction and a device-to-host copy of
+ * out[5] = (force[3], heat, work) are issued on the handle's stream and the
+ * call returns at once.  out is host memory that the caller keeps alive and
+ * does not read until lbm_sync (or another synchronizing call) returns;
+ * page-locked memory (cudaHostAlloc) keeps the copy asynchronous, pageable
+ * memory makes the copy wait for the stream.  Each call may name its own
+ * out (one per step, read after the run).  On a slab the body does not
+ * reach, out is zeroed at once.  LBM_ESTATE without a body. */
+lbm_status lbm_get_wall_loads_async(lbm_handle* h, double out[5]);
+
+/* Wait for the work queued on the handle's stream; returns a sticky error
+ * found by a previous step, else LBM_ECUDA on a device error. */
+lbm_status lbm_sync(lbm_handle* h);
 
 /* Wall diagnostics of the current (updated) flow field (Sec. 3.1-3.2; the
  * paper defines C_p and reads wall values with Eq. int1 at d = 2; the wall

@@ -733,16 +733,19 @@ lbm_status lbm_slab_points(const lbm_handle* h, int* n_points, int* global_index
 namespace {
 
 void drop_step_graph(lbm_handle* h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-  h->graph_f = nullptr;
+  for (StepGraph& g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = StepGraph{};
+  }
 }
 
-// Capture two steps (both buffer parities) of the current state as a graph;
-// the host-side buffer swaps of the two steps cancel, so the handle is back
-// at the captured parity afterwards.
-lbm_status capture_step_graph(lbm_handle* h) {
-  drop_step_graph(h);
+// Capture n_steps (1 or 2) steps from the current buffer parity as a graph.
+// Capturing runs the host side of the steps (the buffer swaps) but no
+// kernel: the handle is left at the parity after them, where a launch of
+// the graph brings the device as well.
+lbm_status capture_steps(lbm_handle* h, int n_steps, StepGraph& out) {
+  if (out.exec) cudaGraphExecDestroy(out.exec);
+  out = StepGraph{};
   // the legacy default stream cannot be captured: record on a private
   // stream (the graph keeps no stream) and launch on the handle's stream
   cudaStream_t run_st = h->st;
@@ -751,33 +754,48 @@ lbm_status capture_step_graph(lbm_handle* h) {
     return fail(h, LBM_ECUDA, "capture stream");
   }
   cudaStream_t st = run_st ? run_st : h->cap_st;
+  void* f0 = h->f;
+  const int cur0 = h->cur;
   const long long l0 = h->launches;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return fail(h, LBM_ECUDA, "graph capture begin");
   }
   h->st = st;
-  lbm_status s = h->ops->step(h);
-  if (!s) s = h->ops->step(h);
+  lbm_status s = LBM_OK;
+  for (int k = 0; k < n_steps && !s; ++k) s = h->ops->step(h);
   h->st = run_st;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &g);
-  h->graph_launches = h->launches - l0;
+  const long long nl = h->launches - l0;
   h->launches = l0;
+  auto rewind = [&] {
+    // nothing ran: put the host side back at the starting parity
+    if (h->f != f0) {
+      std::swap(h->f, h->f2);
+      std::swap(h->M, h->M2);
+    }
+    h->cur = cur0;
+  };
   if (s || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
+    rewind();
     return s ? s : fail(h, LBM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
-  const cudaError_t ei = cudaGraphInstantiate(&h->gexec, g, 0);
+  const cudaError_t ei = cudaGraphInstantiate(&out.exec, g, 0);
   cudaGraphDestroy(g);
   if (ei != cudaSuccess) {
-    h->gexec = nullptr;
+    out.exec = nullptr;
     cudaGetLastError();
+    rewind();
     return fail(h, LBM_ECUDA, "graph instantiate");
   }
-  h->graph_f = h->f;
-  h->graph_geom = h->geom_version;
+  out.f = f0;
+  out.cur = cur0;
+  out.geom = h->geom_version;
+  out.launches = nl;
+  rewind();
   return LBM_OK;
 }
 
@@ -787,19 +805,29 @@ lbm_status lbm_step(lbm_handle* h, int n_steps) {
   if (!h || n_steps < 0) return LBM_EINVAL;
   DeviceGuard dg(h->cfg.device);
   if (h->sticky) return (lbm_status)h->sticky;
-  // pairs of steps replay a captured graph (fewer host launches for small
-  // grids); profiling runs and odd remainders step eagerly
+  // after a first eager step (which sets the kernels' launch attributes)
+  // steps replay captured graphs, two at a time and one for an odd
+  // remainder (fewer host launches for small grids); profiling runs step
+  // eagerly
   const bool graphs = h->use_graph && !h->prof;
   int k = 0;
   while (k < n_steps) {
-    if (graphs && h->stepped && n_steps - k >= 2) {
-      if (!h->gexec || h->graph_f != h->f || h->graph_geom != h->geom_version) {
-        lbm_status s = capture_step_graph(h);
+    if (graphs && h->stepped) {
+      const int n = n_steps - k >= 2 ? 2 : 1;
+      StepGraph& g = h->graphs[n == 2 ? 0 : 1 + h->cur];
+      if (!g.exec || g.f != h->f || g.cur != h->cur || g.geom != h->geom_version) {
+        lbm_status s = capture_steps(h, n, g);
         if (s) return s;
       }
-      if (cudaGraphLaunch(h->gexec, h->st) != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch");
-      h->launches += h->graph_launches;
-      k += 2;
+      if (cudaGraphLaunch(g.exec, h->st) != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch");
+      h->launches += g.launches;
+      // the host side of the replayed steps: one buffer swap per step
+      if (n == 1) {
+        std::swap(h->f, h->f2);
+        std::swap(h->M, h->M2);
+        h->cur = 1 - h->cur;
+      }
+      k += n;
       continue;
     }
     lbm_status s = h->ops->step(h);
@@ -873,12 +901,37 @@ lbm_status lbm_get_state(lbm_handle* h, int dst_is_device, double* f, double* E)
   return s;
 }
 
+}  // extern "C"
+
+namespace {
+// the device address of page-locked host memory the device can read in
+// place (null for pageable memory): the upload kernels then read it over
+// the bus directly, with no device staging buffer and no separate copy
+const double* mapped_host(const double* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? (const double*)a.devicePointer : nullptr;
+}
+}  // namespace
+
+extern "C" {
+
 lbm_status lbm_set_state(lbm_handle* h, int src_is_device, const double* f, const double* E) {
   if (!h || !f || !E) return LBM_EINVAL;
   DeviceGuard dg(h->cfg.device);
   const long long N = h->g.N;
   if (src_is_device) {
     lbm_status s = h->ops->set_state(h, f, E);
+    if (s) return s;
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+  }
+  const double *mf = mapped_host(f), *mE = mapped_host(E);
+  if (mf && mE) {
+    lbm_status s = h->ops->set_state(h, mf, mE);
     if (s) return s;
     CK(cudaStreamSynchronize(h->st));
     return LBM_OK;
@@ -1002,6 +1055,13 @@ lbm_status lbm_set_fields(lbm_handle* h, int src_is_device, const double* rho, c
     CK(cudaStreamSynchronize(h->st));
     return LBM_OK;
   }
+  const double *mr = mapped_host(rho), *mu = mapped_host(u), *mT = mapped_host(T);
+  if (mr && mu && mT) {
+    lbm_status s = h->ops->set_fields(h, mr, mu, mT);
+    if (s) return s;
+    CK(cudaStreamSynchronize(h->st));
+    return LBM_OK;
+  }
   double* buf = nullptr;
   CK(cudaMalloc(&buf, N * 8 * (h->D + 2)));
   lbm_status s = LBM_OK;
@@ -1038,6 +1098,29 @@ lbm_status lbm_get_wall_loads(lbm_handle* h, double force[3], double* heat, doub
   if (heat) *heat = out[3];
   if (work) *work = out[4];
   return LBM_OK;
+}
+
+lbm_status lbm_get_wall_loads_async(lbm_handle* h, double out[5]) {
+  if (!h || !out) return LBM_EINVAL;
+  if (h->slab && !h->has_ib) {
+    for (int a = 0; a < 5; ++a) out[a] = 0.0;
+    return LBM_OK;
+  }
+  DeviceGuard dg(h->cfg.device);
+  if (!h->has_ib) return fail(h, LBM_ESTATE, "no immersed body");
+  lbm_status s = launch(h, kProfOther, [&] { k_wall_loads<<<1, 256, 0, h->st>>>(h->D, h->NL, h->G, h->W, h->owned, h->loads); });
+  if (s) return s;
+  // stream order keeps the next call's reduction behind this copy, so one
+  // device slot serves every call
+  CK(cudaMemcpyAsync(out, h->loads, 5 * 8, cudaMemcpyDeviceToHost, h->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_handle* h) {
+  if (!h) return LBM_EINVAL;
+  DeviceGuard dg(h->cfg.device);
+  CK(cudaStreamSynchronize(h->st));
+  return (lbm_status)h->sticky;
 }
 
 lbm_status lbm_get_wall_diagnostics(lbm_handle* h, double coeffs[4], double* per_point) {

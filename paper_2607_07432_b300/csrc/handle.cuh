@@ -17,6 +17,14 @@ constexpr int kProfClasses = 5;
 enum { kProfStep = 0, kProfIBForce = 1, kProfIBSpread = 2, kProfBC = 3, kProfOther = 4 };
 
 struct Ops;
+
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  void* f = nullptr;         // population buffer the captured steps start from
+  int cur = 0;               // auxiliary-buffer parity they start from
+  int geom = -1;             // geometry version they were captured with
+  long long launches = 0;    // kernels per replay
+};
 }  // namespace lbmib_host
 
 struct lbm_handle {
@@ -72,13 +80,11 @@ struct lbm_handle {
   int sticky = LBM_OK;
   int geom_version = 0;
   bool prof = false;
-  // two steps (both buffer parities) captured as a CUDA graph for
-  // lbm_step: valid while the buffers are at the captured parity and the
-  // geometry is unchanged
-  cudaGraphExec_t gexec = nullptr;
-  void* graph_f = nullptr;
-  int graph_geom = -1;
-  long long graph_launches = 0;
+  // steps captured as CUDA graphs for lbm_step: [0] two steps (both buffer
+  // parities), [1 + cur] one step from buffer parity cur; each is valid
+  // while the buffers are at its captured parity and the geometry is
+  // unchanged
+  lbmib_host::StepGraph graphs[3];
   int use_graph = 1;
   bool stepped = false;      // a first eager step has set the kernels' launch attributes
   cudaStream_t cap_st = nullptr;  // capture stream when the handle runs on the legacy default stream

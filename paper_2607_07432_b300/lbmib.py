@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16DEV, "bf16": BF16DEV}
 EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", "ib_set_geometry",
            "lbm_step", "lbm_check", "lbm_get_fields", "lbm_get_state", "lbm_set_state", "lbm_set_fields",
            "lbm_get_wall_loads", "lbm_get_wall_diagnostics", "lbm_get_constants", "ib_get_sizes", "ib_get_setup", "lbm_profile",
-           "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_batch_create",
+           "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_get_wall_loads_async", "lbm_sync", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_case", "lbm_batch_step",
            "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
            "lbm_batch_autotune", "lbm_save_state", "lbm_load_state", "lbm_create_slab", "lbm_slab_info",
@@ -310,6 +310,19 @@ class Solver:
         heat, work = ct.c_double(), ct.c_double()
         self._check(lib().lbm_get_wall_loads_noalloc(self.h, force, ct.byref(heat), ct.byref(work)))
         return dict(force=np.array(force[:self.D]), heat=heat.value, work=work.value)
+
+    def wall_loads_async(self, out):
+        """lbm_get_wall_loads_async: queue the last step's loads (force[3],
+        heat, work) into `out`, 5 float64 of host memory (page-locked keeps
+        the copy asynchronous), valid after sync()."""
+        n = out.numel() if hasattr(out, "numel") else out.size
+        if str(out.dtype).rsplit(".", 1)[-1] != "float64" or n < 5 or getattr(out, "is_cuda", False):
+            raise ValueError("wall_loads_async needs 5 contiguous float64 host values")
+        self._check(lib().lbm_get_wall_loads_async(self.h, _ptr(out)))
+
+    def sync(self):
+        """lbm_sync: wait for the work queued on the handle's stream."""
+        self._check(lib().lbm_sync(self.h))
 
     def constants(self):
         out = (ct.c_double * 8)()

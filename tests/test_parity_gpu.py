@@ -121,6 +121,7 @@ def test_boundaries_in_kernel_match_separate_kernel(lattice, precision, monkeypa
     """The fused kernel's in-place far-field faces (equilibrium on inlet and
     far-field faces, the outlet written as a copy by its inner neighbour)
     equal the separate boundary kernel bit for bit."""
+    import torch
     from paper_2607_07432_b300 import inputs, lbmib
     if lattice == "D2Q9":
         case = C.cylinder_c1()
@@ -172,9 +173,13 @@ def test_naca_downscale_fp32_against_oracle():
 
 @pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
 def test_step_graph_matches_eager_steps(lattice, monkeypatch):
-    """lbm_step replays pairs of steps from a captured CUDA graph; the state
-    equals eager stepping (LBMIB_NO_GRAPH=1) bit for bit, for even and odd
-    step counts and after the geometry is replaced."""
+    """lbm_step replays captured CUDA graphs (two steps, or one step from
+    either buffer parity); the state equals eager stepping (LBMIB_NO_GRAPH=1)
+    bit for bit, for even and odd step counts, single steps in a row and
+    after the geometry is replaced.  The loads queued by
+    lbm_get_wall_loads_async after each single step equal the synchronous
+    lbm_get_wall_loads of that step."""
+    import torch
     from paper_2607_07432_b300 import inputs, lbmib
     if lattice == "D2Q9":
         case = C.cylinder_c1()
@@ -191,6 +196,15 @@ def test_step_graph_matches_eager_steps(lattice, monkeypatch):
         s.set_geometry(case["geo"](th))
         s.step(7)
         s.step(4)
+        rows = torch.zeros((5, 5), dtype=torch.float64).pin_memory()
+        sync_loads = []
+        for k in range(5):
+            s.step(1)
+            s.wall_loads_async(rows[k])
+            wl = s.wall_loads()
+            sync_loads.append(list(wl["force"]) + [0.0] * (3 - s.D) + [wl["heat"], wl["work"]])
+        s.sync()
+        assert np.array_equal(rows.numpy(), np.array(sync_loads))
         s.set_geometry(case["geo"](th))
         s.step(5)
         s.check()
