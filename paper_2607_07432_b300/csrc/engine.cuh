@@ -43,10 +43,11 @@ struct Engine {
     if (L::D != 3 || h->zchunk_fixed) return;
     using Lay = FusedLayout<L, S, C, 0>;
     int sms = 0, occ = 0;
+    // both index widths have the same launch shape and shared memory
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->cfg.device) != cudaSuccess ||
-        cudaFuncSetAttribute(k_fused<L, S, C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<L, S, C, 0>, Lay::NT, Lay::bytes) !=
+        cudaFuncSetAttribute(k_fused<L, S, C, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Lay::bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<L, S, C, 0, false>, Lay::NT, Lay::bytes) !=
             cudaSuccess ||
         sms <= 0 || occ <= 0) {
       cudaGetLastError();
@@ -420,14 +421,17 @@ struct Engine {
   template <int HY>
   static void batch_launch(BatchPlan* b, int parity) {
     using Lay = FusedLayout<L, S, C, HY>;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_fused_batched<L, S, C, HY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Lay::bytes);
-      attr = true;
+    bool narrow = true;
+    for (lbm_handle* h : b->cases) narrow = narrow && narrow_index<L>(h->g.N);
+    if (narrow) {
+      smem_attr_once<k_fused_batched<L, S, C, HY, true>>((int)Lay::bytes);
+      k_fused_batched<L, S, C, HY, true><<<b->n_work, Lay::NT, Lay::bytes, b->st>>>(
+          (const CaseDesc<S, C>*)b->descs[parity], (const int4*)b->work);
+    } else {
+      smem_attr_once<k_fused_batched<L, S, C, HY, false>>((int)Lay::bytes);
+      k_fused_batched<L, S, C, HY, false><<<b->n_work, Lay::NT, Lay::bytes, b->st>>>(
+          (const CaseDesc<S, C>*)b->descs[parity], (const int4*)b->work);
     }
-    k_fused_batched<L, S, C, HY><<<b->n_work, Lay::NT, Lay::bytes, b->st>>>(
-        (const CaseDesc<S, C>*)b->descs[parity], (const int4*)b->work);
   }
   static lbm_status batch_fused(BatchPlan* b, int parity) {
     bool done = false;

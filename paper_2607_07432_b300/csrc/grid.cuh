@@ -80,9 +80,10 @@ __device__ __forceinline__ C pop_offset(int i, C thr) {
     return C(L::w(i));
   }
 }
-template <class L, class S, class C>
-__device__ __forceinline__ C load_pop(const S* f, int i, long long N, long long n, C thr) {
-  const C v = C(Store<S>::load(f[(long long)i * N + n]));
+// I: element index type (long long, or unsigned where Q N < 2^32)
+template <class L, class S, class C, class I = long long>
+__device__ __forceinline__ C load_pop(const S* f, int i, I N, I n, C thr) {
+  const C v = C(Store<S>::load(f[(I)i * N + n]));
   return Store<S>::dev ? v + pop_offset<L, S, C>(i, thr) : v;
 }
 // the value a population takes after a store and a reload
@@ -94,9 +95,9 @@ __device__ __forceinline__ C roundtrip_pop(int i, C v, C thr) {
   }
   return C(Store<S>::load(Store<S>::save(v)));
 }
-template <class L, class S, class C>
-__device__ __forceinline__ void store_pop(S* f, int i, long long N, long long n, C v, C thr) {
-  f[(long long)i * N + n] = Store<S>::save(Store<S>::dev ? v - pop_offset<L, S, C>(i, thr) : v);
+template <class L, class S, class C, class I = long long>
+__device__ __forceinline__ void store_pop(S* f, int i, I N, I n, C v, C thr) {
+  f[(I)i * N + n] = Store<S>::save(Store<S>::dev ? v - pop_offset<L, S, C>(i, thr) : v);
 }
 
 }  // namespace lbmib

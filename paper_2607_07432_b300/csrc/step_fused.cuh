@@ -3,12 +3,12 @@
 //
 // Each CTA owns a TX x TY column of the (x, y) plane and marches along z
 // (2.5D blocking).  Shared memory holds two rings of planes:
-//   * corrected macroscopic fields (rho, u, theta, rho E') of four planes
-//     z-1..z+2 with a halo of two nodes in x and y (MUSCL stencils and the
+//   * corrected macroscopic fields (rho, u, theta, rho E') of five planes
+//     z-1..z+3 with a halo of two nodes in x and y (MUSCL stencils and the
 //     velocity gradients of halo nodes), and
 //   * post-collision populations of three planes z-1..z+1 with a halo of one
 //     node (pull streaming and the face-crossing flux tables).
-// Per plane: load the macros of plane z+2, collide plane z+1 (halo included),
+// Per plane: load the macros of plane z+3, collide plane z+1 (halo included),
 // then stream, form the energy face fluxes and update rho E of plane z.
 //
 // Between steps the state carries, besides the populations, the predicted
@@ -68,10 +68,10 @@ struct FusedLayout {
   static constexpr int HX1 = TX + 2, HY1 = TY + 2, NH1 = HX1 * HY1;
   static constexpr int HX2 = TX + 4, HY2 = TY + 4, NH2 = HX2 * HY2;
   static constexpr int NT = NH1;
-  // macro planes: iteration z reads planes z-1..z+2; plane z-2 was last
-  // read (z face of plane z-1) before the barrier that opens iteration z,
-  // so its slot takes plane z+2
-  static constexpr int RM = D == 3 ? 4 : 1;
+  // macro planes: iteration z reads planes z-1..z+2 and fills plane z+3;
+  // plane z-2 was last read (z face of plane z-1) before the barrier that
+  // opens iteration z, so its slot takes plane z+3
+  static constexpr int RM = D == 3 ? 5 : 1;
   static constexpr int RF = D == 3 ? 3 : 1;   // f^col planes
   // corrected macros of a plane: rho, u (3 slots), theta, E' per node, kept
   // as vectors so that one shared-memory load reads several fields
@@ -96,7 +96,8 @@ __device__ __forceinline__ int find_row_dev(const int* cell_id, int n_rows, int 
 }
 
 // body of the fused step for the tile (bx, by) and z-chunk bz of one case
-template <class L, class S, class C, int HY>
+// NARROW: element offsets in 32 bits (the host takes it when Q N < 2^32)
+template <class L, class S, class C, int HY, bool NARROW>
 __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, int zchunk,
                                            int bx, int by, int bz) {
   using Lay = FusedLayout<L, S, C, HY>;
@@ -118,7 +119,9 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   const int nz = g.n[2];
   const int z0 = D == 3 ? bz * zchunk : 0;
   const int z1 = D == 3 ? min(nz, z0 + zchunk) : 1;
-  const long long N = g.N;
+  using Ix = std::conditional_t<NARROW, unsigned, long long>;
+  const Ix N = (Ix)g.N;
+  auto lin = [&](int x, int y, int z) { return (Ix)x + (Ix)g.n[0] * ((Ix)y + (Ix)g.n[1] * (Ix)z); };
   const bool interior = cx >= 1 && cx <= TX && cy >= 1 && cy <= TY && gx < g.n[0] && gy < g.n[1];
   const int wx = g.wrap(0, gx), wy = g.wrap(1, gy);
 
@@ -127,7 +130,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   auto fslot = [&](int z) { return D == 3 ? (int)((unsigned)(z + 4 * RF) % (unsigned)RF) : 0; };
   auto halo2_node = [&](int k, int gz) {
     const int kx = k % HX2, ky = k / HX2;
-    return g.lin(g.wrap(0, x0 + kx - 2), g.wrap(1, y0 + ky - 2), gz);
+    return lin(g.wrap(0, x0 + kx - 2), g.wrap(1, y0 + ky - 2), gz);
   };
 
   // corrected macros (rho, u, theta, rho E') of plane z over the halo-2 region,
@@ -138,12 +141,12 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     if constexpr (RPM) {
       const int gz = g.wrap(2, z);
       {
-        const long long n = halo2_node(t, gz);
+        const Ix n = halo2_node(t, gz);
 #pragma unroll
         for (int q = 0; q < D + 2; ++q) rm[0][RPM ? q : 0] = a.M_in[q * N + n];
       }
       if (t + NT < NH2) {
-        const long long n = halo2_node(t + NT, gz);
+        const Ix n = halo2_node(t + NT, gz);
 #pragma unroll
         for (int q = 0; q < D + 2; ++q) rm[RPM ? 1 : 0][RPM ? q : 0] = a.M_in[q * N + n];
       }
@@ -201,7 +204,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     const int gz = g.wrap(2, z);
     for (int k = t; k < NH2; k += NT) {
       C rho, jm[3], E;
-      const long long n = halo2_node(k, gz);
+      const Ix n = halo2_node(k, gz);
       rho = a.M_in[n];
 #pragma unroll
       for (int d = 0; d < D; ++d) jm[d] = a.M_in[(1 + d) * N + n];
@@ -251,9 +254,9 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   unsigned char rfl = 0;
   auto prefetch_regs = [&](int z, auto LO, auto HI, bool aux) {
     if constexpr (RP) {
-      const long long n = g.lin(wx, wy, g.wrap(2, z));
+      const Ix n = lin(wx, wy, g.wrap(2, z));
 #pragma unroll
-      for (int i = decltype(LO)::value; i < decltype(HI)::value; ++i) rf[i] = a.f_in[(long long)i * N + n];
+      for (int i = decltype(LO)::value; i < decltype(HI)::value; ++i) rf[i] = a.f_in[(Ix)i * N + n];
       if (aux) {
         rP = a.Pp[n];
 #pragma unroll
@@ -265,7 +268,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   // collision of this thread's node of plane z (halo-1 region, one node per thread)
   auto collide_plane = [&](int z, bool regs) {
     C* dst = fr + (size_t)fslot(z) * Q * NH1;
-    const long long n = g.lin(wx, wy, g.wrap(2, z));
+    const Ix n = lin(wx, wy, g.wrap(2, z));
     auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
     const Macro<C> m = macro_at(z, hx, hy);
     C du[3][3], aC[3][3];
@@ -286,7 +289,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       is_forced = rfl != 0;
     } else {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C>(a.f_in, i, N, n, C(g.thref));
+      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C, Ix>(a.f_in, i, N, n, C(g.thref));
       Pp = a.Pp[n];
 #pragma unroll
       for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
@@ -342,14 +345,14 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     return energy_face_flux<L, C, AX>(MAl, FCl, ph);
   };
 
-  // prologue: macros of planes z0-2..z0+1, collisions of planes z0-1 and z0
+  // prologue: macros of planes z0-2..z0+2, collisions of planes z0-1 and z0
   if constexpr (D == 3) {
-    for (int z = z0 - 2; z <= z0 + 1; ++z) load_macros(z);
+    for (int z = z0 - 2; z <= z0 + 2; ++z) load_macros(z);
     __syncthreads();
     collide_plane(z0 - 1, false);
     collide_plane(z0, false);
     prefetch_regs(z0 + 1, std::integral_constant<int, 0>{}, std::integral_constant<int, Q>{}, true);
-    prefetch_moments(z0 + 2);
+    prefetch_moments(z0 + 3);
     __syncthreads();
   }
   // the -z face of plane z is the +z face of plane z-1: carried in a register
@@ -375,19 +378,21 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         Fz_prev = Fz_pend;
       }
       if (xeq) E = a.E_inf;
-      a.M_out[(1 + D) * N + g.lin(gx, gy, zp)] = E;
+      a.M_out[(1 + D) * N + lin(gx, gy, zp)] = E;
     }
   };
   for (int z = z0; z < z1; ++z) {
     __syncthreads();
     if (z > z0) finish(z - 1);
     if constexpr (D == 3) {
-      load_macros(z + 2, true);
-      __syncthreads();
+      // the macros of plane z+3 go to a slot no one reads in this
+      // iteration; the collision of plane z+1 reads planes z..z+2, filled
+      // in earlier iterations: one barrier covers both
+      load_macros(z + 3, true);
       collide_plane(z + 1, true);
       __syncthreads();
       prefetch_regs(z + 2, std::integral_constant<int, 0>{}, std::integral_constant<int, QA>{}, false);
-      prefetch_moments(z + 3);
+      prefetch_moments(z + 4);
     } else {
       load_macros(0);
       __syncthreads();
@@ -395,14 +400,14 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       __syncthreads();
     }
     C rho = C(0), j[3] = {C(0), C(0), C(0)};
-    long long n = 0;
+    Ix n = 0;
     if (interior) {
-      n = g.lin(gx, gy, z);
+      n = lin(gx, gy, z);
       // Eq. LB pull streaming and the predicted moments of step n+1
       sfor<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const C v = fcol_at(i, z - L::c(i, 2), sx - L::c(i, 0), cy - L::c(i, 1));
-        store_pop<L, S, C>(a.f_out, i, N, n, v, C(g.thref));
+        store_pop<L, S, C, Ix>(a.f_out, i, N, n, v, C(g.thref));
         rho += v;
         sfor<0, D>([&](auto A) {
           constexpr int d = decltype(A)::value;
@@ -415,7 +420,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         j[0] = j[1] = j[2] = C(0);
         sfor<0, Q>([&](auto I) {
           constexpr int i = decltype(I)::value;
-          store_pop<L, S, C>(a.f_out, i, N, n, a.feq_inf[i], C(g.thref));
+          store_pop<L, S, C, Ix>(a.f_out, i, N, n, a.feq_inf[i], C(g.thref));
           const C v = roundtrip_pop<L, S, C>(i, a.feq_inf[i], C(g.thref));
           rho += v;
           sfor<0, D>([&](auto A) {
@@ -449,10 +454,10 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
   finish(z1 - 1);
 }
 
-template <class L, class S, class C, int HY>
+template <class L, class S, class C, int HY, bool NARROW>
 __global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S, C, HY>::min_blocks)
     k_fused(Grid g, FusedArgs<S, C> a, Phys<C> ph, int zchunk) {
-  fused_body<L, S, C, HY>(g, a, ph, zchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+  fused_body<L, S, C, HY, NARROW>(g, a, ph, zchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Several cases in one launch: work item k = (case, tile x, tile y, z-chunk)
@@ -465,26 +470,52 @@ struct CaseDesc {
   int zchunk;
 };
 
-template <class L, class S, class C, int HY>
+template <class L, class S, class C, int HY, bool NARROW>
 __global__ void __launch_bounds__(FusedLayout<L, S, C, HY>::NT, FusedLayout<L, S, C, HY>::min_blocks)
     k_fused_batched(const CaseDesc<S, C>* descs, const int4* work) {
   const int4 w = work[blockIdx.x];
   const CaseDesc<S, C>& d = descs[w.x];
-  fused_body<L, S, C, HY>(d.g, d.a, d.ph, d.zchunk, w.y, w.z, w.w);
+  fused_body<L, S, C, HY, NARROW>(d.g, d.a, d.ph, d.zchunk, w.y, w.z, w.w);
+}
+
+// 32-bit element offsets reach every array of a case with Q N < 2^32
+template <class L>
+inline bool narrow_index(long long N) {
+  return (long long)L::Q * N < (1LL << 32);
+}
+
+// the dynamic shared-memory limit of a kernel is a per-device attribute:
+// set it once on each device that launches the kernel (one flag array per
+// kernel: the template takes the kernel itself, not its type)
+template <auto kernel>
+inline void smem_attr_once(int bytes) {
+  constexpr int kMaxDev = 64;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return;
+  }
+  if (!done[dev]) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done[dev] = true;
+  }
 }
 
 template <class L, class S, class C, int HY>
 inline void launch_fused_tile(const Grid& g, const FusedArgs<S, C>& a, const Phys<C>& ph, cudaStream_t st,
                               int zchunk) {
   using Lay = FusedLayout<L, S, C, HY>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fused<L, S, C, HY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes);
-    attr = true;
-  }
   dim3 grid((g.n[0] + Lay::TX - 1) / Lay::TX, (g.n[1] + Lay::TY - 1) / Lay::TY,
             L::D == 3 ? (g.n[2] + zchunk - 1) / zchunk : 1);
-  k_fused<L, S, C, HY><<<grid, Lay::NT, Lay::bytes, st>>>(g, a, ph, zchunk);
+  if (narrow_index<L>(g.N)) {
+    smem_attr_once<k_fused<L, S, C, HY, true>>((int)Lay::bytes);
+    k_fused<L, S, C, HY, true><<<grid, Lay::NT, Lay::bytes, st>>>(g, a, ph, zchunk);
+  } else {
+    smem_attr_once<k_fused<L, S, C, HY, false>>((int)Lay::bytes);
+    k_fused<L, S, C, HY, false><<<grid, Lay::NT, Lay::bytes, st>>>(g, a, ph, zchunk);
+  }
 }
 
 // zchunk: planes per CTA along z (3D); tile_rows selects the halo-1 tile
