@@ -349,6 +349,88 @@ def steady_summary(cd, nu, every, window):
     return dict(Cd=cd_f, Nu=nu_f, steps_to_steady=steady)
 
 
+def run_rotsphere(args):
+    """Subsonic flow past a sphere turning about z (Sec. 3.9): Ma 0.3,
+    Re 300, adiabatic no-slip wall with targets omega x r, Omega* =
+    omega D / (2 u_inf) = 0.3 and 0.6, characteristic far field on the
+    outlet and the lateral faces, a uniform 10D x 6D x 6D grid (D = 32
+    cells by default).
+    Reports time-averaged C_d, C_l (along -y, the side where the surface
+    moves with the stream) and the Strouhal number of the lift."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    D = float(args.rot_d)
+    shape = (int(10 * D), int(6 * D), int(6 * D))
+    freq = int(round(np.sqrt(np.pi * D * D / 10.0)))
+    ctr = (2.5 * D, 3.0 * D, 3.0 * D)
+    steps, window, every = args.rot_steps, args.rot_window, 20
+    paper = {"0.3": {"Cd": 0.750, "Cl": 0.332, "St": 0.202}, "0.6": {"Cd": 0.862, "Cl": 0.512, "St": None}}
+    res = {}
+    for om in [float(v) for v in args.rot_omegas.split(",")]:
+        s = lbmib.Solver("D3Q19", "fp32", shape, mach=0.3, reynolds=300.0, ref_length=D,
+                         bc=[lbmib.BC_INLET] + [lbmib.BC_CHAR] * 5)
+        u_inf = s.constants()["u_mag"]
+        omega = 2.0 * om * u_inf / D
+        s.set_geometry(inputs.rotating(inputs.icosphere(ctr, D, freq, tbc=1, t_value=0.0), ctr, (0.0, 0.0, omega)))
+        if args.rot_noise > 0:
+            # seeded velocity noise on the uniform start, to seed the wake
+            # instability without waiting for round-off to grow
+            c = s.constants()
+            N = s.N
+            rng = np.random.default_rng(20260009)
+            u0 = args.rot_noise * u_inf * rng.standard_normal(3 * N)
+            u0[:N] += u_inf
+            s.set_fields(np.ones(N), u0, np.full(N, c["theta_inf"]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cd, cl, cz = [], [], []
+        for _ in range(steps // every):
+            s.step(every)
+            d = s.wall_diagnostics(per_point=False)
+            cd.append(d["Cd"])
+            cl.append(-d["Cl"])
+            cz.append(d["Cl2"])
+        s.check()
+        wall = time.perf_counter() - t0
+        s.close()
+        w = window // every
+        cd, cl, cz = np.array(cd), np.array(cl), np.array(cz)
+        # Strouhal number: the spectral peak of the lift fluctuation (both
+        # lateral components) over the averaging window
+        best = (0.0, None)
+        for sig in (cl[-w:], cz[-w:]):
+            x = (sig - sig.mean()) * np.hanning(w)
+            p = np.abs(np.fft.rfft(x)) ** 2
+            k = int(np.argmax(p[1:]) + 1)
+            # peak between bins: vertex of the parabola through the log
+            # power of the peak bin and its neighbours
+            kf = float(k)
+            if 1 <= k < len(p) - 1 and min(p[k - 1], p[k], p[k + 1]) > 0:
+                a, b, c = np.log(p[k - 1]), np.log(p[k]), np.log(p[k + 1])
+                if a - 2 * b + c < 0:
+                    kf = k + 0.5 * (a - c) / (a - 2 * b + c)
+            amp = float(np.std(sig))
+            if amp > best[0]:
+                best = (amp, kf / (w * every) * D / u_inf)
+        amp, st = best
+        # lift fluctuation per 4000-step block (growth or decay of shedding)
+        blk = 4000 // every
+        rms_blocks = [float(np.std(cl[i:i + blk])) for i in range(0, len(cl) - blk + 1, blk)]
+        res["%.1f" % om] = {"Cd": float(cd[-w:].mean()), "Cl": float(cl[-w:].mean()), "Cl_rms_blocks": rms_blocks,
+                            "Cl_rms": amp, "St": st if amp > 1e-3 else None, "omega": omega,
+                            "steps": steps, "window": window, "wall_s": wall,
+                            "paper_fodibm_r": paper.get("%.1f" % om)}
+    line = {"metric": "time-averaged C_d, C_l and lift Strouhal number of a rotating sphere (Ma 0.3, Re 300)",
+            "value": next(iter(res.values()))["Cd"], "unit": "C_d at Omega* %s" % next(iter(res)), "n_gpus": 1,
+            "higher_is_better": False,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "3D rotating sphere D3Q19 %dx%dx%d, D = %d (%d points), Omega* %s, "
+                                   "adiabatic wall, characteristic far field, start noise %g u_inf"
+                                   % (shape + (int(D), 10 * freq * freq + 2, args.rot_omegas, args.rot_noise))},
+            "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
     isothermal wall): C_d and Nu as running means, and the steps until the
@@ -664,7 +746,12 @@ def main():
     ap.add_argument("--no-other-forms", action="store_true",
                     help="skip the FP16 / BF16 storage and 64-case batch sub-records")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
-                                                                    "convergence"])
+                                                                    "convergence", "rotsphere"])
+    ap.add_argument("--rot-steps", type=int, default=36000)
+    ap.add_argument("--rot-window", type=int, default=16000)
+    ap.add_argument("--rot-d", type=int, default=48, help="sphere diameter in cells (grid 10D x 6D x 6D)")
+    ap.add_argument("--rot-noise", type=float, default=0.01)
+    ap.add_argument("--rot-omegas", default="0.3,0.6")
     ap.add_argument("--prec-steps-small", type=int, default=20000)
     ap.add_argument("--prec-steps-full", type=int, default=40000)
     ap.add_argument("--ws-cases", type=int, default=256)
@@ -686,6 +773,8 @@ def main():
         return run_precision(args)
     if args.workload == "convergence":
         return run_convergence(args)
+    if args.workload == "rotsphere":
+        return run_rotsphere(args)
     args.warmup = max(args.warmup, 3)
     import torch
     torch.cuda.set_device(local)

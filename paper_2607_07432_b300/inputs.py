@@ -116,6 +116,22 @@ def icosphere(center, diameter, frequency, tbc=0, t_value=1.0):
     return _as_geometry(X, U, shape, tbc, t_value)
 
 
+def rotating(geometry, center, omega):
+    """Velocity targets of a body turning rigidly about `center`:
+    u_target = omega x (X - center) (3D, omega a vector; 2D, omega the
+    scalar rate about z).  Returns the geometry with its targets replaced."""
+    X = geometry["X"]
+    r = X - np.asarray(center, dtype=np.float64)[None, : X.shape[1]]
+    if X.shape[1] == 2:
+        w = float(omega)
+        u = np.stack([-w * r[:, 1], w * r[:, 0]], axis=1)
+    else:
+        u = np.cross(np.broadcast_to(np.asarray(omega, dtype=np.float64), r.shape), r)
+    out = dict(geometry)
+    out["u_target"] = np.ascontiguousarray(u, dtype=np.float64)
+    return out
+
+
 def batch_cases(n_cases, seed, mach_range=(0.1, 0.8)):
     """Seeded uneven 2D case set (circles and ellipses, aspect 1-3, diameters
     10-60, 32-512 points, grids 256x128 .. 1024x512, Ma uniform in
