@@ -431,6 +431,126 @@ def run_rotsphere(args):
     print(json.dumps(line), flush=True)
 
 
+def run_refined(args):
+    """Two-level static refinement against uniform grids on the 2D cylinder
+    (Ma 0.2, Re 40, isothermal wall 1.1 T_inf): uniform D = 20 (200x100),
+    uniform D = 40 (400x200), and level 0 at D = 20 with the box of level-0
+    nodes [30, 150] x [20, 80] around the cylinder and its wake (by default)
+    refined to D = 40.  All
+    three at the theta_inf of the refined case; C_d from running means over
+    the last 2000 level-0 steps of `--ref-steps`."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    steps, every, window = args.ref_steps, 50, 2000
+    kw = dict(mach=0.2, reynolds=40.0, bc=[lbmib.BC_INLET, lbmib.BC_OUTLET, lbmib.BC_FARFIELD, lbmib.BC_FARFIELD])
+    out = {}
+
+    def history(step, diag, n_steps):
+        cd = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_steps // every):
+            step(every)
+            cd.append(diag()["Cd"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        cd = np.array(cd)
+        w = window // every
+        return float(cd[-w:].mean()), float(np.abs(cd[-w:] - cd[-w:].mean()).max()), wall
+
+    r = lbmib.Refined("D2Q9", "fp32", (200, 100), tuple(args.ref_lo), tuple(args.ref_hi), ref_length=20.0, **kw)
+    th = r.level0.constants()["theta_inf"]
+    G = r.G
+    lo = r.box_lo
+    r.level1.set_geometry(inputs.cylinder((G + 2 * (60.0 - lo[0]), G + 2 * (50.0 - lo[1])), 40.0, 126, tbc=0,
+                                          t_value=1.1 * th))
+    n1 = int(np.prod(r.level1.shape))
+    cd, spread, wall = history(r.step, lambda: r.level1.wall_diagnostics(per_point=False), steps)
+    r.check()
+    r.close()
+    out["refined"] = {"Cd": cd, "Cd_spread": spread, "wall_s": wall, "level0_nodes": 200 * 100,
+                      "level1_nodes": n1, "node_updates_per_level0_step": 200 * 100 + 2 * n1}
+    for name, shape, D, ctr, n_pts, scale in (("uniform D=20", (200, 100), 20.0, (60.0, 50.0), 63, 1),
+                                              ("uniform D=40", (400, 200), 40.0, (120.0, 100.0), 126, 2)):
+        s = lbmib.Solver("D2Q9", "fp32", shape, ref_length=D, theta_inf=th, **kw)
+        s.set_geometry(inputs.cylinder(ctr, D, n_pts, tbc=0, t_value=1.1 * th))
+        cd, spread, wall = history(lambda n: s.step(n * scale), lambda: s.wall_diagnostics(per_point=False), steps)
+        s.check()
+        s.close()
+        out[name] = {"Cd": cd, "Cd_spread": spread, "wall_s": wall,
+                     "node_updates_per_level0_step": int(np.prod(shape)) * scale}
+    line = {"metric": "C_d of the 2D cylinder on a two-level refined grid against uniform grids",
+            "value": out["refined"]["Cd"], "unit": "C_d", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "2D cylinder Ma 0.2, Re 40, 200x100 level 0 (D = 20) with [%d,%d]x[%d,%d] "
+                                   "refined by 2 (D = 40), against uniform D = 20 and D = 40"
+                                   % (args.ref_lo[0], args.ref_hi[0], args.ref_lo[1], args.ref_hi[1]),
+                       "theta_inf": th, "level0_steps": steps},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_refined_sphere(args):
+    """Two-level refinement on the 3D sphere (Ma 0.3, Re 300, isothermal wall
+    1.1 T_inf): level 0 192x96x96 at D = 16 with the box of level-0 nodes
+    [32, 112] x [24, 72] x [24, 72] around the sphere and its near wake
+    refined to D = 32, against the uniform D = 32 grid (384x192x192) and the
+    uniform D = 16 grid.  C_d and Nu as running means over the last 3000
+    level-0 steps of `--ref-steps`; cost as device time per level-0 step."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    steps, every, window = args.ref_steps, 100, 3000
+    kw = dict(mach=0.3, reynolds=300.0, bc=[lbmib.BC_INLET, lbmib.BC_OUTLET] + [lbmib.BC_FARFIELD] * 4)
+    lo, hi = (32, 24, 24), (112, 72, 72)
+    out = {}
+
+    def history(step, diag, n_steps):
+        cd, nu = [], []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(n_steps // every):
+            ev0.record()
+            step(every)
+            ev1.record()
+            d = diag()
+            ms += ev0.elapsed_time(ev1)
+            cd.append(d["Cd"])
+            nu.append(d["Nu"])
+        w = window // every
+        cd, nu = np.array(cd), np.array(nu)
+        return dict(Cd=float(cd[-w:].mean()), Nu=float(nu[-w:].mean()),
+                    Cd_spread=float(np.abs(cd[-w:] - cd[-w:].mean()).max()), ms_per_level0_step=ms / n_steps)
+
+    r = lbmib.Refined("D3Q19", "fp32", (192, 96, 96), lo, hi, ref_length=16.0, **kw)
+    th = r.level0.constants()["theta_inf"]
+    G = r.G
+    ctr1 = tuple(G + 2.0 * (c - l) for c, l in zip((48.0, 48.0, 48.0), lo))
+    r.level1.set_geometry(inputs.icosphere(ctr1, 32.0, 18, tbc=0, t_value=1.1 * th))
+    n1 = int(np.prod(r.level1.shape))
+    out["refined"] = history(r.step, lambda: r.level1.wall_diagnostics(per_point=False), steps)
+    out["refined"].update(level0_nodes=192 * 96 * 96, level1_nodes=n1)
+    r.check()
+    r.close()
+    for name, shape, D, freq, scale in (("uniform D=32", (384, 192, 192), 32.0, 18, 2),
+                                        ("uniform D=16", (192, 96, 96), 16.0, 9, 1)):
+        s = lbmib.Solver("D3Q19", "fp32", shape, ref_length=D, theta_inf=th, **kw)
+        s.set_geometry(inputs.icosphere((3.0 * D, 3.0 * D, 3.0 * D), D, freq, tbc=0, t_value=1.1 * th))
+        out[name] = history(lambda n: s.step(n * scale), lambda: s.wall_diagnostics(per_point=False), steps)
+        out[name]["nodes"] = int(np.prod(shape))
+        s.check()
+        s.close()
+    ref = out["uniform D=32"]
+    line = {"metric": "C_d and Nu of the 3D sphere on a two-level refined grid against uniform grids, and cost",
+            "value": out["refined"]["Cd"], "unit": "C_d", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "3D sphere Ma 0.3, Re 300, 192x96x96 level 0 (D = 16) with [32,112]x[24,72]x[24,72] "
+                                   "refined by 2 (D = 32), against uniform D = 32 and D = 16",
+                       "theta_inf": th, "level0_steps": steps},
+            "speedup_vs_uniform_fine": ref["ms_per_level0_step"] / out["refined"]["ms_per_level0_step"],
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
     isothermal wall): C_d and Nu as running means, and the steps until the
@@ -746,7 +866,11 @@ def main():
     ap.add_argument("--no-other-forms", action="store_true",
                     help="skip the FP16 / BF16 storage and 64-case batch sub-records")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
-                                                                    "convergence", "rotsphere"])
+                                                                    "convergence", "rotsphere", "refined",
+                                                                    "refined_sphere"])
+    ap.add_argument("--ref-steps", type=int, default=40000)
+    ap.add_argument("--ref-lo", type=int, nargs=2, default=[30, 20])
+    ap.add_argument("--ref-hi", type=int, nargs=2, default=[150, 80])
     ap.add_argument("--rot-steps", type=int, default=36000)
     ap.add_argument("--rot-window", type=int, default=16000)
     ap.add_argument("--rot-d", type=int, default=48, help="sphere diameter in cells (grid 10D x 6D x 6D)")
@@ -775,6 +899,10 @@ def main():
         return run_convergence(args)
     if args.workload == "rotsphere":
         return run_rotsphere(args)
+    if args.workload == "refined":
+        return run_refined(args)
+    if args.workload == "refined_sphere":
+        return run_refined_sphere(args)
     args.warmup = max(args.warmup, 3)
     import torch
     torch.cuda.set_device(local)

@@ -331,6 +331,48 @@ lbm_status lbm_slab_plan(int nz, int n_slabs, int halo, int* out);
 lbm_status lbm_slab_keep(const lbm_config* cfg, int z0, int z1, int halo, int n_points, const double* X,
                          const double* normals, int* keep, int* owned);
 
+/* ---- two-level static refinement (the locally refined meshes of Secs.
+ * 3.2-3.9; the paper gives no refinement algorithm, so what follows is this
+ * library's reading) ---------------------------------------------------
+ * Level 0 covers the domain described by cfg (its grid, boundary
+ * conditions, Reynolds number on ref_length level-0 cells).  Level 1
+ * refines the box of level-0 nodes [box_lo, box_hi] (inclusive) by 2: its
+ * node k along an axis sits at level-0 coordinate box_lo + (k - G)/2 with G
+ * = 4 ghost nodes beyond the box on every side (no boundary condition
+ * there).  Acoustic scaling: level 1 steps twice per level-0 step with the
+ * same lattice velocities and theta and twice the lattice viscosity and
+ * conductivity (Reynolds number on 2 ref_length cells); theta_inf <= 0
+ * applies the theta rule to level 1, and level 0 takes the same value.
+ * Per level-0 step: the ghost nodes take the nested mean (x, then y, then
+ * z) of the level-0 nodes around them of the predicted moments and of
+ * f-bar_i - f^eq_i, rebuilt as f^eq + s01 (f-bar - f^eq), s01 = tau-bar_1 /
+ * (2 tau-bar_0), tau-bar = mu / (rho c_s^2) + 1/2; the first level-1 step
+ * sees level 0 at n, the second the mean of n and n+1; the previous-step
+ * rho(1-theta) comes from level 0 (mean of n-1 and n, then n) and the a^F
+ * deviator halved.  Level-0 nodes R = 2 or more nodes inside the box then
+ * take the coinciding level-1 node's state (f^eq + s10 (f-bar - f^eq), s10
+ * = 2 tau-bar_0 / tau-bar_1, rho E, its previous-step values, the deviator
+ * doubled).  The energy equation couples through the same values (no
+ * refluxing).  A body goes on level 1 (ib_set_geometry on its handle, in
+ * level-1 node coordinates) and must stay clear of its ghost nodes. */
+typedef struct lbm_refined lbm_refined;
+/* LBM_EINVAL unless every box face lies at least 3 level-0 nodes inside
+ * level 0 and the box spans more than 2 R nodes per axis. */
+lbm_status lbm_refined_create(const lbm_config* cfg, const int box_lo[3], const int box_hi[3],
+                              lbm_refined** out);
+void lbm_refined_destroy(lbm_refined* r);
+const char* lbm_refined_last_error(const lbm_refined* r);
+/* The handle of level 0 or 1 (owned by r: fields, state, geometry,
+ * diagnostics; step the pair with lbm_refined_step only).  Level 1's ghost
+ * nodes hold scratch values between steps (each transfer overwrites them);
+ * level-0 nodes inside the box hold the restricted level-1 solution. */
+lbm_status lbm_refined_level(lbm_refined* r, int level, lbm_handle** h);
+/* info[0] = G, [1] = R, [2..4] level-1 grid, [5..7] box_lo. */
+lbm_status lbm_refined_info(const lbm_refined* r, int info[8]);
+/* Advance n_steps level-0 steps (2 n_steps level-1 steps), asynchronously
+ * on the configured stream. */
+lbm_status lbm_refined_step(lbm_refined* r, int n_steps);
+
 /* ---- several cases advanced together ------------------------------------
  * A batch owns n cases (same lattice, precision and device; grids, bodies
  * and flow parameters may differ) on one stream of its own.  A batched step

@@ -110,7 +110,7 @@ struct SlabSpec {
   int z0, z1, ghost_lo, ghost_hi, nz_global;
 };
 
-lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle** out) {
+lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle** out, bool ghost_faces = false) {
   if (!cfg || !out || cfg->struct_size != sizeof(lbm_config)) return LBM_EINVAL;
   *out = nullptr;
   const int D = cfg->lattice == LBM_D3Q19 ? 3 : 2;
@@ -123,7 +123,8 @@ lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle**
   bool has_char = false, has_outlet = false;
   for (int f = 0; f < 2 * D; ++f) {
     const int t = cfg->bc[f];
-    if ((t < LBM_BC_PERIODIC || t > LBM_BC_FARFIELD) && t != LBM_BC_CHARACTERISTIC && !(slab && t == kBCGhostFace))
+    if ((t < LBM_BC_PERIODIC || t > LBM_BC_FARFIELD) && t != LBM_BC_CHARACTERISTIC &&
+        !((slab || ghost_faces) && t == kBCGhostFace))
       return LBM_EINVAL;
     has_char = has_char || t == LBM_BC_CHARACTERISTIC;
     has_outlet = has_outlet || t == LBM_BC_OUTLET;
@@ -232,6 +233,14 @@ lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle**
 extern "C" {
 
 lbm_status lbm_create(const lbm_config* cfg, lbm_handle** out) { return create_impl(cfg, nullptr, out); }
+
+}  // extern "C"
+
+lbm_status lbmib_host::create_patch_handle(const lbm_config* cfg, lbm_handle** out) {
+  return create_impl(cfg, nullptr, out, true);
+}
+
+extern "C" {
 
 lbm_status lbm_create_slab(const lbm_config* cfg, int z0, int z1, int halo, lbm_handle** out) {
   if (!cfg || !out || cfg->struct_size != sizeof(lbm_config)) return LBM_EINVAL;

@@ -10,6 +10,7 @@
 #include "handle.cuh"
 #include "ib.cuh"
 #include "physics.cuh"
+#include "refine.cuh"
 #include "state.cuh"
 #include "step_fused.cuh"
 
@@ -492,10 +493,46 @@ struct Engine {
                                                               bad);
     });
   }
+  // two-level refinement transfers (kernels in refine.cuh)
+  // out: the ghost state (Q + 1 values per ghost node) followed by the
+  // shell scratch (Q + D + 2 values per shell node)
+  static lbm_status refine_ghost_state(lbm_handle* h0, const RefineDev& r, void* out) {
+    C* g = (C*)out;
+    C* B = g + (size_t)(L::Q + 1) * r.n_ghost;
+    lbm_status s = launch(h0, kProfOther, [&] {
+      k_refine_shell<L, S, C><<<nblk(r.n_shell, 128), 128, 0, h0->st>>>(r, (const S*)h0->f, (const C*)h0->M, B);
+    });
+    if (s) return s;
+    return launch(h0, kProfOther, [&] {
+      k_refine_ghost_state<L, S, C><<<nblk(r.n_ghost, 128), 128, 0, h0->st>>>(r, B, g);
+    });
+  }
+  // level 0 has stepped to n+1: its P / A [cur] hold time n, [1 - cur] time
+  // n-1; level 1's [cur] buffers are the previous-step values its next
+  // step reads
+  static lbm_status refine_fill(lbm_handle* h0, lbm_handle* h1, const RefineDev& r, const void* Ga,
+                                const void* Gb) {
+    return launch(h1, kProfOther, [&] {
+      k_refine_fill<L, S, C><<<nblk(r.n_ghost, 128), 128, 0, h1->st>>>(
+          r, (S*)h1->f, (C*)h1->M, (C*)h1->P[h1->cur], (C*)h1->A[h1->cur], (const C*)Ga, (const C*)Gb,
+          (const C*)h0->P[1 - h0->cur], (const C*)h0->P[h0->cur], (const C*)h0->A[1 - h0->cur],
+          (const C*)h0->A[h0->cur]);
+    });
+  }
+  // after level 1's second step its [1 - cur] buffers hold level-1 time n
+  static lbm_status refine_restrict(lbm_handle* h0, lbm_handle* h1, const RefineDev& r) {
+    const long long nr = (long long)r.rn[0] * r.rn[1] * (L::D == 3 ? r.rn[2] : 1);
+    return launch(h0, kProfOther, [&] {
+      k_refine_restrict<L, S, C><<<nblk(nr, 128), 128, 0, h0->st>>>(
+          r, (S*)h0->f, (C*)h0->M, (C*)h0->P[h0->cur], (C*)h0->A[h0->cur], (const S*)h1->f, (const C*)h1->M,
+          (const C*)h1->P[1 - h1->cur], (const C*)h1->A[1 - h1->cur]);
+    });
+  }
   static const Ops* ops() {
     static const Ops o = {&init,        &step,        &fields,    &get_state, &set_state,
                           &set_fields_api, &health, &batch_build, &batch_fused, &batch_aux,
-                          &ib_part,     &bc_part,     &wall_diag};
+                          &ib_part,     &bc_part,     &wall_diag, &refine_ghost_state, &refine_fill,
+                          &refine_restrict};
     return &o;
   }
 };

@@ -36,6 +36,21 @@ struct Grid {
   }
 };
 
+// Transfers between the two levels of a refined case (lbm_refined_*):
+// level-1 node k along an axis sits at level-0 coordinate lo + (k - G)/2
+struct RefineDev {
+  Grid g0, g1;            // level-0 and level-1 grids
+  int lo[3];              // level-0 node of level-1 node G (per axis)
+  int G;                  // ghost width (level-1 nodes)
+  int n_ghost;
+  const int4* ghost;      // level-1 coordinates of the ghost nodes
+  int n_shell;            // level-0 nodes the ghost nodes read
+  const long long* shell; // their level-0 indices
+  const int* corners;     // per ghost node 2^D shell indices (corner sx + 2 sy + 4 sz; -1: not read)
+  int rlo[3], rn[3];      // restricted level-0 nodes: first node and count per axis
+  double mu0, mu1, Cv;
+};
+
 // Population storage.  FP64 stores f-bar as is; the other formats store
 // the deviation f-bar_i - w_i (reference density 1), converted to the
 // compute type on load.

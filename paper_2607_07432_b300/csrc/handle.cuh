@@ -162,7 +162,18 @@ struct Ops {
   lbm_status (*bc_part)(lbm_handle*);
   // wall diagnostics of the current state into a device array (NL rows)
   lbm_status (*wall_diag)(lbm_handle*, double* out, int* err);
+  // two-level refinement transfers (level-0 handle, level-1 handle):
+  // ghost state of level 1 from level 0 into a device array, its write into
+  // level 1 (Gb null: the first level-1 step), restriction into level 0
+  lbm_status (*refine_ghost_state)(lbm_handle* h0, const lbmib::RefineDev&, void* out);
+  lbm_status (*refine_fill)(lbm_handle* h0, lbm_handle* h1, const lbmib::RefineDev&, const void* Ga,
+                            const void* Gb);
+  lbm_status (*refine_restrict)(lbm_handle* h0, lbm_handle* h1, const lbmib::RefineDev&);
 };
+
+// a handle whose every face is a ghost face (no boundary condition, edge
+// reads clamped): the level-1 box of a refined case
+lbm_status create_patch_handle(const lbm_config* cfg, lbm_handle** out);
 
 // A set of cases advanced together (lbm_batch_*): one fused launch covers
 // every case; the per-case IB and boundary kernels surround it.

@@ -32,7 +32,8 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", 
            "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
            "lbm_batch_autotune", "lbm_save_state", "lbm_load_state", "lbm_create_slab", "lbm_slab_info",
            "lbm_slab_exchange_bytes", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_points",
-           "lbm_slab_plan", "lbm_slab_keep"]
+           "lbm_slab_plan", "lbm_slab_keep", "lbm_refined_create", "lbm_refined_destroy",
+           "lbm_refined_last_error", "lbm_refined_level", "lbm_refined_info", "lbm_refined_step"]
 
 
 class Config(ct.Structure):
@@ -66,6 +67,12 @@ def load():
     lib.lbm_slab_exchange_bytes.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(ct.c_size_t)]
     lib.lbm_save_state.argtypes = [ct.c_void_p, ct.c_char_p]
     lib.lbm_load_state.argtypes = [ct.c_void_p, ct.c_char_p]
+    lib.lbm_refined_last_error.restype = ct.c_char_p
+    lib.lbm_refined_last_error.argtypes = [ct.c_void_p]
+    lib.lbm_refined_destroy.argtypes = [ct.c_void_p]
+    lib.lbm_refined_step.argtypes = [ct.c_void_p, ct.c_int]
+    lib.lbm_refined_create.argtypes = [ct.POINTER(Config), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                       ct.POINTER(ct.c_void_p)]
     lib.lbm_batch_last_error.restype = ct.c_char_p
     lib.lbm_batch_last_error.argtypes = [ct.c_void_p]
     lib.lbm_batch_destroy.argtypes = [ct.c_void_p]
@@ -104,6 +111,28 @@ def _ptr(a):
     return a.ctypes.data_as(ct.c_void_p)
 
 
+def _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamma, theta_inf, inflow_dir, sigma,
+            d_n, method, bc, tau_mode, use_ac, device, stream):
+    cfg = Config()
+    lib().lbm_config_default(ct.byref(cfg))
+    D = 2 if lattice in ("D2Q9", D2Q9) else 3
+    cfg.lattice = D2Q9 if D == 2 else D3Q19
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.nx, cfg.ny = int(shape[0]), int(shape[1])
+    cfg.nz = int(shape[2]) if D == 3 else 1
+    cfg.mach, cfg.reynolds, cfg.ref_length = mach, reynolds, ref_length
+    cfg.prandtl, cfg.gamma, cfg.theta_inf = prandtl, gamma, theta_inf
+    for a in range(3):
+        cfg.inflow_dir[a] = float(inflow_dir[a]) if a < len(inflow_dir) else 0.0
+    cfg.sigma_hrr, cfg.d_n, cfg.method = sigma, d_n, int(method)
+    bc = list(bc) if bc is not None else [BC_PERIODIC] * (2 * D)
+    for k in range(6):
+        cfg.bc[k] = int(bc[k]) if k < len(bc) else BC_PERIODIC
+    cfg.tau_mode, cfg.use_ac, cfg.device = int(tau_mode), int(use_ac), int(device)
+    cfg.stream = ct.c_void_p(stream) if stream else None
+    return cfg
+
+
 class Solver:
     """One case on one GPU (lbm_create ... lbm_destroy)."""
 
@@ -114,24 +143,10 @@ class Solver:
         """slab = (z0, z1, halo): a z slab of the case (lbm_create_slab); shape
         is then the global grid."""
         L = lib()
-        cfg = Config()
-        L.lbm_config_default(ct.byref(cfg))
+        cfg = _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamma, theta_inf,
+                      inflow_dir, sigma, d_n, method, bc, tau_mode, use_ac, device, stream)
         self.D = 2 if lattice in ("D2Q9", D2Q9) else 3
         self.Q = 9 if self.D == 2 else 19
-        cfg.lattice = D2Q9 if self.D == 2 else D3Q19
-        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        cfg.nx, cfg.ny = int(shape[0]), int(shape[1])
-        cfg.nz = int(shape[2]) if self.D == 3 else 1
-        cfg.mach, cfg.reynolds, cfg.ref_length = mach, reynolds, ref_length
-        cfg.prandtl, cfg.gamma, cfg.theta_inf = prandtl, gamma, theta_inf
-        for a in range(3):
-            cfg.inflow_dir[a] = float(inflow_dir[a]) if a < len(inflow_dir) else 0.0
-        cfg.sigma_hrr, cfg.d_n, cfg.method = sigma, d_n, int(method)
-        bc = list(bc) if bc is not None else [BC_PERIODIC] * (2 * self.D)
-        for k in range(6):
-            cfg.bc[k] = int(bc[k]) if k < len(bc) else BC_PERIODIC
-        cfg.tau_mode, cfg.use_ac, cfg.device = int(tau_mode), int(use_ac), int(device)
-        cfg.stream = ct.c_void_p(stream) if stream else None
         self.cfg = cfg
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -374,6 +389,71 @@ class CaseView(Solver):
 
     def close(self):
         self.h = None
+
+
+class Refined:
+    """Two-level static refinement (lbm_refined_*): level 0 over `shape`
+    (Reynolds number on ref_length level-0 cells) and level 1, the box of
+    level-0 nodes [box_lo, box_hi] refined by 2 with G ghost nodes.  The
+    levels are CaseView objects (`level0`, `level1`); a body goes on level 1
+    in its node coordinates (`to_level1`)."""
+
+    def __init__(self, lattice, precision, shape, box_lo, box_hi, mach=0.1, reynolds=100.0, ref_length=10.0,
+                 prandtl=0.71, gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98, d_n=1.5,
+                 method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=2, device=0, stream=None):
+        L = lib()
+        self.cfg = _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamma, theta_inf,
+                           inflow_dir, sigma, d_n, method, bc, tau_mode, use_ac, device, stream)
+        D = 2 if lattice in ("D2Q9", D2Q9) else 3
+        lo = (ct.c_int * 3)(*[int(v) for v in (list(box_lo) + [0, 0])[:3]])
+        hi = (ct.c_int * 3)(*[int(v) for v in (list(box_hi) + [0, 0])[:3]])
+        r = ct.c_void_p()
+        st = L.lbm_refined_create(ct.byref(self.cfg), lo, hi, ct.byref(r))
+        if st:
+            raise LBMError(st, "lbm_refined_create failed")
+        self.r = r
+        info = (ct.c_int * 8)()
+        self._check(L.lbm_refined_info(r, info))
+        self.G, self.R = info[0], info[1]
+        self.box_lo = tuple(info[5:5 + D])
+        shape1 = tuple(info[2:2 + D])
+        hs = []
+        for lev in (0, 1):
+            h = ct.c_void_p()
+            self._check(L.lbm_refined_level(r, lev, ct.byref(h)))
+            hs.append(h)
+        self.level0 = CaseView(hs[0], lattice, tuple(int(v) for v in shape[:D]))
+        self.level1 = CaseView(hs[1], lattice, shape1)
+
+    def _check(self, st):
+        if st:
+            raise LBMError(st, lib().lbm_refined_last_error(self.r).decode() if self.r else "")
+
+    def to_level1(self, X):
+        """Level-0 coordinates (N x D) to level-1 node coordinates."""
+        X = np.asarray(X, dtype=np.float64)
+        lo = np.asarray(self.box_lo, dtype=np.float64)
+        return self.G + 2.0 * (X - lo[None, :X.shape[1]])
+
+    def step(self, n=1):
+        self._check(lib().lbm_refined_step(self.r, int(n)))
+
+    def check(self):
+        self.level0.check()
+        self.level1.check()
+
+    def close(self):
+        if self.r:
+            lib().lbm_refined_destroy(self.r)
+            self.r = None
+            self.level0.close()
+            self.level1.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
