@@ -72,6 +72,7 @@ struct nop_net {
   double* fields = nullptr;  // rho, u (2 planes), T for nop_infer_into
   long long adam_t = 0;
   bool prepared = false;
+  int* tc_status = nullptr;  // set by a tensor-core convolution whose MMA wait timed out
   std::vector<void*> allocs;
 };
 
@@ -168,6 +169,58 @@ lbm_status launch_check(nop_net* net, const char* what) {
   return LBM_OK;
 }
 
+// after the stream has been synchronized: launch errors, then the
+// tensor-core convolutions' wait status
+lbm_status finish(nop_net* net, const char* what) {
+  lbm_status s = launch_check(net, what);
+  if (s) return s;
+  int st = 0;
+  if (cudaMemcpy(&st, net->tc_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(net, LBM_ECUDA, std::string(what) + ": status read");
+  }
+  if (st) {
+    cudaMemset(net->tc_status, 0, sizeof(int));
+    return fail(net, LBM_ETIMEOUT, std::string(what) + ": a tensor-core convolution timed out waiting for its MMAs");
+  }
+  return LBM_OK;
+}
+
+// the tensor-core convolution with chunks of 8 NG input channels; its
+// dynamic shared-memory limit (for the largest Cout, 128) is set once per
+// device
+template <int NG, bool DB>
+void conv_tc(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float* bias, float* Y, int B, int H, int W,
+             int Cin, int Cout, int relu, int accumulate) {
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    cudaFuncSetAttribute(k_conv3x3_tc<NG, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv_tc_smem(NG, 128, DB));
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  const unsigned grid = (unsigned)((long long)B * H * (W / kTcM));
+  k_conv3x3_tc<NG, DB><<<grid, 128, conv_tc_smem(NG, Cout, DB), net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout,
+                                                                           relu, accumulate, net->tc_status);
+}
+
+// one 3x3 convolution (see k_conv3x3): on the tcgen05 tensor cores when a
+// CTA's 128 pixels fit an image row and the output channels one
+// accumulator (W % 128 == 0, Cout <= 128), else on the mma.sync path
+void conv(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float* bias, float* Y, int B, int H, int W,
+          int Cin, int Cout, int relu, int accumulate) {
+  if (W % kTcM == 0 && Cout <= 128) {
+    if (Cin % 32 == 0)
+      conv_tc<4, false>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+    else
+      conv_tc<2, false>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+    return;
+  }
+  dim3 grid((unsigned)((long long)B * H * ((W + kRowPx - 1) / kRowPx)), (unsigned)((Cout + kTN - 1) / kTN));
+  k_conv3x3<<<grid, 128, 0, net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+}
+
 // BF16 copies of the master weights (after every change of the masters)
 lbm_status prepare(nop_net* net) {
   if (net->prepared) return LBM_OK;
@@ -192,8 +245,7 @@ lbm_status forward(nop_net* net, int B) {
     switch (op.kind) {
       case kConv: {
         const Layer& l = net->L[op.layer];
-        dim3 grid((unsigned)((long long)B * Ho * ((Wo + kRowPx - 1) / kRowPx)), (unsigned)((l.coutp + kTN - 1) / kTN));
-        k_conv3x3<<<grid, 128, 0, net->st>>>(ti.act, l.Wt, l.bias, to.act, B, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
+        conv(net, ti.act, l.Wt, l.bias, to.act, B, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
         break;
       }
       case kPool:
@@ -239,8 +291,7 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
         k_bias_partial<<<nbias, l.coutp, 0, net->st>>>(to.grad, net->part, P, l.coutp);
         k_sum_chunks<<<blocks(l.coutp), 256, 0, net->st>>>(net->part, nbias, l.coutp, l.db);
         if (op.in != net->x_t || want_dx) {
-          dim3 grid((unsigned)((long long)B * Hi * ((Wi + kRowPx - 1) / kRowPx)), (unsigned)((l.cinp + kTN - 1) / kTN));
-          k_conv3x3<<<grid, 128, 0, net->st>>>(to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
+          conv(net, to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
         }
         break;
       }
@@ -353,6 +404,8 @@ lbm_status nop_create(const nop_config* cfg, nop_net** out) {
   if (!s) s = dalloc(net, &net->loss_part, net->loss_blocks);
   if (!s) s = dalloc(net, &net->loss_dev, 1);
   if (!s) s = dalloc(net, &net->fields, 4 * (long long)cfg->height * cfg->width);
+  if (!s) s = dalloc(net, &net->tc_status, 1);
+  if (!s && cudaMemsetAsync(net->tc_status, 0, sizeof(int), net->st) != cudaSuccess) s = LBM_ECUDA;
   if (!s && (cudaMemsetAsync(net->master, 0, np * sizeof(float), net->st) != cudaSuccess ||
              cudaMemsetAsync(net->adam_m, 0, np * sizeof(float), net->st) != cudaSuccess ||
              cudaMemsetAsync(net->adam_v, 0, np * sizeof(float), net->st) != cudaSuccess ||
@@ -429,7 +482,7 @@ lbm_status nop_forward(nop_net* net, int batch, const float* x, float* y) {
   const long long P = pixels(net, 0, batch);
   k_crop_channels<<<blocks(P * net->cfg.out_channels), 256, 0, net->st>>>(t.act, y, P, t.C, net->cfg.out_channels);
   NCK(cudaStreamSynchronize(net->st));
-  return launch_check(net, "nop_forward");
+  return finish(net, "nop_forward");
 }
 
 lbm_status nop_backward(nop_net* net, int batch, const float* x, const float* dy, float* dparams, float* dx) {
@@ -451,7 +504,7 @@ lbm_status nop_backward(nop_net* net, int batch, const float* x, const float* dy
                                                                           net->cfg.in_channels);
   }
   NCK(cudaStreamSynchronize(net->st));
-  return launch_check(net, "nop_backward");
+  return finish(net, "nop_backward");
 }
 
 lbm_status nop_train_step(nop_net* net, int batch, const float* x, const float* target, float lr, double* loss) {
@@ -479,7 +532,7 @@ lbm_status nop_train_step(nop_net* net, int batch, const float* x, const float* 
   NCK(cudaMemcpyAsync(&l, net->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, net->st));
   NCK(cudaStreamSynchronize(net->st));
   if (loss) *loss = l;
-  return launch_check(net, "nop_train_step");
+  return finish(net, "nop_train_step");
 }
 
 lbm_status nop_infer_into(nop_net* net, lbm_handle* h, const float* x, const double off[4], const double scale[4]) {
@@ -497,7 +550,7 @@ lbm_status nop_infer_into(nop_net* net, lbm_handle* h, const float* x, const dou
   k_to_fields<<<blocks(N), 256, 0, net->st>>>(net->T[net->y_t].act, net->T[net->y_t].C, N, off[0], off[1], off[2],
                                               off[3], scale[0], scale[1], scale[2], scale[3], rho, u, T);
   NCK(cudaStreamSynchronize(net->st));
-  if ((s = launch_check(net, "k_to_fields"))) return s;
+  if ((s = finish(net, "k_to_fields"))) return s;
   s = lbm_set_fields(h, 1, rho, u, T);
   if (s) return fail(net, s, "lbm_set_fields failed");
   return LBM_OK;
