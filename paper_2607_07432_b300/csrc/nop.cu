@@ -189,20 +189,28 @@ lbm_status finish(nop_net* net, const char* what) {
 // the tensor-core convolution with chunks of 8 NG input channels; its
 // dynamic shared-memory limit (for the largest Cout, 128) is set once per
 // device
-template <int NG, bool DB>
+template <int NG, bool DB, int R>
 void conv_tc(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float* bias, float* Y, int B, int H, int W,
              int Cin, int Cout, int relu, int accumulate) {
   static bool attr[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr[dev]) {
-    cudaFuncSetAttribute(k_conv3x3_tc<NG, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)conv_tc_smem(NG, 128, DB));
+    cudaFuncSetAttribute(k_conv3x3_tc<NG, DB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)conv_tc_smem(NG, 128, DB, R));
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  const unsigned grid = (unsigned)((long long)B * H * (W / kTcM));
-  k_conv3x3_tc<NG, DB><<<grid, 128, conv_tc_smem(NG, Cout, DB), net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout,
-                                                                           relu, accumulate, net->tc_status);
+  const unsigned grid = (unsigned)((long long)B * (H / R) * (W / kTcM));
+  k_conv3x3_tc<NG, DB, R><<<grid, 128, conv_tc_smem(NG, Cout, DB, R), net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout,
+                                                                                 relu, accumulate, net->tc_status);
+}
+
+constexpr int kTcRows = 2;  // image rows per tensor-core CTA (when H allows)
+
+// grid of the row-wise resampling kernels: (x, channel group) of one row
+// along x, rows along y (grid-stride beyond 65535 rows)
+dim3 row_grid(int rows, int W, int C) {
+  return dim3((unsigned)((W * (C / 4) + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
 }
 
 // one 3x3 convolution (see k_conv3x3): on the tcgen05 tensor cores when a
@@ -211,10 +219,17 @@ void conv_tc(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float*
 void conv(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float* bias, float* Y, int B, int H, int W,
           int Cin, int Cout, int relu, int accumulate) {
   if (W % kTcM == 0 && Cout <= 128) {
-    if (Cin % 32 == 0)
-      conv_tc<4, false>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
-    else
-      conv_tc<2, false>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+    if (H % kTcRows == 0) {
+      if (Cin % 32 == 0)
+        conv_tc<4, false, kTcRows>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+      else
+        conv_tc<2, false, kTcRows>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+    } else {
+      if (Cin % 32 == 0)
+        conv_tc<4, false, 1>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+      else
+        conv_tc<2, false, 1>(net, X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+    }
     return;
   }
   dim3 grid((unsigned)((long long)B * H * ((W + kRowPx - 1) / kRowPx)), (unsigned)((Cout + kTN - 1) / kTN));
@@ -249,13 +264,15 @@ lbm_status forward(nop_net* net, int B) {
         break;
       }
       case kPool:
-        k_pool2<<<blocks(n_out), 256, 0, net->st>>>(ti.act, to.act, n_out, Ho, Wo, to.C);
+        k_pool2<<<row_grid(B * Ho, Wo, to.C), 256, 0, net->st>>>(ti.act, to.act, B * Ho, Ho, Wo, to.C);
         break;
       case kUp:
-        k_up2<<<blocks(n_out), 256, 0, net->st>>>(ti.act, to.act, n_out, Ho, Wo, to.C);
+        k_up2<<<row_grid(B * Ho, Wo, to.C), 256, 0, net->st>>>(ti.act, to.act, B * Ho, Ho, Wo, to.C);
         break;
       case kAdd:
-        k_add<<<blocks(n_out), 256, 0, net->st>>>(ti.act, net->T[op.in2].act, to.act, n_out);
+        k_add<<<blocks(n_out / 4), 256, 0, net->st>>>(reinterpret_cast<const float4*>(ti.act),
+                                                        reinterpret_cast<const float4*>(net->T[op.in2].act),
+                                                        reinterpret_cast<float4*>(to.act), n_out / 4);
         break;
     }
   }
@@ -296,15 +313,17 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
         break;
       }
       case kPool:
-        k_pool2_bwd<<<blocks(n_in), 256, 0, net->st>>>(to.grad, ti.grad, n_in, Hi, Wi, ti.C);
+        k_pool2_bwd<<<row_grid(B * Hi, Wi, ti.C), 256, 0, net->st>>>(to.grad, ti.grad, B * Hi, Hi, Wi, ti.C);
         break;
       case kUp:
-        k_up2_bwd<<<blocks(n_in), 256, 0, net->st>>>(to.grad, ti.grad, n_in, Hi, Wi, ti.C);
+        k_up2_bwd<<<row_grid(B * Hi, Wi, ti.C), 256, 0, net->st>>>(to.grad, ti.grad, B * Hi, Hi, Wi, ti.C);
         break;
       case kAdd: {
         const long long n = pixels(net, to.level, B) * to.C;
-        k_acc<<<blocks(n), 256, 0, net->st>>>(to.grad, ti.grad, n);
-        k_acc<<<blocks(n), 256, 0, net->st>>>(to.grad, net->T[op.in2].grad, n);
+        k_acc<<<blocks(n / 4), 256, 0, net->st>>>(reinterpret_cast<const float4*>(to.grad),
+                                                    reinterpret_cast<float4*>(ti.grad), n / 4);
+        k_acc<<<blocks(n / 4), 256, 0, net->st>>>(reinterpret_cast<const float4*>(to.grad),
+                                                    reinterpret_cast<float4*>(net->T[op.in2].grad), n / 4);
         break;
       }
     }

@@ -224,11 +224,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 // bytes of one staging buffer (In then Ws) and of the dynamic shared memory:
 // one or two buffers (DB), two mbarriers and the TMEM address
-__host__ __device__ constexpr size_t conv_tc_stage_bytes(int NG, int N) {
-  return (size_t)3 * NG * kTcCols * 16 + (size_t)9 * NG * N * 16;
+__host__ __device__ constexpr size_t conv_tc_stage_bytes(int NG, int N, int R) {
+  return (size_t)(R + 2) * NG * kTcCols * 16 + (size_t)9 * NG * N * 16;
 }
-__host__ __device__ constexpr size_t conv_tc_smem(int NG, int N, bool DB) {
-  return (DB ? 2 : 1) * conv_tc_stage_bytes(NG, N) + 32;
+__host__ __device__ constexpr size_t conv_tc_smem(int NG, int N, bool DB, int R) {
+  return (DB ? 2 : 1) * conv_tc_stage_bytes(NG, N, R) + 32;
 }
 
 // wait (bounded) for phase `phase` of an mbarrier; true when it completed
@@ -250,14 +250,14 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t phase) {
 // x0-1..x0+128 (zero outside the image) and the weights of all taps for
 // those channels, as BF16; consecutive threads read consecutive 32-byte
 // pieces of one pixel's channels
-template <int NG>
+template <int NG, int R>
 __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, const float* __restrict__ X,
                                          const __nv_bfloat16* __restrict__ Wt, int b, int y, int x0, int c0, int H,
                                          int W, int Cin, int Cout, int tid) {
   // four items per thread per pass: all eight loads are issued before the
   // first conversion, so each thread keeps several loads in flight
   constexpr int kBatch = 4;
-  constexpr int total = 3 * kTcCols * NG;
+  constexpr int total = (R + 2) * kTcCols * NG;
   for (int u0 = tid; u0 < total; u0 += kBatch * 128) {
     float4 lo[kBatch], hi[kBatch];
 #pragma unroll
@@ -314,14 +314,14 @@ __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, c
   }
 }
 
-template <int NG, bool DB>
+template <int NG, bool DB, int R>
 __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X, const __nv_bfloat16* __restrict__ Wt,
                                                     const float* __restrict__ bias, float* __restrict__ Y, int B,
                                                     int H, int W, int Cin, int Cout, int relu, int accumulate,
                                                     int* status) {
   extern __shared__ __align__(128) unsigned char sm[];
-  const size_t stage = conv_tc_stage_bytes(NG, Cout);
-  const size_t in_bytes = (size_t)3 * NG * kTcCols * 16;
+  const size_t stage = conv_tc_stage_bytes(NG, Cout, R);
+  const size_t in_bytes = (size_t)(R + 2) * NG * kTcCols * 16;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + (DB ? 2 : 1) * stage);   // two barriers
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -335,11 +335,13 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
   int bid = blockIdx.x;
   const int xt = bid % tiles_x;
   bid /= tiles_x;
-  const int y = bid % H;
-  const int b = bid / H;
+  const int y = (bid % (H / R)) * R;  // first of the CTA's R output rows
+  const int b = bid / (H / R);
   const int x0 = xt * kTcM;
-  // TMEM columns: a power of two >= 32 holding Cout FP32 accumulators
-  const uint32_t ncols = Cout <= 32 ? 32u : (Cout <= 64 ? 64u : 128u);
+  // TMEM columns: a power of two >= 32 holding R x Cout FP32 accumulators
+  // (row rr's at columns rr Cout ..)
+  uint32_t ncols = 32u;
+  while (ncols < (uint32_t)(R * Cout)) ncols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
                  "r"(ncols));
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   const int nch = Cin / (8 * NG);
-  tc_stage<NG>(sm, sm + in_bytes, X, Wt, b, y, x0, 0, H, W, Cin, Cout, tid);
+  tc_stage<NG, R>(sm, sm + in_bytes, X, Wt, b, y, x0, 0, H, W, Cin, Cout, tid);
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -367,20 +369,22 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
       const unsigned char* In = sm + bb * stage;
       const unsigned char* Ws = In + in_bytes;
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
+      for (int rr = 0; rr < R; ++rr)
 #pragma unroll
-        for (int sl = 0; sl < NG / 2; ++sl) {
-          const uint64_t ad =
-              umma_desc(smem_u32(In + ((size_t)(ky * NG + 2 * sl) * kTcCols + kx) * 16), kTcCols * 16, 128);
-          const uint64_t bd = umma_desc(smem_u32(Ws + (size_t)(tap * NG + 2 * sl) * Cout * 16), Cout * 16, 128);
-          const uint32_t acc = (ch > 0 || tap > 0 || sl > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+          for (int sl = 0; sl < NG / 2; ++sl) {
+            const uint64_t ad = umma_desc(smem_u32(In + ((size_t)((rr + ky) * NG + 2 * sl) * kTcCols + kx) * 16),
+                                          kTcCols * 16, 128);
+            const uint64_t bd = umma_desc(smem_u32(Ws + (size_t)(tap * NG + 2 * sl) * Cout * 16), Cout * 16, 128);
+            const uint32_t acc = (ch > 0 || tap > 0 || sl > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(rr * Cout)),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
         }
-      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                        smem_u32(mbar + bb))
                    : "memory");
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
       }
       phases ^= 1u;
       if (ch + 1 < nch) {
-        tc_stage<NG>(sm, sm + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
+        tc_stage<NG, R>(sm, sm + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
       }
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
         phases ^= 1u << (bb ^ 1);
       }
       unsigned char* nb = sm + (bb ^ 1) * stage;
-      tc_stage<NG>(nb, nb + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
+      tc_stage<NG, R>(nb, nb + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncthreads();
     }
@@ -422,13 +426,14 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
   }
   if (!ok && tid == 0) atomicExch(status, 1);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (ok) {
-    // accumulators of pixel x0 + 32 warp + lane, 32 columns at a time
+  for (int rr = 0; ok && rr < R; ++rr) {
+    // accumulators of pixel x0 + 32 warp + lane of row y + rr, 32 columns
+    // at a time
     const int x = x0 + warp * 32 + lane;
-    float* dst = Y + (((long long)b * H + y) * W + x) * Cout;
+    float* dst = Y + (((long long)b * H + y + rr) * W + x) * Cout;
     for (int n0 = 0; n0 < Cout; n0 += 32) {
       float v[32];
-      tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
+      tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(rr * Cout + n0), v);
       const int nv = Cout - n0 < 32 ? Cout - n0 : 32;
 #pragma unroll
       for (int j = 0; j < 32; j += 4) {
@@ -603,80 +608,107 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int n, long long le
 namespace lbmib {
 namespace nop {
 
+// The resampling and elementwise kernels work on float4 groups of channels
+// (C is a multiple of 16).  The resampling ones take one image row per
+// blockIdx.y (grid-stride over rows = b H + y of the tensor they iterate)
+// and (x, channel group) along blockIdx.x, with 32-bit index arithmetic.
+
 // 2x2 average pooling: out (H/2 x W/2) = mean of the four children, summed
 // in the order (2y,2x), (2y,2x+1), (2y+1,2x), (2y+1,2x+1).
-__global__ void k_pool2(const float* __restrict__ in, float* __restrict__ out, long long n_out, int Ho, int Wo,
-                        int C) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_out) return;
-  const int c = (int)(i % C);
-  const long long q = i / C;
-  const int x = (int)(q % Wo);
-  const long long r = q / Wo;
-  const int y = (int)(r % Ho);
-  const long long b = r / Ho;
+__global__ void k_pool2(const float* __restrict__ in, float* __restrict__ out, int rows, int Ho, int Wo, int C) {
+  const int C4 = C >> 2, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Wo * C4) return;
+  const int x = j / C4, c4 = j - x * C4;
   const int Wi = 2 * Wo;
-  const long long base = ((b * 2 * Ho + 2 * y) * Wi + 2 * x) * C + c;
-  const float s = ((in[base] + in[base + C]) + in[base + (long long)Wi * C]) + in[base + (long long)Wi * C + C];
-  out[i] = 0.25f * s;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int y = r % Ho;
+    const long long b = r / Ho;
+    const float4* p0 = reinterpret_cast<const float4*>(in + ((b * 2 * Ho + 2 * y) * Wi + 2 * x) * C) + c4;
+    const float4 a = p0[0], bq = p0[C4], c = p0[(long long)Wi * C4], d = p0[(long long)Wi * C4 + C4];
+    float4 o;
+    o.x = 0.25f * (((a.x + bq.x) + c.x) + d.x);
+    o.y = 0.25f * (((a.y + bq.y) + c.y) + d.y);
+    o.z = 0.25f * (((a.z + bq.z) + c.z) + d.z);
+    o.w = 0.25f * (((a.w + bq.w) + c.w) + d.w);
+    reinterpret_cast<float4*>(out + ((long long)r * Wo + x) * C)[c4] = o;
+  }
 }
 
 // adjoint of k_pool2, accumulated: din(y, x) += dout(y/2, x/2) / 4
-__global__ void k_pool2_bwd(const float* __restrict__ dout, float* __restrict__ din, long long n_in, int Hi,
-                            int Wi, int C) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_in) return;
-  const int c = (int)(i % C);
-  const long long q = i / C;
-  const int x = (int)(q % Wi);
-  const long long r = q / Wi;
-  const int y = (int)(r % Hi);
-  const long long b = r / Hi;
-  din[i] += 0.25f * dout[((b * (Hi / 2) + y / 2) * (Wi / 2) + x / 2) * C + c];
+__global__ void k_pool2_bwd(const float* __restrict__ dout, float* __restrict__ din, int rows, int Hi, int Wi,
+                            int C) {
+  const int C4 = C >> 2, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Wi * C4) return;
+  const int x = j / C4, c4 = j - x * C4;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int y = r % Hi;
+    const long long b = r / Hi;
+    const float4 g = reinterpret_cast<const float4*>(dout + ((b * (Hi / 2) + y / 2) * (Wi / 2) + x / 2) * C)[c4];
+    float4* d = reinterpret_cast<float4*>(din + ((long long)r * Wi + x) * C) + c4;
+    float4 o = *d;
+    o.x += 0.25f * g.x;
+    o.y += 0.25f * g.y;
+    o.z += 0.25f * g.z;
+    o.w += 0.25f * g.w;
+    *d = o;
+  }
 }
 
 // nearest-neighbour x2 up-sampling: out(y, x) = in(y/2, x/2)
-__global__ void k_up2(const float* __restrict__ in, float* __restrict__ out, long long n_out, int Ho, int Wo,
-                      int C) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_out) return;
-  const int c = (int)(i % C);
-  const long long q = i / C;
-  const int x = (int)(q % Wo);
-  const long long r = q / Wo;
-  const int y = (int)(r % Ho);
-  const long long b = r / Ho;
-  out[i] = in[((b * (Ho / 2) + y / 2) * (Wo / 2) + x / 2) * C + c];
+__global__ void k_up2(const float* __restrict__ in, float* __restrict__ out, int rows, int Ho, int Wo, int C) {
+  const int C4 = C >> 2, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Wo * C4) return;
+  const int x = j / C4, c4 = j - x * C4;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int y = r % Ho;
+    const long long b = r / Ho;
+    reinterpret_cast<float4*>(out + ((long long)r * Wo + x) * C)[c4] =
+        reinterpret_cast<const float4*>(in + ((b * (Ho / 2) + y / 2) * (Wo / 2) + x / 2) * C)[c4];
+  }
 }
 
 // adjoint of k_up2, accumulated: din(y, x) += sum of the four children
-__global__ void k_up2_bwd(const float* __restrict__ dout, float* __restrict__ din, long long n_in, int Hi,
-                          int Wi, int C) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_in) return;
-  const int c = (int)(i % C);
-  const long long q = i / C;
-  const int x = (int)(q % Wi);
-  const long long r = q / Wi;
-  const int y = (int)(r % Hi);
-  const long long b = r / Hi;
+__global__ void k_up2_bwd(const float* __restrict__ dout, float* __restrict__ din, int rows, int Hi, int Wi,
+                          int C) {
+  const int C4 = C >> 2, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Wi * C4) return;
+  const int x = j / C4, c4 = j - x * C4;
   const int Wo = 2 * Wi;
-  const long long base = ((b * 2 * Hi + 2 * y) * Wo + 2 * x) * C + c;
-  const float s = ((dout[base] + dout[base + C]) + dout[base + (long long)Wo * C]) + dout[base + (long long)Wo * C + C];
-  din[i] += s;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int y = r % Hi;
+    const long long b = r / Hi;
+    const float4* p0 = reinterpret_cast<const float4*>(dout + ((b * 2 * Hi + 2 * y) * Wo + 2 * x) * C) + c4;
+    const float4 a = p0[0], bq = p0[C4], c = p0[(long long)Wo * C4], d = p0[(long long)Wo * C4 + C4];
+    float4* q = reinterpret_cast<float4*>(din + ((long long)r * Wi + x) * C) + c4;
+    float4 o = *q;
+    o.x += ((a.x + bq.x) + c.x) + d.x;
+    o.y += ((a.y + bq.y) + c.y) + d.y;
+    o.z += ((a.z + bq.z) + c.z) + d.z;
+    o.w += ((a.w + bq.w) + c.w) + d.w;
+    *q = o;
+  }
 }
 
-// out = a + b
-__global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out,
-                      long long n) {
+// out = a + b (n4 float4 groups)
+__global__ void k_add(const float4* __restrict__ a, const float4* __restrict__ b, float4* __restrict__ out,
+                      long long n4) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = a[i] + b[i];
+  if (i >= n4) return;
+  const float4 u = a[i], v = b[i];
+  out[i] = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
 }
 
-// dst += src
-__global__ void k_acc(const float* __restrict__ src, float* __restrict__ dst, long long n) {
+// dst += src (n4 float4 groups)
+__global__ void k_acc(const float4* __restrict__ src, float4* __restrict__ dst, long long n4) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] += src[i];
+  if (i >= n4) return;
+  const float4 u = src[i];
+  float4 v = dst[i];
+  v.x += u.x;
+  v.y += u.y;
+  v.z += u.z;
+  v.w += u.w;
+  dst[i] = v;
 }
 
 // ReLU backward in place: g = g if y > 0 else 0 (y is the activation output)
