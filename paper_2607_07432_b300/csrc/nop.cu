@@ -298,15 +298,17 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
       case kConv: {
         const Layer& l = net->L[op.layer];
         const long long P = pixels(net, to.level, B);
-        if (op.relu) k_relu_mask<<<blocks(P * to.C), 256, 0, net->st>>>(to.act, to.grad, P * to.C);
+        if (op.relu)
+          k_relu_mask<<<blocks(P * to.C / 4), 256, 0, net->st>>>(reinterpret_cast<const float4*>(to.act),
+                                                                  reinterpret_cast<float4*>(to.grad), P * to.C / 4);
         const int nchunk = wgrad_chunks(B, Hi, Wi);
         dim3 wg((unsigned)nchunk, (unsigned)((l.coutp + 31) / 32), (unsigned)((l.cinp + 31) / 32));
         k_conv3x3_wgrad<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp);
         const long long len = (long long)l.coutp * 9 * l.cinp;
-        k_sum_chunks<<<blocks(len), 256, 0, net->st>>>(net->part, nchunk, len, l.dW);
+        k_sum_chunks<<<(unsigned)((len + 31) / 32), dim3(32, 8), 0, net->st>>>(net->part, nchunk, len, l.dW);
         const int nbias = (int)((P + kWChunk - 1) / kWChunk);
-        k_bias_partial<<<nbias, l.coutp, 0, net->st>>>(to.grad, net->part, P, l.coutp);
-        k_sum_chunks<<<blocks(l.coutp), 256, 0, net->st>>>(net->part, nbias, l.coutp, l.db);
+        k_bias_partial<<<nbias, dim3(l.coutp, 4), 0, net->st>>>(to.grad, net->part, P, l.coutp);
+        k_sum_chunks<<<(unsigned)((l.coutp + 31) / 32), dim3(32, 8), 0, net->st>>>(net->part, nbias, l.coutp, l.db);
         if (op.in != net->x_t || want_dx) {
           conv(net, to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
         }
@@ -538,7 +540,7 @@ lbm_status nop_train_step(nop_net* net, int batch, const float* x, const float* 
   const double inv_count = 1.0 / ((double)P * net->cfg.out_channels);
   const int nb = (int)blocks(P * t.C);
   k_mse<<<nb, 256, 0, net->st>>>(t.act, target, t.grad, net->loss_part, P, t.C, net->cfg.out_channels, inv_count);
-  k_mse_total<<<1, 1, 0, net->st>>>(net->loss_part, nb, inv_count, net->loss_dev);
+  k_mse_total<<<1, 1024, 0, net->st>>>(net->loss_part, nb, inv_count, net->loss_dev);
   if ((s = backward(net, batch, false))) return s;
   net->adam_t += 1;
   const float b1 = 0.9f, b2 = 0.999f;

@@ -585,21 +585,37 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const float* __restrict__
 // Bias-gradient partials: part[chunk][co] = sum_{p in chunk} G[p][co], pixels
 // in order.  grid = chunks, block = Cout threads.
 __global__ void k_bias_partial(const float* __restrict__ G, float* __restrict__ part, long long P, int Cout) {
-  const int co = threadIdx.x;
+  // threadIdx.x = c_out, threadIdx.y = stripe: stripe k sums the chunk's
+  // pixels p = k, k + 4, ... in order; the four stripes are added in order
+  __shared__ float red[4][256];  // Cout <= 256
+  const int co = threadIdx.x, k = threadIdx.y;
   const long long pbeg = (long long)blockIdx.x * kWChunk;
   const long long pend = pbeg + kWChunk < P ? pbeg + kWChunk : P;
   float s = 0.f;
-  for (long long p = pbeg; p < pend; ++p) s += G[p * Cout + co];
-  part[(long long)blockIdx.x * Cout + co] = s;
+  for (long long p = pbeg + k; p < pend; p += 4) s += G[p * Cout + co];
+  red[k][co] = s;
+  __syncthreads();
+  if (k == 0) part[(long long)blockIdx.x * Cout + co] = ((red[0][co] + red[1][co]) + red[2][co]) + red[3][co];
 }
 
-// out[j] = sum_{c = 0..n-1} part[c][j] in chunk order (deterministic).
+// out[j] = sum_{c = 0..n-1} part[c][j], deterministic: 32 j per block
+// (threadIdx.x), eight stripes of chunks c = y, y + 8, ... summed in order
+// (threadIdx.y = y), the stripes added in order.
 __global__ void k_sum_chunks(const float* __restrict__ part, int n, long long len, float* __restrict__ out) {
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= len) return;
+  __shared__ float red[8][32];
+  const long long j = (long long)blockIdx.x * 32 + threadIdx.x;
+  const int y = threadIdx.y;
   float s = 0.f;
-  for (int c = 0; c < n; ++c) s += part[(long long)c * len + j];
-  out[j] = s;
+  if (j < len)
+    for (int c = y; c < n; c += 8) s += part[(long long)c * len + j];
+  red[y][threadIdx.x] = s;
+  __syncthreads();
+  if (y == 0 && j < len) {
+    float t = red[0][threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+    out[j] = t;
+  }
 }
 
 }  // namespace nop
@@ -712,9 +728,16 @@ __global__ void k_acc(const float4* __restrict__ src, float4* __restrict__ dst, 
 }
 
 // ReLU backward in place: g = g if y > 0 else 0 (y is the activation output)
-__global__ void k_relu_mask(const float* __restrict__ y, float* __restrict__ g, long long n) {
+__global__ void k_relu_mask(const float4* __restrict__ y, float4* __restrict__ g, long long n4) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && !(y[i] > 0.f)) g[i] = 0.f;
+  if (i >= n4) return;
+  const float4 a = y[i];
+  float4 v = g[i];
+  if (!(a.x > 0.f)) v.x = 0.f;
+  if (!(a.y > 0.f)) v.y = 0.f;
+  if (!(a.z > 0.f)) v.z = 0.f;
+  if (!(a.w > 0.f)) v.w = 0.f;
+  g[i] = v;
 }
 
 // channel padding: dst[p][c] = c < Cs ? src[p][c] : 0 (Cd >= Cs)
@@ -765,10 +788,19 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
 }
 
 // loss = inv_count * sum_b part[b], blocks in order (one thread)
+// one block of 1024 threads: thread t sums the partials of blocks t, t +
+// 1024, ... in order, then a fixed-order tree (deterministic)
 __global__ void k_mse_total(const double* __restrict__ part, int n, double inv_count, double* __restrict__ out) {
+  __shared__ double red[1024];
   double s = 0.0;
-  for (int b = 0; b < n; ++b) s += part[b];
-  *out = s * inv_count;
+  for (int b = threadIdx.x; b < n; b += 1024) s += part[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0] * inv_count;
 }
 
 // Adam with bias correction on the FP32 master weights.
