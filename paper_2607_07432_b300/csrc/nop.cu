@@ -201,11 +201,11 @@ void conv_tc(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float*
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
   const unsigned grid = (unsigned)((long long)B * (H / R) * (W / kTcM));
-  k_conv3x3_tc<NG, DB, R><<<grid, 128, conv_tc_smem(NG, Cout, DB, R), net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout,
+  k_conv3x3_tc<NG, DB, R><<<grid, 128 * R, conv_tc_smem(NG, Cout, DB, R), net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout,
                                                                                  relu, accumulate, net->tc_status);
 }
 
-constexpr int kTcRows = 2;  // image rows per tensor-core CTA (when H allows)
+constexpr int kTcRows = 4;  // image rows per tensor-core CTA (when H allows)
 
 // grid of the row-wise resampling kernels: (x, channel group) of one row
 // along x, rows along y (grid-stride beyond 65535 rows)

@@ -152,25 +152,28 @@ __global__ void __launch_bounds__(128) k_conv3x3(const float* __restrict__ X,
 
 // ---------------------------------------------------------------------------
 // The same convolution on the 5th-generation tensor cores (tcgen05): one CTA
-// computes 128 consecutive pixels of one image row (M = 128) for all Cout
-// output channels (N = Cout <= 128), accumulating in tensor memory.
+// of 128 R threads computes R image rows of 128 consecutive pixels each
+// (one M = 128 accumulator per row) for all Cout output channels (N = Cout
+// <= 128), accumulating in tensor memory (row rr at columns rr Cout ..).
 //
 // Per chunk of 8 NG input channels (NG = 4 groups of 8, or 2 when Cin is
 // not a multiple of 32) the CTA stages, as BF16 in the canonical K-major
-// layout without swizzling (8 x 16-byte core matrices), the three input
-// rows it needs (130 columns: In[row][group][column][8 channels]) and the
-// chunk's weights of all nine taps (Ws[tap][group][c_out][8 channels]).
-// One thread issues the chunk's 9 NG / 2 MMAs of K = 16 (per tap, the A
-// operand is the staged rows from column offset kx) and commits them to an
-// mbarrier.  With one staging buffer (DB false, the form the network uses)
-// the CTA waits for them before staging the next chunk; with two (DB true)
-// it stages the next chunk into the other buffer while they run.  On the
-// 512x256 network the single buffer is faster (2.46 against 3.58 ms per
-// forward pass): the second buffer halves the CTAs resident per SM, and the
-// staging loads, not the MMAs, set the pace.  The epilogue reads the accumulators back with
-// tcgen05.ld (warp w owns TMEM lanes / pixels 32w..32w+31), adds the bias,
-// applies ReLU and writes (or accumulates into) Y.  Waits are bounded: on a
-// timeout the CTA records it in *status and skips its stores.
+// layout without swizzling (8 x 16-byte core matrices), the R + 2 input rows
+// its outputs need (130 columns: In[row][group][column][8 channels]) and the
+// chunk's weights of all nine taps (Ws[tap][group][c_out][8 channels]), so
+// each staged row and weight serves R output rows.  One thread issues the
+// chunk's 9 R NG / 2 MMAs of K = 16 (per output row and tap, the A operand
+// is the staged row ky below it from column offset kx) and commits them to
+// an mbarrier.  With one staging buffer (DB false, the form the network
+// uses) the CTA waits for them before staging the next chunk; with two (DB
+// true) it stages the next chunk into the other buffer while they run.  On
+// the 512x256 network one buffer is faster (at R = 1: 2.46 against 3.58 ms
+// per forward pass): the staging loads, not the MMAs, set the pace, and a
+// second buffer halves the CTAs resident per SM.  R = 4 (512 threads) is
+// the fastest of 1, 2 and 4 there (1.51 ms).  In the epilogue warp w reads
+// TMEM lanes 32 (w % 4) .. (its 32 pixels) of row w / 4 with tcgen05.ld,
+// adds the bias, applies ReLU and writes (or accumulates into) Y.  Waits are
+// bounded: on a timeout the CTA records it in *status and skips its stores.
 constexpr int kTcM = 128;               // pixels per CTA
 constexpr int kTcCols = kTcM + 2;       // staged input columns
 constexpr unsigned long long kTcWaitNs = 200000000ull;  // MMA-completion wait limit (0.2 s)
@@ -250,7 +253,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t phase) {
 // x0-1..x0+128 (zero outside the image) and the weights of all taps for
 // those channels, as BF16; consecutive threads read consecutive 32-byte
 // pieces of one pixel's channels
-template <int NG, int R>
+template <int NG, int R, int NT>
 __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, const float* __restrict__ X,
                                          const __nv_bfloat16* __restrict__ Wt, int b, int y, int x0, int c0, int H,
                                          int W, int Cin, int Cout, int tid) {
@@ -258,11 +261,11 @@ __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, c
   // first conversion, so each thread keeps several loads in flight
   constexpr int kBatch = 4;
   constexpr int total = (R + 2) * kTcCols * NG;
-  for (int u0 = tid; u0 < total; u0 += kBatch * 128) {
+  for (int u0 = tid; u0 < total; u0 += kBatch * NT) {
     float4 lo[kBatch], hi[kBatch];
 #pragma unroll
     for (int k = 0; k < kBatch; ++k) {
-      const int u = u0 + k * 128;
+      const int u = u0 + k * NT;
       lo[k] = hi[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (u < total) {
         const int g = u % NG, rc = u / NG;
@@ -278,7 +281,7 @@ __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, c
     }
 #pragma unroll
     for (int k = 0; k < kBatch; ++k) {
-      const int u = u0 + k * 128;
+      const int u = u0 + k * NT;
       if (u >= total) break;
       const int g = u % NG, rc = u / NG;
       const int col = rc % kTcCols, r = rc / kTcCols;
@@ -291,11 +294,11 @@ __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, c
     }
   }
   const int wtotal = 9 * NG * Cout;
-  for (int u0 = tid; u0 < wtotal; u0 += kBatch * 128) {
+  for (int u0 = tid; u0 < wtotal; u0 += kBatch * NT) {
     uint4 w[kBatch];
 #pragma unroll
     for (int k = 0; k < kBatch; ++k) {
-      const int u = u0 + k * 128;
+      const int u = u0 + k * NT;
       w[k] = make_uint4(0u, 0u, 0u, 0u);
       if (u < wtotal) {
         const int g = u % NG, rc = u / NG;
@@ -305,7 +308,7 @@ __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, c
     }
 #pragma unroll
     for (int k = 0; k < kBatch; ++k) {
-      const int u = u0 + k * 128;
+      const int u = u0 + k * NT;
       if (u >= wtotal) break;
       const int g = u % NG, rc = u / NG;
       const int tap = rc % 9, co = rc / 9;
@@ -315,7 +318,7 @@ __device__ __forceinline__ void tc_stage(unsigned char* In, unsigned char* Ws, c
 }
 
 template <int NG, bool DB, int R>
-__global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X, const __nv_bfloat16* __restrict__ Wt,
+__global__ void __launch_bounds__(128 * R) k_conv3x3_tc(const float* __restrict__ X, const __nv_bfloat16* __restrict__ Wt,
                                                     const float* __restrict__ bias, float* __restrict__ Y, int B,
                                                     int H, int W, int Cin, int Cout, int relu, int accumulate,
                                                     int* status) {
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   const int nch = Cin / (8 * NG);
-  tc_stage<NG, R>(sm, sm + in_bytes, X, Wt, b, y, x0, 0, H, W, Cin, Cout, tid);
+  tc_stage<NG, R, 128 * R>(sm, sm + in_bytes, X, Wt, b, y, x0, 0, H, W, Cin, Cout, tid);
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
       }
       phases ^= 1u;
       if (ch + 1 < nch) {
-        tc_stage<NG, R>(sm, sm + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
+        tc_stage<NG, R, 128 * R>(sm, sm + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
       }
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
         phases ^= 1u << (bb ^ 1);
       }
       unsigned char* nb = sm + (bb ^ 1) * stage;
-      tc_stage<NG, R>(nb, nb + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
+      tc_stage<NG, R, 128 * R>(nb, nb + in_bytes, X, Wt, b, y, x0, (ch + 1) * 8 * NG, H, W, Cin, Cout, tid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncthreads();
     }
@@ -426,14 +429,15 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float* __restrict__ X,
   }
   if (!ok && tid == 0) atomicExch(status, 1);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  for (int rr = 0; ok && rr < R; ++rr) {
-    // accumulators of pixel x0 + 32 warp + lane of row y + rr, 32 columns
-    // at a time
-    const int x = x0 + warp * 32 + lane;
+  if (ok) {
+    // warp w reads TMEM lanes 32 (w % 4) .. (pixels x0 + 32 (w % 4) + lane)
+    // of row y + w / 4, 32 columns at a time
+    const int rr = warp >> 2;
+    const int x = x0 + (warp & 3) * 32 + lane;
     float* dst = Y + (((long long)b * H + y + rr) * W + x) * Cout;
     for (int n0 = 0; n0 < Cout; n0 += 32) {
       float v[32];
-      tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(rr * Cout + n0), v);
+      tmem_ld32<32>(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(rr * Cout + n0), v);
       const int nv = Cout - n0 < 32 ? Cout - n0 : 32;
 #pragma unroll
       for (int j = 0; j < 32; j += 4) {
