@@ -166,7 +166,7 @@ lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle**
                                     : theta_rule(cfg->mach, cfg->gamma, cfg->reynolds, cfg->ref_length,
                                                  cfg->prandtl, D);
   h->rho_inf = 1.0;
-  h->g.thref = float(h->theta_inf);
+  for (float& o : h->g.off) o = 0.f;  // storage offsets: set by the engine's init
   const double c_inf = std::sqrt(h->gamma * h->R * h->theta_inf);
   h->u_mag = cfg->mach * c_inf;
   double dn = 0.0;

@@ -78,6 +78,16 @@ struct Engine {
                                            C(h->u_inf[2]), C(h->theta_inf));
     });
     if (s) return s;
+    // storage offsets (pop_offset): the free-stream equilibrium for 16-bit
+    // storage, read back before any state is stored; w_i otherwise
+    if constexpr (sizeof(S) == 2) {
+      C fe[L::Q];
+      CK(cudaMemcpyAsync(fe, h->feq_inf, sizeof(fe), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      for (int i = 0; i < L::Q; ++i) h->g.off[i] = float(fe[i]);
+    } else {
+      for (int i = 0; i < L::Q; ++i) h->g.off[i] = float(L::w(i));
+    }
     // uniform free-stream start (reading Q25)
     std::vector<double> rho(h->g.N, h->rho_inf), T(h->g.N, h->theta_inf), u(h->g.N * L::D);
     for (int a = 0; a < L::D; ++a)

@@ -20,7 +20,7 @@ struct Grid {
   int per[3];
   long long N;
   int zoff;  // global z of local plane 0 (a z slab of a larger case; 0 otherwise)
-  float thref;  // reference temperature of 16-bit population storage (see pop_offset)
+  float off[19];  // values 16-bit storage subtracts from the populations (see pop_offset)
   __host__ __device__ __forceinline__ int wrap(int a, int v) const {
     if (per[a]) {
       v = v % n[a];
@@ -82,37 +82,35 @@ struct Store<__nv_bfloat16> {
 };
 
 // Reference value subtracted from population i before it is stored: w_i for
-// FP32 storage; for FP16 / BF16 storage the rest equilibrium at the run's
-// free-stream temperature, f^eq_i(rho = 1, u = 0, theta = thr) =
-// w_i thr + delta_0i (1 - thr) (Eq. feq), so that at theta_inf != 1 the
-// stored deviations near a wall at rest stay small and lose little to the
-// 16-bit rounding (at thr = 1 this is w_i)
+// FP32 storage; for FP16 / BF16 storage the free-stream equilibrium of the
+// case, f^eq_i(rho_inf, u_inf, theta_inf) (Eq. feq; off[i], set when the
+// case is created), so that the stored deviations stay small wherever the
+// flow is near the free stream and lose little to the 16-bit rounding
 template <class L, class S, class C>
-__device__ __forceinline__ C pop_offset(int i, C thr) {
+__device__ __forceinline__ C pop_offset(int i, const float* off) {
   if constexpr (sizeof(S) == 2) {
-    return C(L::w(i)) * thr + (i == 0 ? C(1) - thr : C(0));
+    return C(off[i]);
   } else {
     return C(L::w(i));
   }
 }
-// I: element index type (long long, or unsigned where Q N < 2^32)
 template <class L, class S, class C, class I = long long>
-__device__ __forceinline__ C load_pop(const S* f, int i, I N, I n, C thr) {
+__device__ __forceinline__ C load_pop(const S* f, int i, I N, I n, const float* off) {
   const C v = C(Store<S>::load(f[(I)i * N + n]));
-  return Store<S>::dev ? v + pop_offset<L, S, C>(i, thr) : v;
+  return Store<S>::dev ? v + pop_offset<L, S, C>(i, off) : v;
 }
 // the value a population takes after a store and a reload
 template <class L, class S, class C>
-__device__ __forceinline__ C roundtrip_pop(int i, C v, C thr) {
+__device__ __forceinline__ C roundtrip_pop(int i, C v, const float* off) {
   if (Store<S>::dev) {
-    const C o = pop_offset<L, S, C>(i, thr);
+    const C o = pop_offset<L, S, C>(i, off);
     return C(Store<S>::load(Store<S>::save(v - o))) + o;
   }
   return C(Store<S>::load(Store<S>::save(v)));
 }
 template <class L, class S, class C, class I = long long>
-__device__ __forceinline__ void store_pop(S* f, int i, I N, I n, C v, C thr) {
-  f[(I)i * N + n] = Store<S>::save(Store<S>::dev ? v - pop_offset<L, S, C>(i, thr) : v);
+__device__ __forceinline__ void store_pop(S* f, int i, I N, I n, C v, const float* off) {
+  f[(I)i * N + n] = Store<S>::save(Store<S>::dev ? v - pop_offset<L, S, C>(i, off) : v);
 }
 
 }  // namespace lbmib

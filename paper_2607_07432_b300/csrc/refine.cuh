@@ -74,7 +74,7 @@ __global__ void k_refine_shell(RefineDev r, const S* f0, const C* M0, C* out) {
   refine_macros<D, C>(M0, N0, n, C(r.Cv), rho, u, th);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    out[i * ns + s] = load_pop<L, S, C>(f0, i, N0, n, C(r.g0.thref)) - feq_i<L, C, i>(rho, u, th);
+    out[i * ns + s] = load_pop<L, S, C>(f0, i, N0, n, r.g0.off) - feq_i<L, C, i>(rho, u, th);
   });
 #pragma unroll
   for (int q = 0; q < D + 2; ++q) out[(Q + q) * ns + s] = M0[q * N0 + n];
@@ -149,8 +149,8 @@ __global__ void k_refine_fill(RefineDev r, S* f1, C* M1, C* P1, C* A1, const C* 
     constexpr int i = decltype(I)::value;
     const long long e = (long long)i * r.n_ghost + k;
     const C fv = second ? C(0.5) * (Ga[e] + Gb[e]) : Ga[e];
-    store_pop<L, S, C>(f1, i, N1, n1, fv, C(r.g1.thref));
-    const C v = roundtrip_pop<L, S, C>(i, fv, C(r.g1.thref));
+    store_pop<L, S, C>(f1, i, N1, n1, fv, r.g1.off);
+    const C v = roundtrip_pop<L, S, C>(i, fv, r.g1.off);
     rho += v;
     sfor<0, D>([&](auto A) {
       constexpr int d = decltype(A)::value;
@@ -205,9 +205,9 @@ __global__ void k_refine_restrict(RefineDev r, S* f0, C* M0, C* P0, C* A0, const
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const C fe = feq_i<L, C, i>(rho1, u, th);
-    const C fv = fe + s10 * (load_pop<L, S, C>(f1, i, N1, n1, C(r.g1.thref)) - fe);
-    store_pop<L, S, C>(f0, i, N0, n0, fv, C(r.g0.thref));
-    const C v = roundtrip_pop<L, S, C>(i, fv, C(r.g0.thref));
+    const C fv = fe + s10 * (load_pop<L, S, C>(f1, i, N1, n1, r.g1.off) - fe);
+    store_pop<L, S, C>(f0, i, N0, n0, fv, r.g0.off);
+    const C v = roundtrip_pop<L, S, C>(i, fv, r.g0.off);
     rho += v;
     sfor<0, D>([&](auto A) {
       constexpr int d = decltype(A)::value;

@@ -46,7 +46,7 @@ __global__ void k_set_fields(Grid g, S* f, C* E, const double* rho, const double
   const C th = C(T[n]);
   sfor<0, L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    store_pop<L, S, C>(f, i, g.N, n, feq_i<L, C, i>(r, uu, th), C(g.thref));
+    store_pop<L, S, C>(f, i, g.N, n, feq_i<L, C, i>(r, uu, th), g.off);
   });
   E[n] = r * (C(0.5) * k + Cv * th);
 }
@@ -60,7 +60,7 @@ __global__ void k_fields(Grid g, const S* f, const C* E, C Cv, C R, double* rho,
   C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const C v = load_pop<L, S, C>(f, i, g.N, n, C(g.thref));
+    const C v = load_pop<L, S, C>(f, i, g.N, n, g.off);
     r += v;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -86,7 +86,7 @@ __global__ void k_get_state(Grid g, const S* f, const C* E, double* fo, double* 
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.N) return;
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) fo[(long long)i * g.N + n] = double(load_pop<L, S, C>(f, i, g.N, n, C(g.thref)));
+  for (int i = 0; i < L::Q; ++i) fo[(long long)i * g.N + n] = double(load_pop<L, S, C>(f, i, g.N, n, g.off));
   Eo[n] = double(E[n]);
 }
 
@@ -95,7 +95,7 @@ __global__ void k_set_state(Grid g, S* f, C* E, const double* fi, const double* 
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.N) return;
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) store_pop<L, S, C>(f, i, g.N, n, C(fi[(long long)i * g.N + n]), C(g.thref));
+  for (int i = 0; i < L::Q; ++i) store_pop<L, S, C>(f, i, g.N, n, C(fi[(long long)i * g.N + n]), g.off);
   E[n] = C(Ei[n]);
 }
 
@@ -109,7 +109,7 @@ __global__ void k_reset_aux(Grid g, const S* f, const C* E, C Cv, C* Pp, C* Ap) 
   C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const C v = load_pop<L, S, C>(f, i, g.N, n, C(g.thref));
+    const C v = load_pop<L, S, C>(f, i, g.N, n, g.off);
     r += v;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -134,7 +134,7 @@ __global__ void k_health(Grid g, const S* f, const C* E, C Cv, unsigned long lon
   C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const C v = load_pop<L, S, C>(f, i, g.N, n, C(g.thref));
+    const C v = load_pop<L, S, C>(f, i, g.N, n, g.off);
     r += v;
 #pragma unroll
     for (int a = 0; a < D; ++a)

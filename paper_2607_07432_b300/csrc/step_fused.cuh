@@ -281,7 +281,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const C v = C(Store<S>::load(rf[RP ? i : 0]));
-        fbar[i] = Store<S>::dev ? v + pop_offset<L, S, C>(i, C(g.thref)) : v;
+        fbar[i] = Store<S>::dev ? v + pop_offset<L, S, C>(i, g.off) : v;
       }
       Pp = rP;
 #pragma unroll
@@ -289,7 +289,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       is_forced = rfl != 0;
     } else {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C, Ix>(a.f_in, i, N, n, C(g.thref));
+      for (int i = 0; i < Q; ++i) fbar[i] = load_pop<L, S, C, Ix>(a.f_in, i, N, n, g.off);
       Pp = a.Pp[n];
 #pragma unroll
       for (int q = 0; q < L::NDEV; ++q) dAFp[q] = a.Ap[q * N + n];
@@ -407,7 +407,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
       sfor<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const C v = fcol_at(i, z - L::c(i, 2), sx - L::c(i, 0), cy - L::c(i, 1));
-        store_pop<L, S, C, Ix>(a.f_out, i, N, n, v, C(g.thref));
+        store_pop<L, S, C, Ix>(a.f_out, i, N, n, v, g.off);
         rho += v;
         sfor<0, D>([&](auto A) {
           constexpr int d = decltype(A)::value;
@@ -420,8 +420,8 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
         j[0] = j[1] = j[2] = C(0);
         sfor<0, Q>([&](auto I) {
           constexpr int i = decltype(I)::value;
-          store_pop<L, S, C, Ix>(a.f_out, i, N, n, a.feq_inf[i], C(g.thref));
-          const C v = roundtrip_pop<L, S, C>(i, a.feq_inf[i], C(g.thref));
+          store_pop<L, S, C, Ix>(a.f_out, i, N, n, a.feq_inf[i], g.off);
+          const C v = roundtrip_pop<L, S, C>(i, a.feq_inf[i], g.off);
           rho += v;
           sfor<0, D>([&](auto A) {
             constexpr int d = decltype(A)::value;
@@ -540,7 +540,7 @@ __global__ void k_moments(Grid g, const S* f, const C* E, C* M) {
   C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    const C v = load_pop<L, S, C>(f, i, g.N, n, C(g.thref));
+    const C v = load_pop<L, S, C>(f, i, g.N, n, g.off);
     r += v;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -593,8 +593,8 @@ __device__ __forceinline__ void bc_node(const Grid& g, S* f, C* M, const BCFaces
     C r = C(0), j[3] = {C(0), C(0), C(0)};
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-      store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i], C(g.thref));
-      const C v = roundtrip_pop<L, S, C>(i, feq_inf[i], C(g.thref));
+      store_pop<L, S, C>(f, i, g.N, dst, feq_inf[i], g.off);
+      const C v = roundtrip_pop<L, S, C>(i, feq_inf[i], g.off);
       r += v;
 #pragma unroll
       for (int a = 0; a < D; ++a)
@@ -612,8 +612,8 @@ __device__ __forceinline__ void bc_node(const Grid& g, S* f, C* M, const BCFaces
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const C fe = feq_of(I);
-      store_pop<L, S, C>(f, i, g.N, dst, fe, C(g.thref));
-      const C v = roundtrip_pop<L, S, C>(i, fe, C(g.thref));
+      store_pop<L, S, C>(f, i, g.N, dst, fe, g.off);
+      const C v = roundtrip_pop<L, S, C>(i, fe, g.off);
       r += v;
 #pragma unroll
       for (int a = 0; a < D; ++a)
