@@ -29,6 +29,16 @@ struct lbm_refined {
   void* Ga = nullptr;
   void* Gb = nullptr;
   std::string err;
+  // two level-0 steps captured as one CUDA graph (both parities of both
+  // levels return to the captured ones), valid while the buffers and the
+  // geometry versions match
+  cudaGraphExec_t gexec = nullptr;
+  void* g_f0 = nullptr;
+  void* g_f1 = nullptr;
+  int g_cur0 = 0, g_cur1 = 0, g_geom0 = -1, g_geom1 = -1;
+  long long g_launch0 = 0, g_launch1 = 0;
+  cudaStream_t cap_st = nullptr;
+  bool stepped = false;
 };
 
 namespace {
@@ -48,6 +58,8 @@ void refined_free(lbm_refined* r) {
     if (r->corners) cudaFree(r->corners);
     if (r->Ga) cudaFree(r->Ga);
     if (r->Gb) cudaFree(r->Gb);
+    if (r->gexec) cudaGraphExecDestroy(r->gexec);
+    if (r->cap_st) cudaStreamDestroy(r->cap_st);
   }
   lbm_destroy(r->h1);
   lbm_destroy(r->h0);
@@ -200,27 +212,113 @@ lbm_status lbm_refined_info(const lbm_refined* r, int info[8]) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// one level-0 step with its two level-1 steps and the transfers; the level
+// steps run eagerly (while a graph is captured) or through lbm_step
+lbm_status refined_once(lbm_refined* r, bool eager) {
+  lbm_handle *h0 = r->h0, *h1 = r->h1;
+  const Ops* ops = h0->ops;
+  lbmib::RefineDev& d = r->dev;
+  auto step = [&](lbm_handle* h) { return eager ? h->ops->step(h) : lbm_step(h, 1); };
+  lbm_status s = ops->refine_ghost_state(h0, d, r->Ga);  // level 0 at n
+  if (!s) s = step(h0);                                   // level 0: n -> n+1
+  if (!s) s = ops->refine_fill(h0, h1, d, r->Ga, nullptr);
+  if (!s) s = step(h1);                                   // level 1: n -> n+1/2
+  if (!s) s = ops->refine_ghost_state(h0, d, r->Gb);     // level 0 at n+1
+  if (!s) s = ops->refine_fill(h0, h1, d, r->Ga, r->Gb);
+  if (!s) s = step(h1);                                   // level 1: n+1/2 -> n+1
+  if (!s) s = ops->refine_restrict(h0, h1, d);
+  return s;
+}
+
+// capture two level-0 steps as a graph; the host side of the captured steps
+// (buffer swaps) returns both levels to the parities they started from
+lbm_status refined_capture(lbm_refined* r) {
+  lbm_handle *h0 = r->h0, *h1 = r->h1;
+  if (r->gexec) cudaGraphExecDestroy(r->gexec);
+  r->gexec = nullptr;
+  cudaStream_t run_st = h0->st;
+  if (!run_st && !r->cap_st && cudaStreamCreateWithFlags(&r->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return rfail(r, LBM_ECUDA, "capture stream");
+  }
+  cudaStream_t st = run_st ? run_st : r->cap_st;
+  const long long l0 = h0->launches, l1 = h1->launches;
+  void* f0 = h0->f;
+  void* f1 = h1->f;
+  const int c0 = h0->cur, c1 = h1->cur;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return rfail(r, LBM_ECUDA, "graph capture begin");
+  }
+  h0->st = h1->st = st;
+  lbm_status s = refined_once(r, true);
+  if (!s) s = refined_once(r, true);
+  h0->st = h1->st = run_st;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  r->g_launch0 = h0->launches - l0;
+  r->g_launch1 = h1->launches - l1;
+  h0->launches = l0;
+  h1->launches = l1;
+  if (s || e != cudaSuccess || h0->f != f0 || h1->f != f1 || h0->cur != c0 || h1->cur != c1) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rfail(r, s ? s : LBM_ECUDA, "refined step graph capture");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&r->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    r->gexec = nullptr;
+    cudaGetLastError();
+    return rfail(r, LBM_ECUDA, "refined step graph instantiate");
+  }
+  r->g_f0 = f0;
+  r->g_f1 = f1;
+  r->g_cur0 = c0;
+  r->g_cur1 = c1;
+  r->g_geom0 = h0->geom_version;
+  r->g_geom1 = h1->geom_version;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 lbm_status lbm_refined_step(lbm_refined* r, int n_steps) {
   if (!r || n_steps < 0) return LBM_EINVAL;
   lbm_handle *h0 = r->h0, *h1 = r->h1;
   DeviceGuard dg(h0->cfg.device);
   if (h0->sticky) return (lbm_status)h0->sticky;
   if (h1->sticky) return (lbm_status)h1->sticky;
-  const Ops* ops = h0->ops;
-  lbmib::RefineDev& d = r->dev;
-  for (int k = 0; k < n_steps; ++k) {
-    lbm_status s = ops->refine_ghost_state(h0, d, r->Ga);  // level 0 at n
-    if (!s) s = lbm_step(h0, 1);                            // level 0: n -> n+1
-    if (!s) s = ops->refine_fill(h0, h1, d, r->Ga, nullptr);
-    if (!s) s = lbm_step(h1, 1);                            // level 1: n -> n+1/2
-    if (!s) s = ops->refine_ghost_state(h0, d, r->Gb);     // level 0 at n+1
-    if (!s) s = ops->refine_fill(h0, h1, d, r->Ga, r->Gb);
-    if (!s) s = lbm_step(h1, 1);                            // level 1: n+1/2 -> n+1
-    if (!s) s = ops->refine_restrict(h0, h1, d);
+  // after a first eager step, pairs of level-0 steps replay a captured
+  // graph; profiling runs and odd remainders step through lbm_step
+  const bool graphs = h0->use_graph && h1->use_graph && !h0->prof && !h1->prof;
+  int k = 0;
+  while (k < n_steps) {
+    if (graphs && r->stepped && n_steps - k >= 2) {
+      if (!r->gexec || r->g_f0 != h0->f || r->g_f1 != h1->f || r->g_cur0 != h0->cur || r->g_cur1 != h1->cur ||
+          r->g_geom0 != h0->geom_version || r->g_geom1 != h1->geom_version) {
+        lbm_status s = refined_capture(r);
+        if (s) return s;
+      }
+      if (cudaGraphLaunch(r->gexec, h0->st) != cudaSuccess) return rfail(r, LBM_ECUDA, "refined graph launch");
+      h0->launches += r->g_launch0;
+      h1->launches += r->g_launch1;
+      k += 2;
+      continue;
+    }
+    lbm_status s = refined_once(r, false);
     if (s) {
       const lbm_handle* hb = h1->err.empty() ? h0 : h1;
       return rfail(r, s, hb->err);
     }
+    r->stepped = h0->stepped && h1->stepped;
+    ++k;
   }
   return LBM_OK;
 }

@@ -95,3 +95,23 @@ def test_refined_fp32_against_fp64():
             u64, u32, T64, T32 = u64[inner], u32[inner], T64[inner[1:]], T32[inner[1:]]
         assert np.linalg.norm(u32 - u64) / np.linalg.norm(u64) < 1e-5
         assert np.linalg.norm(T32 - T64) / np.linalg.norm(T64) < 1e-5
+
+
+def test_refined_graph_replay_matches_eager(monkeypatch):
+    """lbm_refined_step replays pairs of level-0 steps from a captured graph;
+    both levels equal eager stepping (LBMIB_NO_GRAPH=1) bit for bit, for
+    even and odd step counts."""
+    c = _case2d()
+    o, geo = _oracle(c)
+    out = []
+    for off in ("0", "1"):
+        monkeypatch.setenv("LBMIB_NO_GRAPH", off)
+        g = _gpu(c, "fp32", geo)
+        g.step(5)
+        g.step(4)
+        g.step(1)
+        out.append([lv.state() for lv in (g.level0, g.level1)])
+        g.close()
+    for lev in (0, 1):
+        assert np.array_equal(out[0][lev][0], out[1][lev][0])
+        assert np.array_equal(out[0][lev][1], out[1][lev][1])
