@@ -43,8 +43,21 @@ design notes of the repository):
       across it (the off-diagonal part), shear viscosity mu at any theta
       and frame, linear stability at low theta.  use_ac: AC_FULL (default),
       AC_CUBIC (the cubic term only: frame-dependent attenuation at
-      theta != 1), AC_OFF.
-  Q7  spatial derivatives are 2nd-order central; time derivative of
+      theta != 1), AC_OFF, and AC_UPWIND: the AC_FULL terms with first-order
+      one-sided differences taken on the upstream side of the node (the
+      backward difference along b where the node's u_b >= 0, the forward one
+      otherwise).  The paper gives no stencil for a^C.  With central
+      differences a uniform stream faster than the sound speed is linearly
+      unstable: on the odd-even mode along the stream every central
+      difference vanishes, and what is left of the lattice part feeds a
+      density perturbation back through its momentum flux (c^2 - u^2) d rho,
+      whose sign turns at u = c (for a D1Q3 stream at rest temperature
+      theta/3 the mode's eigenvalues solve l^2 - w(1 - 2a) l - (1 - w) = 0,
+      a = theta/3 - u^2, w = 1/tau-bar: a root above 1 exactly when a < 0).
+      One-sided differences see the mode; AC_UPWIND keeps supersonic
+      streams stable (pinned by the Jacobian spectrum of one step).
+  Q7  spatial derivatives are 2nd-order central (those of a^C first-order
+      upstream under AC_UPWIND, Q6); time derivative of
       rho(1-theta) is the backward difference with the stored previous value.
   Q8  the F_i(t - dt) term of Eq. pi2 enters through its traceless second
       moment, the stored deviator of a^F of the previous step.
@@ -74,7 +87,7 @@ CS2 = L.CS2
 BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_GHOST, BC_CHAR = 0, 1, 2, 3, 4, 5
 TAU_THETA, TAU_LITERAL = 0, 1
 # a^C readings (Q6): off, the diagonal cubic defect only, full (default)
-AC_OFF, AC_CUBIC, AC_FULL = 0, 1, 2
+AC_OFF, AC_CUBIC, AC_FULL, AC_UPWIND = 0, 1, 2, 3
 
 
 def theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, dim):
@@ -258,6 +271,33 @@ def deviator(lat, T):
     return out
 
 
+def lattice_correction(prm, grid, rho, u, theta):
+    """a^C of Eq. af2 (reading Q6): c_s^2 (u_a d_b P + u_b d_a P)
+    - d_ab d_a(rho u_a^3), P = rho(1-theta); central differences, or under
+    AC_UPWIND first-order differences on the upstream side of the node (the
+    side the node's u_b comes from: backward where u_b >= 0)."""
+    D = prm.lat.D
+    aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
+    if not prm.use_ac:
+        return aC
+
+    def diff(g, b):
+        if prm.use_ac == AC_UPWIND:
+            back = g - grid.at(g, grid.unit(b, -1))
+            fwd = grid.at(g, grid.unit(b, +1)) - g
+            return np.where(u[b] >= 0.0, back, fwd)
+        return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
+
+    for a in range(D):
+        aC[a][a] = -diff(rho * (u[a] * u[a] * u[a]), a)
+    if prm.use_ac in (AC_FULL, AC_UPWIND):
+        dP = [diff(rho * (1.0 - theta), b) for b in range(D)]
+        for a in range(D):
+            for b in range(D):
+                aC[a][b] = aC[a][b] + CS2 * (u[a] * dP[b] + u[b] * dP[a])
+    return aC
+
+
 def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
     """Sec. 2.2 / App. A collision at every node.
 
@@ -274,19 +314,7 @@ def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
     div = sum(du[a][a] for a in range(D))
     P = rho * (1.0 - theta)
     dPdt = P - P_prev
-    # a^C (reading Q6): c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
-    # P = rho(1-theta), central differences
-    aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
-    if prm.use_ac:
-        def cdiff(g, b):
-            return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
-        for a in range(D):
-            aC[a][a] = -cdiff(rho * (u[a] * u[a] * u[a]), a)
-        if prm.use_ac == AC_FULL:
-            dP = [cdiff(rho * (1.0 - theta), b) for b in range(D)]
-            for a in range(D):
-                for b in range(D):
-                    aC[a][b] = aC[a][b] + CS2 * (u[a] * dP[b] + u[b] * dP[a])
+    aC = lattice_correction(prm, grid, rho, u, theta)
     # Eq. af2
     aF = [[None] * D for _ in range(D)]
     for a in range(D):
