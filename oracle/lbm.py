@@ -43,21 +43,27 @@ design notes of the repository):
       across it (the off-diagonal part), shear viscosity mu at any theta
       and frame, linear stability at low theta.  use_ac: AC_FULL (default),
       AC_CUBIC (the cubic term only: frame-dependent attenuation at
-      theta != 1), AC_OFF, and AC_UPWIND: the AC_FULL terms with first-order
-      one-sided differences taken on the upstream side of the node (the
-      backward difference along b where the node's u_b >= 0, the forward one
-      otherwise).  The paper gives no stencil for a^C.  With central
-      differences a uniform stream faster than the sound speed is linearly
-      unstable: on the odd-even mode along the stream every central
-      difference vanishes, and what is left of the lattice part feeds a
-      density perturbation back through its momentum flux (c^2 - u^2) d rho,
-      whose sign turns at u = c (for a D1Q3 stream at rest temperature
-      theta/3 the mode's eigenvalues solve l^2 - w(1 - 2a) l - (1 - w) = 0,
-      a = theta/3 - u^2, w = 1/tau-bar: a root above 1 exactly when a < 0).
-      One-sided differences see the mode; AC_UPWIND keeps supersonic
-      streams stable (pinned by the Jacobian spectrum of one step).
-  Q7  spatial derivatives are 2nd-order central (those of a^C first-order
-      upstream under AC_UPWIND, Q6); time derivative of
+      theta != 1), AC_OFF, and AC_UPWIND: the AC_FULL terms with each
+      difference along b biased to the upstream side in proportion to the
+      node's Mach number along b (central for a slow component, one-sided at
+      Mach 1, capped at 1.5 times the one-sided bias; lattice_correction).
+      The paper gives no stencil for a^C.  With central differences a
+      uniform stream faster than the sound speed is linearly unstable: on the
+      odd-even mode along the stream every central difference vanishes, and
+      what is left of the lattice part feeds a density perturbation back
+      through its momentum flux (c^2 - u^2) d rho, whose sign turns at u = c
+      (for a D1Q3 stream at temperature theta the mode's eigenvalues solve
+      l^2 - w(1 - 2a) l - (1 - w) = 0, a = theta/3 - u^2, w = 1/tau-bar: a
+      root above 1 exactly when a < 0).  Upstream-biased differences see the
+      mode.  The Mach weighting with the cap 1.5 leaves uniform streams,
+      along an axis and oblique, without growing modes up to Mach 4 while
+      the lattice speed stays below about 0.35 (Mach 3 at theta 0.02, 2.5 at
+      0.05, 4 at 0.01 and below), where a plain one-sided difference lets
+      slowly varying oblique modes grow from Mach 2.5 (caps 1 and 1.25 from
+      Mach 2.5-3, cap 2 from Mach 2 at theta 0.05); pinned by the Jacobian
+      spectrum of one step.
+  Q7  spatial derivatives are 2nd-order central (those of a^C upstream-
+      biased under AC_UPWIND, Q6); time derivative of
       rho(1-theta) is the backward difference with the stored previous value.
   Q8  the F_i(t - dt) term of Eq. pi2 enters through its traceless second
       moment, the stored deviator of a^F of the previous step.
@@ -73,6 +79,11 @@ design notes of the repository):
       velocity in the face value and in eta is the reconstructing cell's.
   Q15 the IB energy forcing f_E = w + q is added once to rho E before the
       fluxes are formed.
+  Q29 artificial bulk viscosity: the paper runs its shock cases with a low
+      artificial bulk viscosity defined in its cited prior work; here a
+      constant mu_b = bulk_ratio mu (default 0) enters the trace of Eq. af2
+      as -2 mu_b div u (central differences), which adds mu_b to the zero
+      bulk viscosity the trace terms give (pinned by sound attenuation).
   Q24 far field: inlet and far-field faces are reset to the free-stream
       equilibrium, the outlet is a zero-gradient copy; stencil reads
       outside a non-periodic axis are clamped to the edge node.
@@ -88,6 +99,8 @@ BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_GHOST, BC_CHAR = 0, 1, 2, 3, 4
 TAU_THETA, TAU_LITERAL = 0, 1
 # a^C readings (Q6): off, the diagonal cubic defect only, full (default)
 AC_OFF, AC_CUBIC, AC_FULL, AC_UPWIND = 0, 1, 2, 3
+# largest upstream weight of the AC_UPWIND differences (reading Q6)
+AC_UPWIND_CAP = 1.5
 
 
 def theta_inf_rule(mach, gamma, reynolds, ref_length, prandtl, dim):
@@ -118,7 +131,8 @@ class Params:
 
     def __init__(self, lattice, shape, mach, reynolds, ref_length, prandtl=0.71,
                  gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98,
-                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=AC_FULL, mu=None, zoff=0):
+                 d_n=1.5, method=IB.FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=AC_FULL, mu=None, zoff=0,
+                 bulk_ratio=0.0):
         self.lat = L.get(lattice)
         D = self.lat.D
         self.shape = tuple(int(s) for s in shape)  # (nx, ny[, nz])
@@ -137,6 +151,8 @@ class Params:
         self.u_inf = self.u_mag * d
         self.mu = self.rho_inf * self.u_mag * ref_length / reynolds if mu is None else float(mu)
         self.lam = self.mu * self.Cp / prandtl
+        # artificial bulk viscosity (reading Q29): mu_b = bulk_ratio mu
+        self.mu_b = float(bulk_ratio) * self.mu
         self.sigma = sigma
         self.d_n = d_n
         self.method = method
@@ -273,20 +289,27 @@ def deviator(lat, T):
 
 def lattice_correction(prm, grid, rho, u, theta):
     """a^C of Eq. af2 (reading Q6): c_s^2 (u_a d_b P + u_b d_a P)
-    - d_ab d_a(rho u_a^3), P = rho(1-theta); central differences, or under
-    AC_UPWIND first-order differences on the upstream side of the node (the
-    side the node's u_b comes from: backward where u_b >= 0)."""
+    - d_ab d_a(rho u_a^3), P = rho(1-theta).  Central differences; under
+    AC_UPWIND each difference along b adds an upstream-biased share of the
+    second difference, D_b g = (g+ - g-)/2 - (alpha_b/2)(g+ - 2g + g-),
+    weighted by the node's Mach number along b,
+    alpha_b = clip(u_b / c, -AC_UPWIND_CAP, AC_UPWIND_CAP), c = sqrt(gamma R T):
+    central where the component is slow, the one-sided difference at
+    alpha = 1, more upstream weight beyond."""
     D = prm.lat.D
     aC = [[np.zeros_like(rho) for _ in range(D)] for _ in range(D)]
     if not prm.use_ac:
         return aC
+    if prm.use_ac == AC_UPWIND:
+        c = np.sqrt(prm.gamma * CS2 * theta)
 
     def diff(g, b):
+        gp = grid.at(g, grid.unit(b, +1))
+        gm = grid.at(g, grid.unit(b, -1))
         if prm.use_ac == AC_UPWIND:
-            back = g - grid.at(g, grid.unit(b, -1))
-            fwd = grid.at(g, grid.unit(b, +1)) - g
-            return np.where(u[b] >= 0.0, back, fwd)
-        return (grid.at(g, grid.unit(b, +1)) - grid.at(g, grid.unit(b, -1))) * 0.5
+            alpha = np.clip(u[b] / c, -AC_UPWIND_CAP, AC_UPWIND_CAP)
+            return 0.5 * (gp - gm) - 0.5 * alpha * (gp - 2.0 * g + gm)
+        return (gp - gm) * 0.5
 
     for a in range(D):
         aC[a][a] = -diff(rho * (u[a] * u[a] * u[a]), a)
@@ -321,7 +344,7 @@ def collide(prm, grid, f, rho, u, theta, fu, P_prev, devAF_prev):
         for b in range(D):
             v = aC[a][b] + fu[a] * u[b] + fu[b] * u[a]
             if a == b:
-                v = v + (2.0 / D) * rho * CS2 * div - CS2 * dPdt
+                v = v + (2.0 / D) * rho * CS2 * div - CS2 * dPdt - (2.0 * prm.mu_b) * div
             aF[a][b] = v
     feq = equilibrium(lat, rho, u, theta)
     # relaxation time (Eq. LB, reading Q9)

@@ -380,3 +380,26 @@ def test_characteristic_far_field_keeps_uniform_flow():
     sim.run(5)
     assert np.abs(sim.f - f0).max() < 1e-15
     assert np.abs(sim.E - E0).max() < 1e-14
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.1])
+def test_bulk_viscosity_sound_attenuation(theta):
+    """Reading Q29: the trace term -2 mu_b div u of a^F adds the bulk
+    viscosity mu_b to the longitudinal viscosity, so a sound wave at rest
+    decays at (1/2)(nu_L + mu_b/rho + (gamma - 1) alpha) k^2."""
+    mu, nx = 0.02, 48
+    base = _sound_rate(theta, 0.0, mu=mu, nx=nx)
+    saved = lbm.Params.__init__
+
+    def init(self, *a, **k):
+        k["bulk_ratio"] = 1.5
+        saved(self, *a, **k)
+    lbm.Params.__init__ = init
+    try:
+        r = _sound_rate(theta, 0.0, mu=mu, nx=nx)
+    finally:
+        lbm.Params.__init__ = saved
+    prm = lbm.Params("D2Q9", (nx, 2), 0.1, 100.0, 10.0, theta_inf=theta, mu=mu)
+    ns = 2.0 * 0.5 * mu + (prm.gamma - 1.0) * prm.lam / prm.Cp
+    expect = (ns + 1.5 * mu) / ns
+    assert abs(r / base - expect) < 0.03 * expect
