@@ -68,6 +68,8 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_INLET = 1, LBM_BC_OUTLET = 2, LBM_BC_FARFIELD
  * as written in Eq. LB (the default; the theta-scaled variant is not stable for
  * theta < 1 and gives a shear viscosity mu/theta) */
 enum { LBM_TAU_THETA = 0, LBM_TAU_LITERAL = 1 };
+/* a^C stencils (use_ac) */
+enum { LBM_AC_OFF = 0, LBM_AC_CUBIC = 1, LBM_AC_CENTRAL = 2, LBM_AC_UPWIND = 3 };
 /* temperature condition at a Lagrangian point (velocity is always Dirichlet) */
 enum { IB_T_DIRICHLET = 0, IB_T_NEUMANN = 1 };
 /* body shape used to classify Eulerian nodes as inside (Omega') or not */
@@ -91,9 +93,15 @@ typedef struct {
   int bc[6];               /* LBM_BC_* per face */
   int tau_mode;            /* LBM_TAU_LITERAL (default) or LBM_TAU_THETA */
   int use_ac;              /* a^C of Eq. af2: 2 = c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
-                              P = rho(1-theta) (default); 1 = the cubic part only; 0 = none */
+                              P = rho(1-theta), central differences (default); 3 = the same terms with
+                              first-order differences on the upstream side of each node (needed for
+                              streams faster than the sound speed, which central differences leave
+                              unstable); 1 = the cubic part only; 0 = none */
   int device;              /* CUDA device ordinal */
   void* stream;            /* cudaStream_t, or NULL */
+  double bulk_ratio;       /* artificial bulk viscosity mu_b = bulk_ratio * mu (default 0: the zero bulk
+                              viscosity of the trace terms of Eq. af2), added to the trace of a^F as
+                              -2 mu_b div u; >= 0 */
 } lbm_config;
 
 typedef struct {

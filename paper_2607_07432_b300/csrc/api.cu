@@ -97,6 +97,7 @@ lbm_status lbm_config_default(lbm_config* c) {
   c->method = IB_FODIBM_R;
   c->tau_mode = LBM_TAU_LITERAL;
   c->use_ac = 2;
+  c->bulk_ratio = 0.0;
   return LBM_OK;
 }
 
@@ -118,7 +119,7 @@ lbm_status create_impl(const lbm_config* cfg, const SlabSpec* slab, lbm_handle**
       (D == 3 && cfg->nz < 3) || (D == 2 && cfg->nz != 1) || cfg->mach <= 0 || cfg->reynolds <= 0 ||
       cfg->ref_length <= 0 || cfg->gamma <= 1.0 || cfg->prandtl <= 0 || cfg->precision < 0 ||
       cfg->precision > LBM_BF16DEV || cfg->method < IB_DIBM || cfg->method > IB_FODIBM_R || cfg->use_ac < 0 ||
-      cfg->use_ac > 2)
+      cfg->use_ac > 3 || !(cfg->bulk_ratio >= 0.0) || !std::isfinite(cfg->bulk_ratio))
     return LBM_EINVAL;
   bool has_char = false, has_outlet = false;
   for (int f = 0; f < 2 * D; ++f) {

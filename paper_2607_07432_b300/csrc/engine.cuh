@@ -28,6 +28,8 @@ struct Engine {
     p.sigma = C(h->cfg.sigma_hrr);
     p.theta_tau = h->cfg.tau_mode == LBM_TAU_THETA ? 1 : 0;
     p.use_ac = h->cfg.use_ac;
+    p.gcs2 = C(h->cfg.gamma * kCs2);
+    p.mub2 = C(2.0 * (h->cfg.bulk_ratio * h->mu));
     return p;
   }
   static lbm_status reset_aux(lbm_handle* h) {

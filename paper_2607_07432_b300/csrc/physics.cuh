@@ -14,6 +14,8 @@ namespace lbmib {
 template <class C>
 struct Phys {
   C cs2, Cv, Cp, mu, lam, sigma;
+  C gcs2;         // gamma c_s^2: the squared sound speed over theta
+  C mub2;         // twice the artificial bulk viscosity mu_b
   int theta_tau;  // 1: tau_LB = mu / (rho c_s^2 theta)
   int use_ac;
 };
@@ -65,18 +67,30 @@ __device__ __forceinline__ C feq_i(C rho, const C* u, C th) {
   return C(wi) * (rho + tth + t1 + t2 + t3);
 }
 
+// Largest upstream weight of the a^C differences under use_ac = 3.
+constexpr double kAcUpwindCap = 1.5;
+
 // Velocity gradient du[a][b] = d u_a / d x_b and a^C, the lattice-dependent
 // part of Eq. af2 (only cited by the paper), read from the Chapman-Enskog
 // expansion of the lattice's third moment:
 //   a^C_ab = c_s^2 (u_a d_b P + u_b d_a P) - d_ab d_a(rho u_a^3),
 // P = rho(1-theta) (use_ac = 2; use_ac = 1 keeps the cubic part only,
-// 0 none).  Central differences; MacroAt(dx,dy,dz) returns the neighbour's
-// Macro, uc is the node's own velocity.  In FP64 the operations follow the
-// oracle's order.
+// 0 none).  Central differences, except for a^C under use_ac = 3: each
+// difference along b leans to the node's upstream side in proportion to its
+// Mach number along b, D_b g = (g+ - g-)/2 - (alpha_b/2)(g+ - 2g + g-),
+// alpha_b = clamp(u_b / c, -kAcUpwindCap, kAcUpwindCap), c^2 = gamma c_s^2
+// theta, which keeps streams faster than the sound speed stable (central
+// differences cannot see their growing odd-even mode).  MacroAt(dx,dy,dz)
+// returns the neighbour's Macro, mc is the node's own.  In FP64 the
+// operations follow the oracle's order.
 template <class L, class C, class MacroAt>
-__device__ __forceinline__ void gradients(const MacroAt& M, const C* uc, C du[3][3], C aC[3][3], int use_ac) {
+__device__ __forceinline__ void gradients(const MacroAt& M, const Macro<C>& mc, C du[3][3], C aC[3][3],
+                                          int use_ac, C gcs2) {
   constexpr int D = L::D;
+  const C* uc = mc.u;
   C dP[3];
+  C c = C(1);
+  if (use_ac == 3) c = sqrt(gcs2 * mc.th);
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     const Macro<C> p = M(b == 0 ? 1 : 0, b == 1 ? 1 : 0, b == 2 ? 1 : 0);
@@ -86,11 +100,25 @@ __device__ __forceinline__ void gradients(const MacroAt& M, const C* uc, C du[3]
       du[a][b] = (p.u[a] - m.u[a]) * C(0.5);
       aC[a][b] = C(0);
     }
-    if (use_ac)
-      aC[b][b] = -((p.rho * (p.u[b] * p.u[b] * p.u[b]) - m.rho * (m.u[b] * m.u[b] * m.u[b])) * C(0.5));
-    dP[b] = (p.rho * (C(1) - p.th) - m.rho * (C(1) - m.th)) * C(0.5);
+    const C gp = p.rho * (p.u[b] * p.u[b] * p.u[b]);
+    const C gm = m.rho * (m.u[b] * m.u[b] * m.u[b]);
+    const C Pp = p.rho * (C(1) - p.th);
+    const C Pm = m.rho * (C(1) - m.th);
+    if (use_ac == 3) {
+      // comparisons keep a NaN weight NaN, as the oracle's clip does
+      C al = uc[b] / c;
+      al = al > C(kAcUpwindCap) ? C(kAcUpwindCap) : (al < C(-kAcUpwindCap) ? C(-kAcUpwindCap) : al);
+      const C hw = C(0.5) * al;
+      const C g0 = mc.rho * (uc[b] * uc[b] * uc[b]);
+      const C P0 = mc.rho * (C(1) - mc.th);
+      aC[b][b] = -(C(0.5) * (gp - gm) - hw * (gp - C(2) * g0 + gm));
+      dP[b] = C(0.5) * (Pp - Pm) - hw * (Pp - C(2) * P0 + Pm);
+    } else {
+      if (use_ac) aC[b][b] = -((gp - gm) * C(0.5));
+      dP[b] = (Pp - Pm) * C(0.5);
+    }
   }
-  if (use_ac == 2) {
+  if (use_ac >= 2) {
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -149,7 +177,7 @@ __device__ __forceinline__ void collide(const C* fbar, const Macro<C>& m, const 
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       C v = aC[a][b] + fu[a] * m.u[b] + fu[b] * m.u[a];
-      if (a == b) v = v + (C(2) / C(D)) * m.rho * cs2 * div - cs2 * dPdt;
+      if (a == b) v = v + (C(2) / C(D)) * m.rho * cs2 * div - cs2 * dPdt - ph.mub2 * div;
       aF[a][b] = v;
     }
   C feq[Q];
@@ -259,7 +287,7 @@ __device__ __forceinline__ void collide_fast(const C* fbar, const Macro<C>& m, c
   for (int a = 0; a < D; ++a) div += du[a][a];
   const C P = m.rho * (C(1) - m.th);
   const C dPdt = P - P_prev;
-  const C trace_term = (C(2) / C(D)) * m.rho * cs2 * div - cs2 * dPdt;
+  const C trace_term = (C(2) / C(D)) * m.rho * cs2 * div - cs2 * dPdt - ph.mub2 * div;
   C aF[3][3];
 #pragma unroll
   for (int a = 0; a < D; ++a)

@@ -272,7 +272,7 @@ __device__ __forceinline__ void fused_body(const Grid& g, const FusedArgs<S, C>&
     auto MA = [&](int dx, int dy, int dz) { return macro_at(z + dz, hx + dx, hy + dy); };
     const Macro<C> m = macro_at(z, hx, hy);
     C du[3][3], aC[3][3];
-    gradients<L, C>(MA, m.u, du, aC, ph.use_ac);
+    gradients<L, C>(MA, m, du, aC, ph.use_ac, ph.gcs2);
     C fbar[Q];
     C dAFp[L::NDEV];
     C Pp;

@@ -19,6 +19,7 @@ FP64, FP32, FP16DEV, BF16DEV = 0, 1, 2, 3
 DIBM, FODIBM, FODIBM_R = 0, 1, 2
 BC_PERIODIC, BC_INLET, BC_OUTLET, BC_FARFIELD, BC_CHAR = 0, 1, 2, 3, 5
 TAU_THETA, TAU_LITERAL = 0, 1
+AC_OFF, AC_CUBIC, AC_CENTRAL, AC_UPWIND = 0, 1, 2, 3
 SHAPE_SPHERE, SHAPE_ELLIPSE, SHAPE_POLYGON, SHAPE_MASK = 0, 1, 2, 3
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EGEOM",
           5: "LBM_ENAN", 6: "LBM_ETIMEOUT", 7: "LBM_ESTATE", 8: "LBM_EUNSUPPORTED"}
@@ -43,7 +44,7 @@ class Config(ct.Structure):
                 ("gamma", ct.c_double), ("theta_inf", ct.c_double), ("inflow_dir", ct.c_double * 3),
                 ("sigma_hrr", ct.c_double), ("d_n", ct.c_double), ("method", ct.c_int),
                 ("bc", ct.c_int * 6), ("tau_mode", ct.c_int), ("use_ac", ct.c_int), ("device", ct.c_int),
-                ("stream", ct.c_void_p)]
+                ("stream", ct.c_void_p), ("bulk_ratio", ct.c_double)]
 
 
 class Geometry(ct.Structure):
@@ -112,7 +113,7 @@ def _ptr(a):
 
 
 def _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamma, theta_inf, inflow_dir, sigma,
-            d_n, method, bc, tau_mode, use_ac, device, stream):
+            d_n, method, bc, tau_mode, use_ac, device, stream, bulk_ratio=0.0):
     cfg = Config()
     lib().lbm_config_default(ct.byref(cfg))
     D = 2 if lattice in ("D2Q9", D2Q9) else 3
@@ -130,6 +131,7 @@ def _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamm
         cfg.bc[k] = int(bc[k]) if k < len(bc) else BC_PERIODIC
     cfg.tau_mode, cfg.use_ac, cfg.device = int(tau_mode), int(use_ac), int(device)
     cfg.stream = ct.c_void_p(stream) if stream else None
+    cfg.bulk_ratio = float(bulk_ratio)
     return cfg
 
 
@@ -139,12 +141,12 @@ class Solver:
     def __init__(self, lattice="D2Q9", precision="fp32", shape=(64, 64), mach=0.1, reynolds=100.0,
                  ref_length=10.0, prandtl=0.71, gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0),
                  sigma=0.98, d_n=1.5, method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=2,
-                 device=0, stream=None, slab=None):
+                 device=0, stream=None, slab=None, bulk_ratio=0.0):
         """slab = (z0, z1, halo): a z slab of the case (lbm_create_slab); shape
         is then the global grid."""
         L = lib()
         cfg = _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamma, theta_inf,
-                      inflow_dir, sigma, d_n, method, bc, tau_mode, use_ac, device, stream)
+                      inflow_dir, sigma, d_n, method, bc, tau_mode, use_ac, device, stream, bulk_ratio)
         self.D = 2 if lattice in ("D2Q9", D2Q9) else 3
         self.Q = 9 if self.D == 2 else 19
         self.cfg = cfg
@@ -400,10 +402,10 @@ class Refined:
 
     def __init__(self, lattice, precision, shape, box_lo, box_hi, mach=0.1, reynolds=100.0, ref_length=10.0,
                  prandtl=0.71, gamma=1.4, theta_inf=0.0, inflow_dir=(1.0, 0.0, 0.0), sigma=0.98, d_n=1.5,
-                 method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=2, device=0, stream=None):
+                 method=FODIBM_R, bc=None, tau_mode=TAU_LITERAL, use_ac=2, device=0, stream=None, bulk_ratio=0.0):
         L = lib()
         self.cfg = _config(lattice, precision, shape, mach, reynolds, ref_length, prandtl, gamma, theta_inf,
-                           inflow_dir, sigma, d_n, method, bc, tau_mode, use_ac, device, stream)
+                           inflow_dir, sigma, d_n, method, bc, tau_mode, use_ac, device, stream, bulk_ratio)
         D = 2 if lattice in ("D2Q9", D2Q9) else 3
         lo = (ct.c_int * 3)(*[int(v) for v in (list(box_lo) + [0, 0])[:3]])
         hi = (ct.c_int * 3)(*[int(v) for v in (list(box_hi) + [0, 0])[:3]])

@@ -257,3 +257,27 @@ def test_rotating_cylinder_with_heat_flux_fp64_parity():
     wl = g.wall_loads(per_point=True)
     assert np.max(np.abs(wl["F"] - sim.last_loads["F"])) < 1e-12 * max(1.0, np.abs(sim.last_loads["F"]).max())
     g.close()
+
+
+@pytest.mark.parametrize("zc", ["4", "7", "13"])
+def test_z_chunk_length_does_not_change_the_state(zc, monkeypatch):
+    """The planes per CTA of the 3D fused step (LBMIB_ZCHUNK; chosen from
+    the grid and SM count otherwise) only partition the work: every chunk
+    length, including ones that leave a ragged last chunk, gives the default
+    state bit for bit (body, far-field boundaries, FP32)."""
+    from paper_2607_07432_b300 import inputs, lbmib
+    out = []
+    for val in (None, zc):
+        if val is None:
+            monkeypatch.delenv("LBMIB_ZCHUNK", raising=False)
+        else:
+            monkeypatch.setenv("LBMIB_ZCHUNK", val)
+        s = lbmib.Solver("D3Q19", "fp32", (40, 24, 30), mach=0.3, reynolds=100.0, ref_length=8.0,
+                         bc=[C.BC_IN, C.BC_OUT, C.BC_FF, C.BC_FF, C.BC_FF, C.BC_FF])
+        th = s.constants()["theta_inf"]
+        s.set_geometry(inputs.icosphere((12.3, 12.1, 14.8), 8.0, 4, tbc=0, t_value=1.05 * th))
+        s.step(9)
+        out.append(s.state())
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
