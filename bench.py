@@ -551,6 +551,161 @@ def run_refined_sphere(args):
     print(json.dumps(line), flush=True)
 
 
+def run_supersonic(args):
+    """High-Mach operating points with the Mach-weighted upstream a^C stencil
+    (LBM_AC_UPWIND), FP32:
+    (1) a seeded uniform Mach 2 stream (theta 0.02, periodic 256x128,
+        populations with 1e-3 relative noise): growth of the density deviation
+        with the central stencil (20 steps) and with LBM_AC_UPWIND (5000 steps);
+    (2) NACA0012 at Mach 0.8, Re 500, 10 degrees (chord 100, 1024x512, inlet
+        and characteristic faces, theta 0.1, impulsive start): C_d and C_l,
+        running means over the last 10 000 of 30 000 steps;
+    (3) the adiabatic sphere at Mach 1.2, Re 300 (D = `--sup-sphere-d`, grid
+        12D x 8D x 8D, theta 0.02, bulk viscosity 3 mu): Mach ramp from 0.3 in
+        8 restarts of 1500 steps, then 30 000 steps; C_d (mean over the last
+        7500) and the shock stand-off on the axis;
+    (4) the adiabatic cylinder at Mach 2, Re 300 (D = `--sup-d`, domain
+        [-10D, 30D] x [-10D, 10D], theta `--sup-theta`, bulk viscosity
+        `--sup-bulk` mu): Mach ramp from 0.5 in 16 restarts of 2000 steps, then
+        `--sup-steps` steps with a health check every 2000; C_d and stand-off
+        every 10 000 steps and the step at which a check fails, if one does.
+    The stand-off is the distance from the stagnation point to where p / p_inf
+    first reaches the normal-shock ratio upstream of it."""
+    from paper_2607_07432_b300 import inputs, lbmib
+    out = {}
+    g = 1.4
+    CH = lbmib.BC_CHAR
+    for name, ac, steps in (("central", lbmib.AC_CENTRAL, 20), ("mach_weighted", lbmib.AC_UPWIND, 5000)):
+        s = lbmib.Solver("D2Q9", "fp32", (256, 128), mach=2.0, reynolds=300.0, ref_length=20.0, theta_inf=0.02,
+                         bc=[0] * 4, use_ac=ac)
+        f0, E0 = s.state()          # the uniform free stream the case starts from
+        rng = np.random.Generator(np.random.PCG64(7))
+        s.set_state(f0 * (1.0 + 1e-3 * rng.standard_normal(f0.shape)), E0)
+        rho = s.fields()[0]
+        d0 = float(np.abs(rho - rho.mean()).max())
+        s.step(steps)
+        rho = s.fields()[0]
+        out["stream_" + name] = {"steps": steps, "deviation_ratio": float(np.abs(rho - rho.mean()).max()) / d0}
+        s.close()
+
+    def standoff(p_line, x_stag, pinf, mach):
+        """Stand-off (cells) from x_stag to where the pressure line (along +x)
+        first reaches the normal-shock ratio going upstream."""
+        row = p_line / pinf
+        ps = 2 * g / (g + 1) * mach * mach - (g - 1) / (g + 1)
+        x0 = int(np.floor(x_stag))
+        for x in range(x0, 0, -1):
+            if row[x - 1] < ps <= row[x]:
+                return x_stag - (x - 1 + (ps - row[x - 1]) / (row[x] - row[x - 1]))
+        return float("nan")
+
+    def ramp_run(make, mach, stages, per, final, m0, chunk, sample):
+        """Restarts at Mach numbers from m0 to mach (fixed theta and mu), then
+        `final` steps at mach with a check every `chunk` steps; sample(s, k)
+        is called after each chunk of the last stage."""
+        state, done, failed = None, 0, None
+        machs = [mach] if stages == 1 else list(np.linspace(m0, mach, stages))
+        for k, m in enumerate(machs):
+            s = make(float(m))
+            if state is not None:
+                s.set_state(*state)
+            n = per if k < len(machs) - 1 else final
+            for j in range(n // chunk):
+                s.step(chunk)
+                done += chunk
+                try:
+                    s.check()
+                except lbmib.LBMError:
+                    failed = done
+                    break
+                if k == len(machs) - 1:
+                    sample(s, (j + 1) * chunk)
+            if failed is not None or k == len(machs) - 1:
+                s.close()
+                return done, failed
+            state = s.state()
+            s.close()
+
+    # (2) NACA0012, Mach 0.8, Re 500, 10 degrees
+    t0 = time.perf_counter()
+    a = np.deg2rad(10.0)
+    hist = []
+
+    def naca(m):
+        s = lbmib.Solver("D2Q9", "fp32", (1024, 512), mach=m, reynolds=500.0, ref_length=100.0, theta_inf=0.1,
+                         bc=[lbmib.BC_INLET, CH, CH, CH], inflow_dir=(np.cos(a), np.sin(a), 0.0),
+                         use_ac=lbmib.AC_UPWIND)
+        s.set_geometry(inputs.naca0012((300.0, 256.0), 100.0, 256, tbc=1, t_value=0.0))
+        return s
+
+    def naca_sample(s, k):
+        if k > 20000:
+            d = s.wall_diagnostics(per_point=False)
+            hist.append((d["Cd"], d["Cl"]))
+    done, failed = ramp_run(naca, 0.8, 1, 0, 30000, 0.8, 100, naca_sample)
+    h = np.array(hist) if hist else np.full((1, 2), np.nan)
+    out["naca0012_mach0.8"] = {"Cd": float(h[:, 0].mean()), "Cl": float(h[:, 1].mean()), "steps": done,
+                               "failed_at_step": failed, "wall_s": time.perf_counter() - t0,
+                               "paper_FODIBM_R": {"Cd": 0.2638, "Cl": 0.4196}}
+
+    # (3) sphere, Mach 1.2, Re 300
+    t0 = time.perf_counter()
+    Ds, ths = args.sup_sphere_d, 0.02
+    sh = (12 * Ds, 8 * Ds, 8 * Ds)
+    hist, last = [], {}
+
+    def sph(m):
+        s = lbmib.Solver("D3Q19", "fp32", sh, mach=m, reynolds=300.0 * m / 1.2, ref_length=float(Ds), theta_inf=ths,
+                         bc=[lbmib.BC_INLET] + [CH] * 5, use_ac=lbmib.AC_UPWIND, bulk_ratio=3.0)
+        s.set_geometry(inputs.icosphere((3.0 * Ds, 4.0 * Ds, 4.0 * Ds), float(Ds), 16, tbc=1, t_value=0.0))
+        return s
+
+    def sph_sample(s, k):
+        if k > 22500:
+            hist.append(s.wall_diagnostics(per_point=False)["Cd"])
+        if k == 30000:
+            _, _, _, p = s.fields()
+            last["standoff_D"] = standoff(p[4 * Ds, 4 * Ds], 2.5 * Ds, ths / 3.0, 1.2) / Ds
+    done, failed = ramp_run(sph, 1.2, 8, 1500, 30000, 0.3, 1500, sph_sample)
+    out["sphere_mach1.2"] = {"Cd": float(np.mean(hist)) if hist else float("nan"),
+                             "standoff_D": last.get("standoff_D", float("nan")), "D": Ds, "steps": done,
+                             "failed_at_step": failed, "wall_s": time.perf_counter() - t0,
+                             "paper_FODIBM_R": {"Cd": 1.287, "standoff_D": 0.678}}
+
+    # (4) cylinder, Mach 2, Re 300
+    t0 = time.perf_counter()
+    D, th, bulk = args.sup_d, args.sup_theta, args.sup_bulk
+    nx, ny, xc = 40 * D, 20 * D, 10.0 * D
+    yc = ny / 2.0
+    hist = []
+
+    def cyl(m):
+        s = lbmib.Solver("D2Q9", "fp32", (nx, ny), mach=m, reynolds=300.0 * m / 2.0, ref_length=float(D),
+                         theta_inf=th, bc=[lbmib.BC_INLET, CH, CH, CH], use_ac=lbmib.AC_UPWIND, bulk_ratio=bulk)
+        s.set_geometry(inputs.cylinder((xc, yc), float(D), int(np.pi * D), tbc=1, t_value=0.0))
+        return s
+
+    def cyl_sample(s, k):
+        if k % 10000 == 0:
+            d = s.wall_diagnostics(per_point=False)
+            _, _, _, p = s.fields()
+            hist.append({"steps_at_mach2": k, "Cd": float(d["Cd"]),
+                         "standoff_D": standoff(p[int(round(yc))], xc - D / 2.0, th / 3.0, 2.0) / D})
+    done, failed = ramp_run(cyl, 2.0, 16, 2000, args.sup_steps, 0.5, 2000, cyl_sample)
+    out["cylinder_mach2"] = {"history": hist, "failed_at_step": failed, "ramp_steps": 15 * 2000, "D": D,
+                             "wall_s": time.perf_counter() - t0, "paper_FODIBM_R": {"Cd": 1.57, "standoff_D": 0.71}}
+    line = {"metric": "high-Mach operating points: uniform-stream stability, NACA0012 at Mach 0.8, sphere at "
+                      "Mach 1.2, cylinder at Mach 2",
+            "value": out["sphere_mach1.2"]["Cd"], "unit": "C_d (sphere, Mach 1.2)", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Mach 2 uniform stream 256x128; NACA0012 Ma 0.8 Re 500 10 deg chord 100 "
+                                   "(1024x512); sphere Ma 1.2 Re 300 D = %d (%dx%dx%d); cylinder Ma 2 Re 300 "
+                                   "D = %d (%dx%d), theta_inf %.3f, bulk viscosity %.1f mu"
+                                   % (Ds, sh[0], sh[1], sh[2], D, nx, ny, th, bulk)},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
     isothermal wall): C_d and Nu as running means, and the steps until the
@@ -867,7 +1022,7 @@ def main():
                     help="skip the FP16 / BF16 storage and 64-case batch sub-records")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
                                                                     "convergence", "rotsphere", "refined",
-                                                                    "refined_sphere"])
+                                                                    "refined_sphere", "supersonic"])
     ap.add_argument("--ref-steps", type=int, default=40000)
     ap.add_argument("--ref-lo", type=int, nargs=2, default=[30, 20])
     ap.add_argument("--ref-hi", type=int, nargs=2, default=[150, 80])
@@ -876,6 +1031,11 @@ def main():
     ap.add_argument("--rot-d", type=int, default=48, help="sphere diameter in cells (grid 10D x 6D x 6D)")
     ap.add_argument("--rot-noise", type=float, default=0.01)
     ap.add_argument("--rot-omegas", default="0.3,0.6")
+    ap.add_argument("--sup-d", type=int, default=60, help="cylinder diameter in cells (Mach 2 workload)")
+    ap.add_argument("--sup-theta", type=float, default=0.02)
+    ap.add_argument("--sup-bulk", type=float, default=3.0, help="artificial bulk viscosity over mu")
+    ap.add_argument("--sup-steps", type=int, default=40000, help="steps at Mach 2 after the ramp")
+    ap.add_argument("--sup-sphere-d", type=int, default=32, help="sphere diameter in cells (Mach 1.2)")
     ap.add_argument("--prec-steps-small", type=int, default=20000)
     ap.add_argument("--prec-steps-full", type=int, default=40000)
     ap.add_argument("--ws-cases", type=int, default=256)
@@ -897,6 +1057,8 @@ def main():
         return run_precision(args)
     if args.workload == "convergence":
         return run_convergence(args)
+    if args.workload == "supersonic":
+        return run_supersonic(args)
     if args.workload == "rotsphere":
         return run_rotsphere(args)
     if args.workload == "refined":
