@@ -706,6 +706,78 @@ def run_supersonic(args):
     print(json.dumps(line), flush=True)
 
 
+def run_airfoil(args):
+    """The NACA0012 airfoil case at full size: chord 400 cells, 1024
+    Lagrangian points, grid 2048x1024 (leading edge at (512, 512); 5.1 x 2.6
+    chords), Re 5000, Mach 0.5 and 0.8 at angles of attack 0, 2.5 and 5
+    degrees, adiabatic wall, inlet and characteristic faces, theta_inf from
+    the built-in rule at Mach 0.5 (0.193) and 0.05 at Mach 0.8 (the rule's
+    0.075 diverges there within 2000 steps), the Mach-weighted upstream a^C
+    stencil (LBM_AC_UPWIND), FP32, uniform start.  Per case: C_d and C_l as means over the last 5 of
+    `--af-chords` chord flow-through times (spread = largest deviation from
+    the mean), the wall C_p extremes and the chordwise position of the upper
+    surface's C_p minimum at the end, and the MLUPS of 2000 timed steps."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    chord, nx, ny, le = 400.0, 2048, 1024, (512.0, 512.0)
+    geo = inputs.naca0012(le, chord, 1024, tbc=1, t_value=0.0)
+    out = {}
+    for mach in (0.5, 0.8):
+        for aoa in (0.0, 2.5, 5.0):
+            a = np.deg2rad(aoa)
+            s = lbmib.Solver("D2Q9", "fp32", (nx, ny), mach=mach, reynolds=5000.0, ref_length=chord,
+                             theta_inf=0.0 if mach < 0.6 else 0.05,
+                             bc=[lbmib.BC_INLET] + [lbmib.BC_CHAR] * 3, inflow_dir=(np.cos(a), np.sin(a), 0.0),
+                             use_ac=lbmib.AC_UPWIND)
+            s.set_geometry(geo)
+            per_chord = int(chord / s.constants()["u_mag"])
+            every = 200
+            n_total = args.af_chords * per_chord // every * every
+            n_avg = 5 * per_chord // every
+            s.step(200)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.step(2000)
+            torch.cuda.synchronize()
+            mlups = nx * ny * 2000 / (time.perf_counter() - t0) / 1e6
+            hist = []
+            for _ in range((n_total - 2200) // every):
+                s.step(every)
+                d = s.wall_diagnostics(per_point=False)
+                hist.append((d["Cd"], d["Cl"]))
+            s.check()
+            d = s.wall_diagnostics(per_point=True)
+            h = np.array(hist[-n_avg:])
+            cp = d["Cp"]
+            out["Ma%.1f_aoa%.1f" % (mach, aoa)] = {
+                "Cd": float(h[:, 0].mean()), "Cl": float(h[:, 1].mean()),
+                "Cd_spread": float(np.abs(h[:, 0] - h[:, 0].mean()).max()),
+                "Cl_spread": float(np.abs(h[:, 1] - h[:, 1].mean()).max()),
+                "Cp_min": float(cp.min()), "Cp_max": float(cp.max()),
+                "upper_Cp_min_at_x_over_c": _upper_cp_min(geo, cp, le, chord),
+                "steps": n_total, "mlups_fp32": mlups}
+            s.close()
+    line = {"metric": "NACA0012 at full size (chord 400, 2048x1024): C_d, C_l and wall C_p over Mach 0.5 / 0.8 "
+                      "and angle of attack 0-5 deg",
+            "value": out["Ma0.8_aoa2.5"]["Cl"], "unit": "C_l (Mach 0.8, 2.5 deg)", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "NACA0012 chord 400, 1024 points, 2048x1024, Re 5000, adiabatic, theta_inf 0.193 "
+                                   "(Ma 0.5) / 0.05 (Ma 0.8), LBM_AC_UPWIND, %d chord flow-throughs" % args.af_chords},
+            "cases": out}
+    print(json.dumps(line), flush=True)
+
+
+def _upper_cp_min(geo, cp, le, chord):
+    """x/c of the smallest C_p among the Lagrangian points above the chord
+    line (y > leading-edge y)."""
+    X = np.asarray(geo.X if hasattr(geo, "X") else geo["X"], dtype=np.float64).reshape(len(cp), -1)
+    up = X[:, 1] > le[1]
+    if not up.any():
+        return float("nan")
+    i = np.argmin(np.where(up, cp, np.inf))
+    return float((X[i, 0] - le[0]) / chord)
+
+
 def run_precision(args):
     """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
     isothermal wall): C_d and Nu as running means, and the steps until the
@@ -1022,7 +1094,7 @@ def main():
                     help="skip the FP16 / BF16 storage and 64-case batch sub-records")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
                                                                     "convergence", "rotsphere", "refined",
-                                                                    "refined_sphere", "supersonic"])
+                                                                    "refined_sphere", "supersonic", "airfoil"])
     ap.add_argument("--ref-steps", type=int, default=40000)
     ap.add_argument("--ref-lo", type=int, nargs=2, default=[30, 20])
     ap.add_argument("--ref-hi", type=int, nargs=2, default=[150, 80])
@@ -1031,6 +1103,7 @@ def main():
     ap.add_argument("--rot-d", type=int, default=48, help="sphere diameter in cells (grid 10D x 6D x 6D)")
     ap.add_argument("--rot-noise", type=float, default=0.01)
     ap.add_argument("--rot-omegas", default="0.3,0.6")
+    ap.add_argument("--af-chords", type=int, default=15, help="chord flow-through times per airfoil case")
     ap.add_argument("--sup-d", type=int, default=60, help="cylinder diameter in cells (Mach 2 workload)")
     ap.add_argument("--sup-theta", type=float, default=0.02)
     ap.add_argument("--sup-bulk", type=float, default=3.0, help="artificial bulk viscosity over mu")
@@ -1059,6 +1132,8 @@ def main():
         return run_convergence(args)
     if args.workload == "supersonic":
         return run_supersonic(args)
+    if args.workload == "airfoil":
+        return run_airfoil(args)
     if args.workload == "rotsphere":
         return run_rotsphere(args)
     if args.workload == "refined":
