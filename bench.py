@@ -778,6 +778,64 @@ def _upper_cp_min(geo, cp, le, chord):
     return float((X[i, 0] - le[0]) / chord)
 
 
+def run_precision_mach12(args):
+    """Reduced-precision storage on the 3D sphere at Mach 1.2 (Re 300,
+    isothermal wall 1.1 T_inf, 256x192x192, D = 48 centred at (100, 96, 96),
+    inlet and characteristic faces, theta_inf 0.02, the Mach-weighted a^C
+    stencil, bulk viscosity 3 mu).  The FP32 path ramps the Mach number from
+    0.3 to 1.2 in 8 restarts of 1500 steps and runs `--p12-settle` steps at
+    Mach 1.2; from that state FP32, FP16 and BF16 storage each run
+    `--p12-steps` steps, and C_d and Nu are averaged over the last half."""
+    import torch
+    from paper_2607_07432_b300 import inputs, lbmib
+    shape, D, center = SHAPE, 48.0, (100.0, 96.0, 96.0)
+    CH = lbmib.BC_CHAR
+    th = 0.02
+
+    def make(prec, m):
+        s = lbmib.Solver("D3Q19", prec, shape, mach=m, reynolds=300.0 * m / 1.2, ref_length=D, theta_inf=th,
+                         bc=[lbmib.BC_INLET] + [CH] * 5, use_ac=lbmib.AC_UPWIND, bulk_ratio=3.0)
+        s.set_geometry(inputs.icosphere(center, D, 27, tbc=0, t_value=1.1 * th))
+        return s
+
+    t0 = time.perf_counter()
+    state = None
+    for k, m in enumerate(np.linspace(0.3, 1.2, 8)):
+        s = make("fp32", float(m))
+        if state is not None:
+            s.set_state(*state)
+        s.step(1500 if k < 7 else args.p12_settle)
+        s.check()
+        state = s.state()
+        s.close()
+    ramp_s = time.perf_counter() - t0
+    res = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        s = make(prec, 1.2)
+        s.set_state(*state)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        cd, nu = coefficient_history(s, args.p12_steps, 50)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t1
+        s.check()
+        s.close()
+        h = len(cd) // 2
+        res[prec] = {"Cd": float(np.mean(cd[h:])), "Nu": float(np.mean(nu[h:])), "wall_s": el,
+                     "mlups": float(np.prod(shape)) * args.p12_steps / el / 1e6}
+    for prec, r in res.items():
+        r["Cd_rel_vs_fp32"] = r["Cd"] / res["fp32"]["Cd"] - 1.0
+        r["Nu_rel_vs_fp32"] = r["Nu"] / res["fp32"]["Nu"] - 1.0
+    line = {"metric": "C_d and Nu by storage form, 3D sphere at Mach 1.2 (Re 300, 256x192x192)",
+            "value": res["bf16"]["Cd_rel_vs_fp32"], "unit": "relative C_d vs FP32 (BF16)", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32 / f16 / bf16 storage, f32 math", "data": "synthetic",
+            "config": {"workload": "3D sphere D3Q19 Ma 1.2 Re 300 D = 48, isothermal wall 1.1 T_inf, theta_inf 0.02, "
+                                   "LBM_AC_UPWIND, bulk viscosity 3 mu; ramp %.1f s; %d settle + %d steps per form"
+                                   % (ramp_s, args.p12_settle, args.p12_steps)},
+            "forms": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
     isothermal wall): C_d and Nu as running means, and the steps until the
@@ -1094,7 +1152,8 @@ def main():
                     help="skip the FP16 / BF16 storage and 64-case batch sub-records")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
                                                                     "convergence", "rotsphere", "refined",
-                                                                    "refined_sphere", "supersonic", "airfoil"])
+                                                                    "refined_sphere", "supersonic", "airfoil",
+                                                                    "precision_mach12"])
     ap.add_argument("--ref-steps", type=int, default=40000)
     ap.add_argument("--ref-lo", type=int, nargs=2, default=[30, 20])
     ap.add_argument("--ref-hi", type=int, nargs=2, default=[150, 80])
@@ -1103,6 +1162,8 @@ def main():
     ap.add_argument("--rot-d", type=int, default=48, help="sphere diameter in cells (grid 10D x 6D x 6D)")
     ap.add_argument("--rot-noise", type=float, default=0.01)
     ap.add_argument("--rot-omegas", default="0.3,0.6")
+    ap.add_argument("--p12-settle", type=int, default=12000)
+    ap.add_argument("--p12-steps", type=int, default=16000)
     ap.add_argument("--af-chords", type=int, default=15, help="chord flow-through times per airfoil case")
     ap.add_argument("--sup-d", type=int, default=60, help="cylinder diameter in cells (Mach 2 workload)")
     ap.add_argument("--sup-theta", type=float, default=0.02)
@@ -1134,6 +1195,8 @@ def main():
         return run_supersonic(args)
     if args.workload == "airfoil":
         return run_airfoil(args)
+    if args.workload == "precision_mach12":
+        return run_precision_mach12(args)
     if args.workload == "rotsphere":
         return run_rotsphere(args)
     if args.workload == "refined":
