@@ -463,7 +463,7 @@ class Batch:
 
     def __init__(self, lattice, precision, cases, device=0):
         """cases: list of dicts with shape, mach, reynolds, ref_length and
-        optional bc, method, inflow_dir, theta_inf, prandtl, gamma."""
+        optional bc, method, inflow_dir, theta_inf, use_ac, bulk_ratio."""
         L = lib()
         n = len(cases)
         cfgs = (Config * n)()
@@ -479,6 +479,8 @@ class Batch:
             cfg.mach, cfg.reynolds, cfg.ref_length = c["mach"], c["reynolds"], c["ref_length"]
             cfg.theta_inf = c.get("theta_inf", 0.0)
             cfg.method = int(c.get("method", FODIBM_R))
+            cfg.use_ac = int(c.get("use_ac", cfg.use_ac))
+            cfg.bulk_ratio = float(c.get("bulk_ratio", 0.0))
             d = c.get("inflow_dir", (1.0, 0.0, 0.0))
             for a in range(3):
                 cfg.inflow_dir[a] = float(d[a]) if a < len(d) else 0.0
