@@ -36,6 +36,8 @@ def test_config_default_without_gpu():
     assert lib.lbm_config_default(ct.byref(cfg)) == 0
     assert cfg.struct_size == ct.sizeof(lbmib.Config)
     assert abs(cfg.sigma_hrr - 0.98) < 1e-15 and abs(cfg.d_n - 1.5) < 1e-15
+    # defaults: central a^C stencil (reading Q6), no artificial bulk viscosity (Q29)
+    assert cfg.use_ac == lbmib.AC_CENTRAL and cfg.bulk_ratio == 0.0
     assert lib.lbm_config_default(None) == 1
 
 
