@@ -302,8 +302,15 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
           k_relu_mask<<<blocks(P * to.C / 4), 256, 0, net->st>>>(reinterpret_cast<const float4*>(to.act),
                                                                   reinterpret_cast<float4*>(to.grad), P * to.C / 4);
         const int nchunk = wgrad_chunks(B, Hi, Wi);
-        dim3 wg((unsigned)nchunk, (unsigned)((l.coutp + 31) / 32), (unsigned)((l.cinp + 31) / 32));
-        k_conv3x3_wgrad<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp);
+        if (Wi % kRowPx == 0 && l.coutp <= kWtM && l.coutp % 8 == 0 && l.cinp % 8 == 0) {
+          // tensor cores: one CTA per (chunk, 32 input channels, row shift)
+          dim3 wt((unsigned)nchunk, (unsigned)((l.cinp + kWtN - 1) / kWtN), 3u);
+          k_conv3x3_wgrad_tc<<<wt, 128, kWtSmem, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp,
+                                                            net->tc_status);
+        } else {
+          dim3 wg((unsigned)nchunk, (unsigned)((l.coutp + 31) / 32), (unsigned)((l.cinp + 31) / 32));
+          k_conv3x3_wgrad<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp);
+        }
         const long long len = (long long)l.coutp * 9 * l.cinp;
         k_sum_chunks<<<(unsigned)((len + 31) / 32), dim3(32, 8), 0, net->st>>>(net->part, nchunk, len, l.dW);
         const int nbias = (int)((P + kWChunk - 1) / kWChunk);

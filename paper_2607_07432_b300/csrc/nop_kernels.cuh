@@ -586,6 +586,187 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const float* __restrict__
     }
 }
 
+// Weight-gradient partials on the tensor cores (tcgen05, accumulators in
+// TMEM), same partial layout and chunking as k_conv3x3_wgrad:
+// part[chunk][co][tap][ci] = sum_{p in chunk} G[p][co] X[p + tap][ci].
+// GEMM per tap: M = c_out (128 rows, zero beyond Cout), N = 32 c_in of the
+// CTA's tile, K = pixels.  Both operands are staged MN-major as BF16: for
+// each group of 8 channels the pixels of the segment follow one another at
+// 16 bytes, so the operand of input column shift dx starts 16 dx bytes
+// later in the same staged row and every shift reads one copy.  A CTA takes
+// one row shift dy (blockIdx.z) and the three column shifts, 3 x 32 TMEM
+// columns; per 64-pixel segment it issues 4 (K steps of 16) x 3 MMAs.  The
+// MMA wait is bounded as in k_conv3x3_tc.
+constexpr int kWtM = 128;                 // c_out rows of the MMA
+constexpr int kWtN = 32;                  // c_in per CTA
+constexpr int kWtCols = kRowPx + 2;       // staged input columns x0-1 .. x0+64
+constexpr int kWtABytes = (kWtM / 8) * kRowPx * 16;
+constexpr int kWtBBytes = (kWtN / 8) * kWtCols * 16;
+constexpr int kWtSmem = kWtABytes + kWtBBytes + 32;
+
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad_tc(const float* __restrict__ G, const float* __restrict__ X,
+                                                          float* __restrict__ part, int B, int H, int W, int Cin,
+                                                          int Cout, int* status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* As = sm;
+  unsigned char* Bs = sm + kWtABytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + kWtBBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int skip;
+  if (tid == 0) skip = *reinterpret_cast<volatile int*>(status);
+  __syncthreads();
+  if (skip) return;
+  const int chunk = blockIdx.x;
+  const int c00 = blockIdx.y * kWtN;
+  const int dy = blockIdx.z;
+  const int tiles_x = W / kRowPx;
+  const long long n_units = (long long)B * H * tiles_x;
+  constexpr uint32_t ncols = 128u;  // 3 x 32 accumulator columns
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  // kind::f16, BF16 x BF16 -> FP32, M = 128, N = 32, A and B MN-major
+  const uint32_t idesc = umma_idesc_bf16(kWtM, kWtN) | (1u << 15) | (1u << 16);
+  bool ok = true;
+  int done_units = 0;
+  uint32_t phase = 0u;
+  // the operands of the next segment are loaded into registers while the
+  // MMAs of the current one run: A items u = tid + 128 k (k < 8), B items
+  // u = tid + 128 k (k < 3, u < 264)
+  constexpr int kAI = kRowPx * (kWtM / 8) / 128, kBI = (kWtCols * (kWtN / 8) + 127) / 128;
+  float4 ra[kAI][2], rb[kBI][2];
+  auto load_unit = [&](long long unit) {
+    const int xt = (int)(unit % tiles_x);
+    const long long r0 = unit / tiles_x;
+    const int y = (int)(r0 % H);
+    const long long b = r0 / H;
+    const int x0 = xt * kRowPx, yy = y + dy - 1;
+#pragma unroll
+    for (int k = 0; k < kAI; ++k) {
+      const int u = tid + 128 * k;
+      const int g = u % (kWtM / 8), px = u / (kWtM / 8);
+      ra[k][0] = ra[k][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g * 8 < Cout) {
+        const float4* src = reinterpret_cast<const float4*>(G + ((b * H + y) * W + x0 + px) * Cout + g * 8);
+        ra[k][0] = src[0];
+        ra[k][1] = src[1];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kBI; ++k) {
+      const int u = tid + 128 * k;
+      const int g = u % (kWtN / 8), col = u / (kWtN / 8);
+      const int xx = x0 + col - 1, ci = c00 + g * 8;
+      rb[k][0] = rb[k][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u < kWtCols * (kWtN / 8) && yy >= 0 && yy < H && xx >= 0 && xx < W && ci < Cin) {
+        const float4* src = reinterpret_cast<const float4*>(X + ((b * H + yy) * W + xx) * Cin + ci);
+        rb[k][0] = src[0];
+        rb[k][1] = src[1];
+      }
+    }
+  };
+  auto pack = [](const float4& lo, const float4& hi) {
+    uint4 pk;
+    pk.x = pack_bf16x2(lo.x, lo.y);
+    pk.y = pack_bf16x2(lo.z, lo.w);
+    pk.z = pack_bf16x2(hi.x, hi.y);
+    pk.w = pack_bf16x2(hi.z, hi.w);
+    return pk;
+  };
+  const long long first = (long long)chunk * kWUnits;
+  if (first < n_units) load_unit(first);
+  for (int uu = 0; uu < kWUnits; ++uu) {
+    const long long unit = first + uu;
+    if (unit >= n_units) break;
+    // A: [c_out group of 8][pixel][8 c_out]; B: input row y + dy - 1, columns
+    // x0 - 1 .. x0 + 64, [c_in group][column][8 c_in]
+#pragma unroll
+    for (int k = 0; k < kAI; ++k) {
+      const int u = tid + 128 * k;
+      const int g = u % (kWtM / 8), px = u / (kWtM / 8);
+      *reinterpret_cast<uint4*>(As + ((size_t)g * kRowPx + px) * 16) = pack(ra[k][0], ra[k][1]);
+    }
+#pragma unroll
+    for (int k = 0; k < kBI; ++k) {
+      const int u = tid + 128 * k;
+      if (u < kWtCols * (kWtN / 8)) {
+        const int g = u % (kWtN / 8), col = u / (kWtN / 8);
+        *reinterpret_cast<uint4*>(Bs + ((size_t)g * kWtCols + col) * 16) = pack(rb[k][0], rb[k][1]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kRowPx / 16; ++ks)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          // MN-major: leading offset between groups of 8 pixels along K
+          // (contiguous, 128 bytes), stride offset between groups of 8
+          // channels along M / N
+          const uint64_t ad = umma_desc(smem_u32(As + (size_t)(ks * 16) * 16), 128, kRowPx * 16);
+          const uint64_t bd = umma_desc(smem_u32(Bs + (size_t)(ks * 16 + dx) * 16), 128, kWtCols * 16);
+          const uint32_t acc = (uu > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(dx * kWtN)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
+    }
+    if (uu + 1 < kWUnits && unit + 1 < n_units) load_unit(unit + 1);
+    // the staged operands are rewritten only after this segment's MMAs
+    const bool fin = tc_wait(mbar, phase);
+    if (!__syncthreads_and((int)fin)) {
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    ++done_units;
+  }
+  if (!ok && tid == 0) atomicExch(status, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok && done_units > 0) {
+    // warp w reads TMEM lanes 32 w .. 32 w + 31 (c_out = lane row)
+    const int co = warp * 32 + lane;
+    float* out = part + (long long)chunk * Cout * 9 * Cin;
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      float v[32];
+      tmem_ld32<32>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dx * kWtN), v);
+      if (co < Cout) {
+        float* dst = out + ((long long)co * 9 + dy * 3 + dx) * Cin + c00;
+        const int nv = Cin - c00 < kWtN ? Cin - c00 : kWtN;
+#pragma unroll
+        for (int j = 0; j < kWtN; j += 4) {
+          if (j >= nv) break;
+          *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+  }
+}
+
 // Bias-gradient partials: part[chunk][co] = sum_{p in chunk} G[p][co], pixels
 // in order.  grid = chunks, block = Cout threads.
 __global__ void k_bias_partial(const float* __restrict__ G, float* __restrict__ part, long long P, int Cout) {

@@ -13,7 +13,8 @@ from oracle import nop as onop
 
 pytestmark = pytest.mark.gpu
 
-H, W, B = 8, 256, 2   # levels 8x256 and 4x128 on tcgen05, 2x64 and 1x32 on mma.sync
+H, W, B = 8, 256, 2   # forward and input gradient: levels 8x256 and 4x128 on tcgen05, 2x64 and 1x32 on
+#                        mma.sync; weight gradient: levels 0-2 on tcgen05, 1x32 on mma.sync
 CIN, COUT = 3, 4
 
 
@@ -91,3 +92,37 @@ def test_wide_network_forward_matches_oracle():
     n.close()
     yo, _ = onop.forward(theta, x.astype(np.float64), CIN, COUT, ch, bf16=True)
     assert _rel(y.cpu().numpy(), yo) < 1e-2
+
+
+def test_wide_network_backward_matches_oracle_on_tensor_cores():
+    """Channels 32-128 at 8x256: the weight gradients of the levels whose
+    rows are multiples of 64 pixels come from the tcgen05 weight-gradient
+    kernel (M = c_out up to 128, several 32-channel input tiles).  As in the
+    full-width mma.sync test, each layer's gradient must be as close to the
+    FP64 gradient as the BF16-operand oracle is (within 1.5x) and no farther
+    from that oracle than twice the oracle's own distance from FP64."""
+    import torch
+    from paper_2607_07432_b300.nop import NeuralOperator
+    ch = (32, 64, 96, 128)
+    rng = _rng(23)
+    x = rng.standard_normal((B, H, W, CIN)).astype(np.float32)
+    dy = rng.standard_normal((B, H, W, COUT)).astype(np.float32)
+    n = NeuralOperator(height=H, width=W, max_batch=B, channels=ch)
+    n.init_params(5)
+    theta = n.params().astype(np.float64)
+    dp = torch.empty(n.n_params, device="cuda")
+    dx = torch.empty((B, H, W, CIN), device="cuda")
+    n.backward(torch.from_numpy(x).cuda(), torch.from_numpy(dy).cuda(), dp, dx)
+    n.close()
+    dp = dp.cpu().numpy().astype(np.float64)
+    _, cache = onop.forward(theta, x.astype(np.float64), CIN, COUT, ch, bf16=True)
+    g, _ = onop.backward(theta, cache, dy.astype(np.float64), CIN, COUT, ch, bf16=True)
+    _, c64 = onop.forward(theta, x.astype(np.float64), CIN, COUT, ch)
+    g64, _ = onop.backward(theta, c64, dy.astype(np.float64), CIN, COUT, ch)
+    off = 0
+    for (ci, co), name in zip(onop.layer_shapes(CIN, COUT, ch), onop.LAYER_NAMES):
+        k = co * 9 * ci + co
+        a, b, c = dp[off:off + k], g[off:off + k], g64[off:off + k]
+        assert _rel(a, c) <= 1.5 * _rel(b, c) + 1e-3, (name, _rel(a, c), _rel(b, c))
+        assert _rel(a, b) <= 2.0 * _rel(b, c) + 1e-2, (name, _rel(a, b), _rel(b, c))
+        off += k
