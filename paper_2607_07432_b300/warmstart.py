@@ -22,12 +22,39 @@ BC = [lbmib.BC_INLET, lbmib.BC_OUTLET, lbmib.BC_FARFIELD, lbmib.BC_FARFIELD]
 # bodies of 8-10 cells at Re 30 diverge within a few hundred steps (the
 # FP64 oracle shows the same), so the heated wall is left out of this set
 WALL_T = 1.0
+# high-Mach sets (hm=True below): the Mach-weighted upstream a^C stencil and a
+# free-stream lattice speed of at most U_CAP (bluff bodies at Ma 0.75 with the
+# built-in theta rule's 0.15 diverge from a uniform start)
+U_CAP = 0.1
 
 
-def solver_for(case, precision="fp32"):
+def case_theta(case, hm):
+    """theta_inf of a case: 0 (the library's rule) for the default sets; for
+    high-Mach sets the rule's value (u_inf <= 0.15, conduction number <= 0.1)
+    lowered until u_inf <= U_CAP."""
+    if not hm:
+        return 0.0
+    g, pr = 1.4, 0.71
+    u1 = case["mach"] * np.sqrt(g / 3.0)
+    k1 = u1 * case["ref_length"] / case["reynolds"] * g / pr
+    th = 1.0
+    if u1 > 0.15:
+        th = min(th, (0.15 / u1) ** 2)
+    if k1 > 0.1:
+        th = min(th, (0.1 / k1) ** 2)
+    u = u1 * np.sqrt(th)
+    return th * (U_CAP / u) ** 2 if u > U_CAP else th
+
+
+def case_config(case, hm):
+    """Keyword arguments of lbmib.Solver / lbmib.Batch for a case."""
+    return dict(mach=case["mach"], reynolds=case["reynolds"], ref_length=case["ref_length"], bc=BC,
+                theta_inf=case_theta(case, hm), use_ac=lbmib.AC_UPWIND if hm else lbmib.AC_CENTRAL)
+
+
+def solver_for(case, precision="fp32", hm=False):
     nx, ny = case["shape"]
-    s = lbmib.Solver("D2Q9", precision, shape=(nx, ny), mach=case["mach"], reynolds=case["reynolds"],
-                     ref_length=case["ref_length"], bc=BC)
+    s = lbmib.Solver("D2Q9", precision, shape=(nx, ny), **case_config(case, hm))
     th = s.constants()["theta_inf"]
     s.set_geometry(inputs.two_body_geometry(case, WALL_T * th))
     return s
@@ -63,15 +90,16 @@ def normalise(fields, const, mach):
     return y
 
 
-def generate(cases, steps, chunk=64):
+def generate(cases, steps, chunk=64, hm=False, failed=None):
     """Steady fields of the cases from uniform starts, `steps` steps each,
     advanced `chunk` cases at a time in one batched launch per step.
-    Returns X [n][ny][nx][3] and Y [n][ny][nx][4] (float32)."""
+    Returns X [n][ny][nx][3] and Y [n][ny][nx][4] (float32).  With a list
+    `failed`, a case whose fields fail the health check is left out and its
+    index appended there (otherwise the check raises)."""
     X, Y = [], []
     for k0 in range(0, len(cases), chunk):
         part = cases[k0:k0 + chunk]
-        b = lbmib.Batch("D2Q9", "fp32", [dict(shape=c["shape"], mach=c["mach"], reynolds=c["reynolds"],
-                                                ref_length=c["ref_length"], bc=BC) for c in part])
+        b = lbmib.Batch("D2Q9", "fp32", [dict(shape=c["shape"], **case_config(c, hm)) for c in part])
         consts = []
         for k, c in enumerate(part):
             v = b.case(k)
@@ -82,7 +110,14 @@ def generate(cases, steps, chunk=64):
         b.sync()
         for k, c in enumerate(part):
             v = b.case(k)
-            v.check()
+            if failed is None:
+                v.check()
+            else:
+                try:
+                    v.check()
+                except lbmib.LBMError:
+                    failed.append(k0 + k)
+                    continue
             X.append(features(c))
             Y.append(normalise(v.fields(), consts[k], c["mach"]))
         b.close()
@@ -133,20 +168,25 @@ def steps_to_steady(hist, target, every, tol=1e-3):
     return int((first + 1) * every)
 
 
-def compare(net, case, steps, every, tol=1e-3):
+def compare(net, case, steps, every, tol=1e-3, hm=False):
     """Uniform start vs warm start on one case.  The uniform run's final
-    drag is the converged answer both are measured against."""
+    drag is the converged answer both are measured against.  A run that
+    fails the health check is reported (diverged) instead of measured."""
     import torch
-    s = solver_for(case)
+    s = solver_for(case, hm=hm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h_u = drag_history(s, steps, every)
+    try:
+        h_u = drag_history(s, steps, every)
+    except lbmib.LBMError:
+        s.close()
+        return dict(diverged="uniform", steps_uniform=None, steps_warm=None)
     torch.cuda.synchronize()
     ms_u = (time.perf_counter() - t0) * 1e3
     cd_inf = h_u[-1]
     const = s.constants()
     s.close()
-    s = solver_for(case)
+    s = solver_for(case, hm=hm)
     x = torch.from_numpy(features(case)[None]).cuda()
     off, sc = scales(const, case["mach"])
     torch.cuda.synchronize()
@@ -155,7 +195,12 @@ def compare(net, case, steps, every, tol=1e-3):
     torch.cuda.synchronize()
     ms_inf = (time.perf_counter() - t0) * 1e3
     t0 = time.perf_counter()
-    h_w = drag_history(s, steps, every)
+    try:
+        h_w = drag_history(s, steps, every)
+    except lbmib.LBMError:
+        s.close()
+        return dict(diverged="warm", cd_inf=float(cd_inf), steps_uniform=steps_to_steady(h_u, cd_inf, every, tol),
+                    steps_warm=None)
     torch.cuda.synchronize()
     ms_w = (time.perf_counter() - t0) * 1e3
     s.close()
