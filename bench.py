@@ -836,6 +836,53 @@ def run_precision_mach12(args):
     print(json.dumps(line), flush=True)
 
 
+def run_nop(args):
+    """Speed of the warm-start network (512x256, batch 8, channels
+    32-64-96-128, 3 inputs, 4 outputs): forward pass and training step
+    (forward, backward, Adam), each timed over `--nop-steps` calls after
+    warm-up, with the forward FLOP count of its convolutions."""
+    import torch
+    from paper_2607_07432_b300.nop import NeuralOperator
+    H, W, B, ch = 256, 512, 8, (32, 64, 96, 128)
+    n = NeuralOperator(height=H, width=W, max_batch=B, channels=ch)
+    n.init_params(1)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn((B, H, W, 3), device="cuda", generator=g)
+    y = torch.empty((B, H, W, 4), device="cuda")
+    t = torch.randn((B, H, W, 4), device="cuda", generator=g)
+    K = args.nop_steps
+    for _ in range(2):
+        n.forward(x, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        n.forward(x, y)
+    torch.cuda.synchronize()
+    fw = (time.perf_counter() - t0) / K * 1e3
+    for _ in range(2):
+        n.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        n.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    tr = (time.perf_counter() - t0) / K * 1e3
+    n.close()
+    # forward FLOPs: 2 x 9 x c_in x c_out per pixel of each convolution's level
+    # (skip connections are added, so a decoder convolution takes the coarser level's channels)
+    shapes = [(3, ch[0]), (ch[0], ch[0]), (ch[0], ch[1]), (ch[1], ch[1]), (ch[1], ch[2]), (ch[2], ch[2]),
+              (ch[2], ch[3]), (ch[3], ch[3]), (ch[3], ch[2]), (ch[2], ch[2]), (ch[2], ch[1]), (ch[1], ch[1]),
+              (ch[1], ch[0]), (ch[0], ch[0]), (ch[0], 4)]
+    levels = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0]
+    fl = sum(2 * 9 * ci * co * B * (H >> l) * (W >> l) for (ci, co), l in zip(shapes, levels))
+    line = {"metric": "warm-start network: forward and training-step time (512x256, batch 8)",
+            "value": tr, "unit": "ms per training step", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "bf16 x bf16 -> f32", "data": "synthetic",
+            "config": {"workload": "4-level U-Net 32-64-96-128 channels, 512x256, batch 8", "calls": K},
+            "forward_ms": fw, "forward_tflops": fl / fw / 1e9, "train_tflops_3x_forward": 3 * fl / tr / 1e9}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Reduced-precision storage on the 3D sphere case (Ma 0.3, Re 300,
     isothermal wall): C_d and Nu as running means, and the steps until the
@@ -1161,7 +1208,7 @@ def main():
     ap.add_argument("--workload", default="sphere", choices=["sphere", "batch64", "warmstart", "precision",
                                                                     "convergence", "rotsphere", "refined",
                                                                     "refined_sphere", "supersonic", "airfoil",
-                                                                    "precision_mach12"])
+                                                                    "precision_mach12", "nop"])
     ap.add_argument("--ref-steps", type=int, default=40000)
     ap.add_argument("--ref-lo", type=int, nargs=2, default=[30, 20])
     ap.add_argument("--ref-hi", type=int, nargs=2, default=[150, 80])
@@ -1170,6 +1217,7 @@ def main():
     ap.add_argument("--rot-d", type=int, default=48, help="sphere diameter in cells (grid 10D x 6D x 6D)")
     ap.add_argument("--rot-noise", type=float, default=0.01)
     ap.add_argument("--rot-omegas", default="0.3,0.6")
+    ap.add_argument("--nop-steps", type=int, default=10)
     ap.add_argument("--p12-settle", type=int, default=12000)
     ap.add_argument("--p12-steps", type=int, default=16000)
     ap.add_argument("--af-chords", type=int, default=15, help="chord flow-through times per airfoil case")
@@ -1207,6 +1255,8 @@ def main():
         return run_airfoil(args)
     if args.workload == "precision_mach12":
         return run_precision_mach12(args)
+    if args.workload == "nop":
+        return run_nop(args)
     if args.workload == "rotsphere":
         return run_rotsphere(args)
     if args.workload == "refined":
