@@ -304,7 +304,7 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
         const int nchunk = wgrad_chunks(B, Hi, Wi);
         if (Wi % kRowPx == 0 && l.coutp <= kWtM && l.coutp % 8 == 0 && l.cinp % 8 == 0) {
           // tensor cores: one CTA per (chunk, 32 input channels, row shift)
-          dim3 wt((unsigned)nchunk, (unsigned)((l.cinp + kWtN - 1) / kWtN), 3u);
+          dim3 wt((unsigned)nchunk * 3u * (unsigned)((l.cinp + kWtN - 1) / kWtN), 1u, 1u);
           k_conv3x3_wgrad_tc<<<wt, 128, kWtSmem, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp,
                                                             net->tc_status);
         } else {

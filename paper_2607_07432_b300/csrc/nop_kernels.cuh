@@ -594,9 +594,9 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const float* __restrict__
 // each group of 8 channels the pixels of the segment follow one another at
 // 16 bytes, so the operand of input column shift dx starts 16 dx bytes
 // later in the same staged row and every shift reads one copy.  A CTA takes
-// one row shift dy (blockIdx.z) and the three column shifts, 3 x 32 TMEM
+// one row shift dy and the three column shifts, 3 x 32 TMEM
 // columns; per 64-pixel segment it issues 4 (K steps of 16) x 3 MMAs.  The
-// MMA wait is bounded as in k_conv3x3_tc.
+// MMA wait is bounded as in k_conv3x3_tc.  grid = chunks x c_in tiles x 3.
 constexpr int kWtM = 128;                 // c_out rows of the MMA
 constexpr int kWtN = 32;                  // c_in per CTA
 constexpr int kWtCols = kRowPx + 2;       // staged input columns x0-1 .. x0+64
@@ -617,9 +617,12 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad_tc(const float* __restric
   if (tid == 0) skip = *reinterpret_cast<volatile int*>(status);
   __syncthreads();
   if (skip) return;
-  const int chunk = blockIdx.x;
-  const int c00 = blockIdx.y * kWtN;
-  const int dy = blockIdx.z;
+  // the CTAs of a chunk (3 row shifts x input-channel tiles) are
+  // neighbours, so they run together and re-reads of its operand rows hit L2
+  const int n_ct = (Cin + kWtN - 1) / kWtN;
+  const int dy = blockIdx.x % 3;
+  const int c00 = (blockIdx.x / 3 % n_ct) * kWtN;
+  const int chunk = blockIdx.x / (3 * n_ct);
   const int tiles_x = W / kRowPx;
   const long long n_units = (long long)B * H * tiles_x;
   constexpr uint32_t ncols = 128u;  // 3 x 32 accumulator columns
