@@ -104,6 +104,16 @@ lbm_status nop_forward(nop_net* net, int batch, const float* x, float* y);
 lbm_status nop_backward(nop_net* net, int batch, const float* x, const float* dy,
                         float* dparams, float* dx);
 
+/* Gradient-check mode (on != 0): the 3x3 convolutions of nop_forward,
+ * nop_backward and nop_train_step run on FP32 operands (weights and
+ * activations unrounded, FP32 products and fixed-order FP32 sums, CUDA
+ * cores) instead of the BF16-operand tensor-core path, so that the
+ * gradients can be compared with the FP64 reference backward to 1e-5.
+ * Slow; for checks only.  The first call with on != 0 allocates the FP32
+ * weight copies (LBM_ENOMEM on failure); on = 0 returns to the BF16 path.
+ * No counterpart in the paper (the network is this library's addition). */
+lbm_status nop_set_fp32(nop_net* net, int on);
+
 /* One training step on a batch: forward, mean-squared-error loss
  * L = sum (y - target)^2 / (batch H W out_channels), backward, Adam update
  * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, learning rate lr) of

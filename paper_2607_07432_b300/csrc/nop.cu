@@ -43,6 +43,8 @@ struct Layer {
   float* bias = nullptr;
   float* dW = nullptr;  // padded weight gradient [coutp][9][cinp]
   float* db = nullptr;  // padded bias gradient [coutp]
+  float* Wt32 = nullptr;  // FP32 weights of the gradient-check mode (nop_set_fp32)
+  float* Wf32 = nullptr;
   long long size() const { return (long long)cout * 9 * cin + cout; }
 };
 
@@ -72,6 +74,7 @@ struct nop_net {
   double* fields = nullptr;  // rho, u (2 planes), T for nop_infer_into
   long long adam_t = 0;
   bool prepared = false;
+  bool fp32 = false;         // FP32 operand convolutions (nop_set_fp32)
   int* tc_status = nullptr;  // set by a tensor-core convolution whose MMA wait timed out
   std::vector<void*> allocs;
 };
@@ -236,6 +239,13 @@ void conv(nop_net* net, const float* X, const __nv_bfloat16* Wt, const float* bi
   k_conv3x3<<<grid, 128, 0, net->st>>>(X, Wt, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
 }
 
+// the FP32 operand convolution of the gradient-check mode
+void conv_f32(nop_net* net, const float* X, const float* W32, const float* bias, float* Y, int B, int H, int W,
+              int Cin, int Cout, int relu, int accumulate) {
+  const long long n = (long long)B * H * W * Cout;
+  k_conv3x3_f32<<<blocks(n), 256, 0, net->st>>>(X, W32, bias, Y, B, H, W, Cin, Cout, relu, accumulate);
+}
+
 // BF16 copies of the master weights (after every change of the masters)
 lbm_status prepare(nop_net* net) {
   if (net->prepared) return LBM_OK;
@@ -243,6 +253,9 @@ lbm_status prepare(nop_net* net) {
     const long long n = (long long)l.coutp * 9 * l.cinp;
     k_prep_layer<<<blocks(n), 256, 0, net->st>>>(net->master + l.offset, l.cin, l.cout, l.cinp, l.coutp, l.Wt,
                                                  l.Wf, l.bias);
+    if (net->fp32)
+      k_prep_layer_f32<<<blocks(n), 256, 0, net->st>>>(net->master + l.offset, l.cin, l.cout, l.cinp, l.coutp,
+                                                       l.Wt32, l.Wf32);
   }
   net->prepared = true;
   return launch_check(net, "k_prep_layer");
@@ -260,7 +273,10 @@ lbm_status forward(nop_net* net, int B) {
     switch (op.kind) {
       case kConv: {
         const Layer& l = net->L[op.layer];
-        conv(net, ti.act, l.Wt, l.bias, to.act, B, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
+        if (net->fp32)
+          conv_f32(net, ti.act, l.Wt32, l.bias, to.act, B, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
+        else
+          conv(net, ti.act, l.Wt, l.bias, to.act, B, Ho, Wo, l.cinp, l.coutp, op.relu, 0);
         break;
       }
       case kPool:
@@ -302,7 +318,13 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
           k_relu_mask<<<blocks(P * to.C / 4), 256, 0, net->st>>>(reinterpret_cast<const float4*>(to.act),
                                                                   reinterpret_cast<float4*>(to.grad), P * to.C / 4);
         const int nchunk = wgrad_chunks(B, Hi, Wi);
-        if (Wi % kRowPx == 0 && l.coutp <= kWtM && l.coutp % 8 == 0 && l.cinp % 8 == 0) {
+        if (net->fp32) {
+          const long long P = (long long)B * Hi * Wi;
+          const long long len = (long long)l.coutp * 9 * l.cinp;
+          dim3 wg((unsigned)nchunk, (unsigned)((len + 127) / 128), 1u);
+          k_conv3x3_wgrad_f32<<<wg, 128, 0, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp,
+                                                        (P + nchunk - 1) / nchunk);
+        } else if (Wi % kRowPx == 0 && l.coutp <= kWtM && l.coutp % 8 == 0 && l.cinp % 8 == 0) {
           // tensor cores: one CTA per (chunk, 32 input channels, row shift)
           dim3 wt((unsigned)nchunk * 3u * (unsigned)((l.cinp + kWtN - 1) / kWtN), 1u, 1u);
           k_conv3x3_wgrad_tc<<<wt, 128, kWtSmem, net->st>>>(to.grad, ti.act, net->part, B, Hi, Wi, l.cinp, l.coutp,
@@ -317,7 +339,10 @@ lbm_status backward(nop_net* net, int B, bool want_dx) {
         k_bias_partial<<<nbias, dim3(l.coutp, 4), 0, net->st>>>(to.grad, net->part, P, l.coutp);
         k_sum_chunks<<<(unsigned)((l.coutp + 31) / 32), dim3(32, 8), 0, net->st>>>(net->part, nbias, l.coutp, l.db);
         if (op.in != net->x_t || want_dx) {
-          conv(net, to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
+          if (net->fp32)
+            conv_f32(net, to.grad, l.Wf32, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
+          else
+            conv(net, to.grad, l.Wf, nullptr, ti.grad, B, Hi, Wi, l.coutp, l.cinp, 0, 1);
         }
         break;
       }
@@ -454,6 +479,23 @@ void nop_destroy(nop_net* net) {
   for (void* p : net->allocs) cudaFree(p);
   if (net->own_stream && net->st) cudaStreamDestroy(net->st);
   delete net;
+}
+
+lbm_status nop_set_fp32(nop_net* net, int on) {
+  if (!net) return LBM_EINVAL;
+  DeviceGuard dg(net->cfg.device);
+  NCK(dg.status());
+  if (on && !net->L.empty() && !net->L[0].Wt32) {
+    for (Layer& l : net->L) {
+      const long long n = (long long)l.coutp * 9 * l.cinp;
+      lbm_status s = dalloc(net, &l.Wt32, n);
+      if (!s) s = dalloc(net, &l.Wf32, n);
+      if (s) return s;
+    }
+  }
+  net->fp32 = on != 0;
+  net->prepared = false;
+  return LBM_OK;
 }
 
 const char* nop_last_error(const nop_net* net) { return net ? net->err.c_str() : "null network"; }

@@ -1025,6 +1025,82 @@ __global__ void k_prep_layer(const float* __restrict__ master, int cin, int cout
   Wf[((long long)ci * 9 + (8 - tap)) * coutp + co] = wb;
 }
 
+// FP32 operand form of the convolutions (the gradient-check mode of the
+// network: no BF16 rounding of weights or activations, FP32 products and
+// sums in a fixed order, CUDA cores).  Weights in the padded layouts of
+// k_prep_layer: Wt32[co][tap][ci] and the flipped, transposed
+// Wf32[ci][8 - tap][co].
+__global__ void k_prep_layer_f32(const float* __restrict__ master, int cin, int cout, int cinp, int coutp,
+                                 float* __restrict__ Wt32, float* __restrict__ Wf32) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)coutp * 9 * cinp;
+  if (i >= n) return;
+  const int ci = (int)(i % cinp);
+  const long long q = i / cinp;
+  const int tap = (int)(q % 9);
+  const int co = (int)(q / 9);
+  const float w = (co < cout && ci < cin) ? master[((long long)co * 9 + tap) * cin + ci] : 0.f;
+  Wt32[i] = w;
+  Wf32[((long long)ci * 9 + (8 - tap)) * coutp + co] = w;
+}
+
+// Y[p][co] (+)= sum over taps (row-major 3x3, offsets -1..1) and c_in of
+// X[p + tap][ci] W32[co][tap][ci] (+ bias[co]), then ReLU if relu; zero
+// padding outside the image; one thread per output value, sums in tap then
+// channel order.
+__global__ void k_conv3x3_f32(const float* __restrict__ X, const float* __restrict__ W32,
+                              const float* __restrict__ bias, float* __restrict__ Y, int B, int H, int W, int Cin,
+                              int Cout, int relu, int accumulate) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)B * H * W * Cout;
+  if (i >= n) return;
+  const int co = (int)(i % Cout);
+  const long long p = i / Cout;
+  const int x = (int)(p % W);
+  const int y = (int)((p / W) % H);
+  const long long b = p / ((long long)W * H);
+  float acc = 0.f;
+  for (int tap = 0; tap < 9; ++tap) {
+    const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    const float* xr = X + ((b * H + yy) * W + xx) * Cin;
+    const float* wr = W32 + ((long long)co * 9 + tap) * Cin;
+    for (int ci = 0; ci < Cin; ++ci) acc = fmaf(xr[ci], wr[ci], acc);
+  }
+  if (bias) acc += bias[co];
+  if (relu) acc = fmaxf(acc, 0.f);
+  Y[i] = accumulate ? Y[i] + acc : acc;
+}
+
+// Weight-gradient partials of the FP32 form: part[c][(co tap) ci] = sum over
+// the pixels p of chunk c (pixels [c P_c, (c + 1) P_c), in order) of
+// G[p][co] X[p + tap][ci]; the chunks are added in order by k_sum_chunks.
+__global__ void k_conv3x3_wgrad_f32(const float* __restrict__ G, const float* __restrict__ X,
+                                    float* __restrict__ part, int B, int H, int W, int Cin, int Cout,
+                                    long long chunk_px) {
+  const long long len = (long long)Cout * 9 * Cin;
+  const long long j = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  const int ci = (int)(j % Cin);
+  const long long q = j / Cin;
+  const int tap = (int)(q % 9);
+  const int co = (int)(q / 9);
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const long long P = (long long)B * H * W;
+  const long long p0 = (long long)blockIdx.x * chunk_px;
+  const long long p1 = p0 + chunk_px < P ? p0 + chunk_px : P;
+  float acc = 0.f;
+  for (long long p = p0; p < p1; ++p) {
+    const int x = (int)(p % W);
+    const int y = (int)((p / W) % H);
+    const int yy = y + dy, xx = x + dx;
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    const long long pp = p + (long long)dy * W + dx;
+    acc = fmaf(G[p * Cout + co], X[pp * Cin + ci], acc);
+  }
+  part[(long long)blockIdx.x * len + j] = acc;
+}
+
 // Padded weight / bias gradients -> the master layout of the layer.
 __global__ void k_unpad_grad(const float* __restrict__ dW, const float* __restrict__ db, int cin, int cout,
                              int cinp, float* __restrict__ grad) {

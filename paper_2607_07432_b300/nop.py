@@ -12,7 +12,7 @@ from . import lbmib
 
 NOP_EXPORTS = ["nop_config_default", "nop_create", "nop_destroy", "nop_last_error", "nop_param_count",
                "nop_init_params", "nop_set_params", "nop_get_params", "nop_forward", "nop_backward",
-               "nop_train_step", "nop_infer_into"]
+               "nop_train_step", "nop_infer_into", "nop_set_fp32"]
 
 
 class NopConfig(ct.Structure):
@@ -42,6 +42,7 @@ def _lib():
         L.nop_get_params.argtypes = [vp, ct.c_int, vp]
         L.nop_forward.argtypes = [vp, ct.c_int, vp, vp]
         L.nop_backward.argtypes = [vp, ct.c_int, vp, vp, vp, vp]
+        L.nop_set_fp32.argtypes = [vp, ct.c_int]
         L.nop_train_step.argtypes = [vp, ct.c_int, vp, vp, ct.c_float, ct.POINTER(ct.c_double)]
         L.nop_infer_into.argtypes = [vp, vp, vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
         _SET = True
@@ -125,6 +126,11 @@ class NeuralOperator:
     def backward(self, x, dy, dparams=None, dx=None):
         _ready()
         self._check(_lib().nop_backward(self.h, int(x.shape[0]), _dev(x), _dev(dy), _dev(dparams), _dev(dx)))
+
+    def set_fp32(self, on=True):
+        """Gradient-check mode: FP32-operand convolutions (slow; see
+        nop_set_fp32 in include/nop.h)."""
+        self._check(_lib().nop_set_fp32(self.h, 1 if on else 0))
 
     def train_step(self, x, target, lr):
         _ready()
