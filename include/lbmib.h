@@ -384,10 +384,13 @@ lbm_status lbm_refined_step(lbm_refined* r, int n_steps);
 /* ---- several cases advanced together ------------------------------------
  * A batch owns n cases (same lattice, precision and device; grids, bodies
  * and flow parameters may differ) on one stream of its own.  A batched step
- * runs each case's immersed-boundary and boundary kernels around one fused
- * launch that covers the tiles of every case in a schedule order; two steps
- * are captured once as a CUDA graph and replayed.  Results are bit-identical
- * to stepping each case on its own. */
+ * runs the immersed-boundary force, spreading, fused and boundary work of
+ * every case (Sec. 2.5 steps 1-5) from work tables in a schedule order,
+ * either as one persistent cooperative launch whose CTAs pass grid-wide
+ * barriers between the phases (launch form 1, 2D lattices, default there)
+ * or as one launch per phase (form 0); two steps are captured once as a CUDA
+ * graph and replayed.  Results are bit-identical to stepping each case on
+ * its own, in either form. */
 typedef struct lbm_batch lbm_batch;
 
 /* Create n cases from cfgs[0..n-1] (their stream fields are ignored). */
@@ -401,13 +404,21 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps);
 /* Advance every case n_steps steps one case after another with per-case
  * launches (the unbatched form, for comparison). */
 lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps);
-/* Wait for the batch stream. */
+/* Wait for the batch stream.  LBM_ETIMEOUT when a persistent launch ended
+ * early because a grid barrier waited past its limit (about a second; the
+ * cases are then not at a whole step). */
 lbm_status lbm_batch_sync(lbm_batch* b);
+/* Launch form of a batched step: 1 = one persistent cooperative launch per
+ * two steps (2D lattices only; the grid is as many CTAs as are resident at
+ * once), 0 = one launch per phase.  LBM_EINVAL for form 1 on D3Q19. */
+lbm_status lbm_batch_set_launch_form(lbm_batch* b, int form);
+lbm_status lbm_batch_get_launch_form(const lbm_batch* b, int* form);
 /* Fused-launch plan: tile_rows 0 (default tile), 16 or 32 (2D FP32 only), and
  * schedule 0 = case-major, 1 = round-robin over cases, 2 = largest first. */
 lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule);
 lbm_status lbm_batch_get_plan(const lbm_batch* b, int* tile_rows, int* schedule);
-/* Autotuner: times each plan over `steps` batched steps on the batch itself
+/* Autotuner: times each plan (launch form, tile rows, schedule) over `steps`
+ * batched steps on the batch itself
  * (state saved before and restored after) and keeps the fastest; with
  * cache_path, results are read from / appended to that text file keyed by
  * the case set.  *best_ms (optional) receives the best time per step. */

@@ -1,9 +1,11 @@
-// Batched stepping of several cases (lbm_batch_*): one launch each of the
-// immersed-boundary force, spreading and boundary kernels and one fused
-// launch cover every case, from work tables; two consecutive steps (both
+// Batched stepping of several cases (lbm_batch_*), from work tables, in one
+// of two launch forms: one persistent cooperative launch that runs every
+// phase of the step for all cases with grid-wide barriers between them (2D
+// lattices, the default there), or one launch each of the immersed-boundary
+// force, spreading, fused and boundary kernels.  Two consecutive steps (both
 // buffer parities) are captured once as a CUDA graph and replayed.  The
-// autotuner times the tile heights and schedules on the batch and keeps the
-// fastest; it restores the state it advanced.
+// autotuner times the tile heights, schedules and launch forms on the batch
+// and keeps the fastest; it restores the state it advanced.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -57,6 +59,15 @@ lbm_status rebuild(lbm_batch* b) {
   BatchPlan& p = b->plan;
   lbm_status s = b->ops->batch_build(&p);
   if (s) return bfail(b, s, p.err.empty() ? "batch plan" : p.err);
+  if (p.launch_form == 1) {
+    // barrier state (zero) and the grid of CTAs resident at once
+    if (!p.bar && cudaMalloc(&p.bar, sizeof(lbmib::GridBarrier)) != cudaSuccess)
+      return bfail(b, LBM_ENOMEM, "barrier state");
+    if (cudaMemsetAsync(p.bar, 0, sizeof(lbmib::GridBarrier), b->st) != cudaSuccess)
+      return bfail(b, LBM_ECUDA, "barrier state");
+    s = b->ops->batch_persistent(&p, 0, 0);
+    if (s) return bfail(b, s, "persistent launch: no resident grid for this plan");
+  }
   p.built_f.clear();
   p.built_geom.clear();
   for (lbm_handle* h : p.cases) {
@@ -72,6 +83,16 @@ lbm_status one_step(lbm_batch* b, int parity) {
   BatchPlan& p = b->plan;
   for (lbm_handle* h : p.cases)
     if (h->sticky) return (lbm_status)h->sticky;
+  if (p.launch_form == 1) {
+    lbm_status s = b->ops->batch_persistent(&p, parity, 1);
+    if (s) return bfail(b, s, p.err);
+    for (lbm_handle* h : p.cases) {
+      std::swap(h->f, h->f2);
+      std::swap(h->M, h->M2);
+      h->cur = 1 - h->cur;
+    }
+    return LBM_OK;
+  }
   lbm_status s = b->ops->batch_aux(&p, parity, 0);
   if (!s) s = b->ops->batch_fused(&p, parity);
   if (s) return bfail(b, s, p.err);
@@ -83,6 +104,21 @@ lbm_status one_step(lbm_batch* b, int parity) {
   s = b->ops->batch_aux(&p, parity, 1);
   if (s) return bfail(b, s, p.err);
   return LBM_OK;
+}
+
+// two steps from parity 0 (eager, also used while capturing): one
+// persistent launch, or the launches of two single steps
+lbm_status two_steps(lbm_batch* b) {
+  BatchPlan& p = b->plan;
+  if (p.launch_form != 1) {
+    lbm_status s = one_step(b, 0);
+    return s ? s : one_step(b, 1);
+  }
+  for (lbm_handle* h : p.cases)
+    if (h->sticky) return (lbm_status)h->sticky;
+  lbm_status s = b->ops->batch_persistent(&p, 0, 2);
+  if (s) return bfail(b, s, p.err);
+  return LBM_OK;  // two buffer swaps: every handle is back at parity 0
 }
 
 }  // namespace
@@ -103,6 +139,7 @@ lbm_status lbm_batch_create(int n, const lbm_config* cfgs, lbm_batch** out) {
     return LBM_ECUDA;
   }
   b->plan.st = b->st;
+  b->plan.launch_form = cfgs[0].lattice == LBM_D2Q9 ? 1 : 0;
   for (int k = 0; k < n; ++k) {
     lbm_config c = cfgs[k];
     c.stream = b->st;
@@ -128,7 +165,7 @@ void lbm_batch_destroy(lbm_batch* b) {
   for (int p = 0; p < 2; ++p)
     for (void* d : {pl.descs[p], pl.ib_descs[p], pl.sp_descs[p], pl.bc_descs[p]})
       if (d) cudaFree(d);
-  for (void* d : {pl.work, pl.ib_work, pl.sp_work, pl.bc_work})
+  for (void* d : {pl.work, pl.ib_work, pl.sp_work, pl.bc_work, pl.bar})
     if (d) cudaFree(d);
   if (b->st) cudaStreamDestroy(b->st);
   delete b;
@@ -148,6 +185,20 @@ lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule) {
   b->plan.schedule = schedule;
   b->plan.built = false;
   drop_graph(b);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_launch_form(lbm_batch* b, int form) {
+  if (!b || form < 0 || form > 1 || (form == 1 && b->plan.cases[0]->D != 2)) return LBM_EINVAL;
+  b->plan.launch_form = form;
+  b->plan.built = false;
+  drop_graph(b);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_launch_form(const lbm_batch* b, int* form) {
+  if (!b || !form) return LBM_EINVAL;
+  *form = b->plan.launch_form;
   return LBM_OK;
 }
 
@@ -172,8 +223,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps) {
     if (n_steps - done >= 2) {
       if (!b->graph_ok) {
         cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
-        lbm_status s = one_step(b, 0);
-        lbm_status s2 = s ? s : one_step(b, 1);
+        lbm_status s2 = two_steps(b);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->st, &g);
         if (s2 || e != cudaSuccess) {
@@ -211,13 +261,26 @@ lbm_status lbm_batch_step_sequential(lbm_batch* b, int n_steps) {
 lbm_status lbm_batch_sync(lbm_batch* b) {
   if (!b) return LBM_EINVAL;
   DeviceGuard dg(b->plan.cases[0]->cfg.device);
-  return cudaStreamSynchronize(b->st) == cudaSuccess ? LBM_OK : bfail(b, LBM_ECUDA, "sync");
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return bfail(b, LBM_ECUDA, "sync");
+  if (b->plan.bar) {
+    // a persistent launch whose grid barrier gave up ended early: the state
+    // is not a whole step; clear the barrier for the next launch
+    lbmib::GridBarrier gb;
+    if (cudaMemcpy(&gb, b->plan.bar, sizeof(gb), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(b, LBM_ECUDA, "barrier status read");
+    if (gb.err) {
+      cudaMemset(b->plan.bar, 0, sizeof(gb));
+      return bfail(b, LBM_ETIMEOUT, "persistent batched step: a grid barrier timed out");
+    }
+  }
+  return LBM_OK;
 }
 
-// Time every (tile rows, schedule) candidate over `steps` batched steps and
-// keep the fastest.  The state each trial advances is saved before and
-// restored after.  With cache_path, a result for the same case set is read
-// from / appended to that text file ("key tile_rows schedule" lines).
+// Time every (launch form, tile rows, schedule) candidate over `steps`
+// batched steps and keep the fastest.  The state each trial advances is
+// saved before and restored after.  With cache_path, a result for the same
+// case set is read from / appended to that text file ("key tile_rows
+// schedule launch_form" lines; a line without the form means form 0).
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, double* best_ms) {
   if (!b || steps <= 0) return LBM_EINVAL;
   DeviceGuard dg(b->plan.cases[0]->cfg.device);
@@ -227,10 +290,16 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, d
   for (lbm_handle* h : p.cases) key << ":" << h->g.n[0] << "x" << h->g.n[1] << "x" << h->g.n[2] << "/" << h->NL;
   if (cache_path) {
     std::ifstream in(cache_path);
-    std::string k;
-    int tr, sc;
-    while (in >> k >> tr >> sc)
-      if (k == key.str()) return lbm_batch_set_plan(b, tr, sc);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string k;
+      int tr = 0, sc = 0, fm = 0;
+      if (!(ls >> k >> tr >> sc) || k != key.str()) continue;
+      if (!(ls >> fm)) fm = 0;
+      lbm_status s = lbm_batch_set_launch_form(b, fm);
+      return s ? s : lbm_batch_set_plan(b, tr, sc);
+    }
   }
   // save the state
   struct Saved {
@@ -274,14 +343,17 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, d
   };
   const int rows[3] = {0, 16, 32};
   const int nrows = (p.cases[0]->D == 2 && p.cases[0]->csize == 4) ? 3 : 1;
+  const int nforms = p.cases[0]->D == 2 ? 2 : 1;
   double best = 1e300;
-  int best_r = 0, best_s = 0;
+  int best_r = 0, best_s = 0, best_f = 0;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   lbm_status st = LBM_OK;
+  for (int fm = 0; fm < nforms && !st; ++fm)
   for (int ri = 0; ri < nrows && !st; ++ri)
     for (int sc = 0; sc < 3 && !st; ++sc) {
+      lbm_batch_set_launch_form(b, fm);
       lbm_batch_set_plan(b, rows[ri], sc);
       st = lbm_batch_step(b, 2);  // warm-up and capture
       if (st) break;
@@ -295,6 +367,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, d
         best = ms;
         best_r = rows[ri];
         best_s = sc;
+        best_f = fm;
       }
       restore();
     }
@@ -303,11 +376,12 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, d
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
+  lbm_batch_set_launch_form(b, best_f);
   lbm_batch_set_plan(b, best_r, best_s);
   if (best_ms) *best_ms = best / (2 * ((steps + 1) / 2));
   if (cache_path) {
     std::ofstream o(cache_path, std::ios::app);
-    o << key.str() << " " << best_r << " " << best_s << "\n";
+    o << key.str() << " " << best_r << " " << best_s << " " << best_f << "\n";
   }
   return LBM_OK;
 }

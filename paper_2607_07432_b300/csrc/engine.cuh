@@ -9,6 +9,7 @@
 
 #include "handle.cuh"
 #include "ib.cuh"
+#include "persist.cuh"
 #include "physics.cuh"
 #include "refine.cuh"
 #include "state.cuh"
@@ -431,6 +432,83 @@ struct Engine {
     }
     return LBM_OK;
   }
+  // the persistent form (2D): one cooperative launch of as many CTAs as are
+  // resident at once runs nsteps steps; the grid size is found at plan build
+  template <int HY, bool NARROW>
+  static lbm_status persist_tile(BatchPlan* b, int parity, int nsteps, bool size_only) {
+    if constexpr (L::D != 2) {
+      return LBM_EINVAL;
+    } else {
+      using Lay = FusedLayout<L, S, C, HY>;
+      auto kern = k_batch_persistent<L, S, C, HY, NARROW>;
+      if (size_only) {
+        int dev = 0, sms = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::bytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Lay::NT, Lay::bytes) != cudaSuccess) {
+          cudaGetLastError();
+          return LBM_ECUDA;
+        }
+        b->persist_grid = occ * sms;
+        return occ > 0 ? LBM_OK : LBM_EINVAL;
+      }
+      PersistDesc<S, C> p;
+      for (int q = 0; q < 2; ++q) {
+        p.descs[q] = (const CaseDesc<S, C>*)b->descs[q];
+        p.ib[q] = (const IBCaseDesc<S, C>*)b->ib_descs[q];
+        p.sp[q] = (const SpreadCaseDesc<C>*)b->sp_descs[q];
+        p.bc[q] = (const BCCaseDesc<S, C>*)b->bc_descs[q];
+      }
+      p.work = (const int4*)b->work;
+      p.n_work = b->n_work;
+      p.ib_work = (const int2*)b->ib_work;
+      p.n_ib = b->n_ib_work;
+      p.sp_work = (const int2*)b->sp_work;
+      p.n_sp = b->n_sp_work;
+      p.bc_work = (const int4*)b->bc_work;
+      p.n_bc = b->n_bc_work;
+      p.bar = (GridBarrier*)b->bar;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)b->persist_grid);
+      cfg.blockDim = dim3(Lay::NT);
+      cfg.dynamicSmemBytes = Lay::bytes;
+      cfg.stream = b->st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, kern, p, parity, nsteps) != cudaSuccess) return LBM_ECUDA;
+      return LBM_OK;
+    }
+  }
+  template <bool NARROW>
+  static lbm_status persist_rows(BatchPlan* b, int parity, int nsteps, bool size_only) {
+    if constexpr (L::D == 2 && sizeof(C) == 4) {
+      if (b->tile_rows == 16) return persist_tile<16, NARROW>(b, parity, nsteps, size_only);
+      if (b->tile_rows == 32) return persist_tile<32, NARROW>(b, parity, nsteps, size_only);
+    }
+    return persist_tile<0, NARROW>(b, parity, nsteps, size_only);
+  }
+  // nsteps >= 1: launch; nsteps == 0: size the grid of the plan's tile
+  static lbm_status batch_persistent(BatchPlan* b, int parity, int nsteps) {
+    if (L::D != 2 || !b->bar) return LBM_EINVAL;
+    bool narrow = true;
+    for (lbm_handle* h : b->cases) narrow = narrow && narrow_index<L>(h->g.N);
+    const bool size_only = nsteps == 0;
+    if (!size_only && b->persist_grid <= 0) return LBM_EINVAL;
+    lbm_status s = narrow ? persist_rows<true>(b, parity, nsteps, size_only)
+                          : persist_rows<false>(b, parity, nsteps, size_only);
+    if (s) {
+      cudaError_t e = cudaGetLastError();
+      b->err = std::string("persistent batched launch: ") + cudaGetErrorString(e);
+      return s;
+    }
+    if (!size_only)
+      for (lbm_handle* h : b->cases) h->launches++;
+    return LBM_OK;
+  }
   template <int HY>
   static void batch_launch(BatchPlan* b, int parity) {
     using Lay = FusedLayout<L, S, C, HY>;
@@ -543,7 +621,7 @@ struct Engine {
   static const Ops* ops() {
     static const Ops o = {&init,        &step,        &fields,    &get_state, &set_state,
                           &set_fields_api, &health, &batch_build, &batch_fused, &batch_aux,
-                          &ib_part,     &bc_part,     &wall_diag, &refine_ghost_state, &refine_fill,
+                          &batch_persistent, &ib_part,     &bc_part,     &wall_diag, &refine_ghost_state, &refine_fill,
                           &refine_restrict};
     return &o;
   }

@@ -36,6 +36,18 @@ struct Grid {
   }
 };
 
+// Grid-wide barrier state (device memory, zero at plan build).  count: CTAs
+// arrived at the current barrier; gen: barriers completed; err: set when a
+// CTA waited past the spin limit (the launch then ends early and the host
+// reports LBM_ETIMEOUT); next: the next work item of a dynamically shared
+// phase.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+  unsigned next;  // work counter of the phase that follows the barrier
+};
+
 // Transfers between the two levels of a refined case (lbm_refined_*):
 // level-1 node k along an axis sits at level-0 coordinate lo + (k - G)/2
 struct RefineDev {

@@ -157,6 +157,9 @@ struct Ops {
   // the IB part (part 0: interpolation, forcing, spreading) or the boundary
   // part (part 1) of every case of a plan, one launch per kernel
   lbm_status (*batch_aux)(BatchPlan*, int parity, int part);
+  // nsteps whole steps of every case from the given parity in one
+  // persistent launch (launch_form 1; LBM_EINVAL where not available)
+  lbm_status (*batch_persistent)(BatchPlan*, int parity, int nsteps);
   // per-case parts of a step around the fused kernel
   lbm_status (*ib_part)(lbm_handle*);
   lbm_status (*bc_part)(lbm_handle*);
@@ -196,6 +199,12 @@ struct BatchPlan {
   void* bc_descs[2] = {nullptr, nullptr};
   void* bc_work = nullptr;
   int n_bc_work = 0;
+  // launch form of a step: 0 = the four batched kernels, 1 = one persistent
+  // cooperative launch for all phases (2D lattices), with its grid barrier
+  // state and grid size (CTAs resident at once)
+  int launch_form = 0;
+  void* bar = nullptr;
+  int persist_grid = 0;
   std::vector<void*> built_f;            // per case h->f at build time (parity 0)
   std::vector<int> built_geom;           // per case geometry version at build time
   bool built = false;

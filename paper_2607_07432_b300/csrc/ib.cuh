@@ -450,8 +450,11 @@ constexpr int kIBPointsPerWarp = 4;
 constexpr int kIBWarps = 2;
 
 // Body of the IB force step for block blk (kIBWarps warps of
-// kIBPointsPerWarp Lagrangian points each) of one case.
-template <class L, class S, class C>
+// kIBPointsPerWarp Lagrangian points each) of one case.  Warp w of the CTA
+// stages in shared-memory slot w (NSLOT slots) and takes the points of warp
+// w % kIBWarps of the block; a CTA of NSLOT warps runs NSLOT / kIBWarps
+// such blocks at once (each caller passes its own blk).
+template <class L, class S, class C, int NSLOT = kIBWarps>
 __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s, const C* M, int blk) {
   constexpr int D = L::D;
   constexpr int KS = D == 2 ? 16 : 64;
@@ -461,11 +464,12 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
   static_assert(NP * 8 == 32 && NV <= 8, "one lane per (point, quantity)");
   // slot values staged per (point, quantity) row, slots contiguous; rows
   // padded by one so that a lane per row reads distinct banks
-  __shared__ double stage[kIBWarps][NP * NV][KS + 1];
-  __shared__ double pstage[kIBWarps][NP * (D + 1)][KP + 1];
-  const int wib = threadIdx.x >> 5;
+  static_assert(NSLOT % kIBWarps == 0, "whole blocks per CTA");
+  __shared__ double stage[NSLOT][NP * NV][KS + 1];
+  __shared__ double pstage[NSLOT][NP * (D + 1)][KP + 1];
+  const int wsl = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int l0 = (blk * kIBWarps + wib) * NP;
+  const int l0 = (blk * kIBWarps + wsl % kIBWarps) * NP;
   if (l0 >= s.NL) return;
   // Eq. int2: every lane evaluates stencil slots of each of the warp's points
 #pragma unroll 1
@@ -507,7 +511,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
           }
         }
 #pragma unroll
-        for (int q = 0; q < NV; ++q) stage[wib][p * NV + q][k] = v[q];
+        for (int q = 0; q < NV; ++q) stage[wsl][p * NV + q][k] = v[q];
       }
     }
   }
@@ -530,7 +534,7 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
         pv[D] = T * w;
       }
 #pragma unroll
-      for (int q = 0; q < D + 1; ++q) pstage[wib][p * (D + 1) + q][k] = pv[q];
+      for (int q = 0; q < D + 1; ++q) pstage[wsl][p * (D + 1) + q][k] = pv[q];
     }
   }
   __syncwarp();
@@ -542,13 +546,13 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
     if (l0 + p < s.NL) {
       if (q < NV) {
         double a_ = 0.0;
-        for (int k = 0; k < KS; ++k) a_ = a_ + stage[wib][p * NV + q][k];
-        stage[wib][p * NV + q][0] = a_;
+        for (int k = 0; k < KS; ++k) a_ = a_ + stage[wsl][p * NV + q][k];
+        stage[wsl][p * NV + q][0] = a_;
       }
       if (q < D + 1) {
         double a_ = 0.0;
-        for (int k = 0; k < KP; ++k) a_ = a_ + pstage[wib][p * (D + 1) + q][k];
-        pstage[wib][p * (D + 1) + q][0] = a_;
+        for (int k = 0; k < KP; ++k) a_ = a_ + pstage[wsl][p * (D + 1) + q][k];
+        pstage[wsl][p * (D + 1) + q][0] = a_;
       }
     }
   }
@@ -559,9 +563,9 @@ __device__ __forceinline__ void ib_force_body(const Grid& g, const IBStepDev& s,
   if (l >= s.NL) return;
   double acc[NV], pacc[D + 1];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) acc[q] = stage[wib][pp * NV + q][0];
+  for (int q = 0; q < NV; ++q) acc[q] = stage[wsl][pp * NV + q][0];
 #pragma unroll
-  for (int q = 0; q < D + 1; ++q) pacc[q] = pstage[wib][pp * (D + 1) + q][0];
+  for (int q = 0; q < D + 1; ++q) pacc[q] = pstage[wsl][pp * (D + 1) + q][0];
   const double ph = s.phi[l];
   const double rho_s = ph * acc[0];
   double j_s[3], u_s[3], uP[3], uV[3];
@@ -682,10 +686,7 @@ struct SpreadCaseDesc {
 };
 
 template <class C>
-static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const int2* work) {
-  const int2 w = work[blockIdx.x];
-  const SpreadCaseDesc<C>& c = d[w.x];
-  const int r = w.y * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void spread_apply_row(const SpreadCaseDesc<C>& c, int r) {
   if (r >= c.n_rows) return;
   const int D = c.D;
   double acc[4];
@@ -700,6 +701,12 @@ static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const 
   for (int a = 0; a < 3; ++a)
     if (a < D) c.M[(1 + a) * N + n] = c.M[(1 + a) * N + n] + C(0.5) * C(acc[a]);
   c.M[(1 + D) * N + n] = c.M[(1 + D) * N + n] + C(acc[3]);
+}
+
+template <class C>
+static __global__ void k_spread_apply_batched(const SpreadCaseDesc<C>* d, const int2* work) {
+  const int2 w = work[blockIdx.x];
+  spread_apply_row<C>(d[w.x], w.y * blockDim.x + threadIdx.x);
 }
 
 // One case: spreading (Eq. spr2, the sums of spread_row) and its application to the

@@ -31,6 +31,7 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", 
            "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_get_wall_loads_async", "lbm_sync", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_case", "lbm_batch_step",
            "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
+           "lbm_batch_set_launch_form", "lbm_batch_get_launch_form",
            "lbm_batch_autotune", "lbm_save_state", "lbm_load_state", "lbm_create_slab", "lbm_slab_info",
            "lbm_slab_exchange_bytes", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_points",
            "lbm_slab_plan", "lbm_slab_keep", "lbm_refined_create", "lbm_refined_destroy",
@@ -81,6 +82,7 @@ def load():
     lib.lbm_batch_step_sequential.argtypes = [ct.c_void_p, ct.c_int]
     lib.lbm_batch_sync.argtypes = [ct.c_void_p]
     lib.lbm_batch_set_plan.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
+    lib.lbm_batch_set_launch_form.argtypes = [ct.c_void_p, ct.c_int]
     for name in ("lbm_step",):
         getattr(lib, name).argtypes = [ct.c_void_p, ct.c_int]
     for name in ("lbm_destroy", "lbm_check", "lbm_last_error", "lbm_launch_count"):
@@ -522,6 +524,16 @@ class Batch:
         tr, sc = ct.c_int(), ct.c_int()
         self._check(lib().lbm_batch_get_plan(self.b, ct.byref(tr), ct.byref(sc)))
         return tr.value, sc.value
+
+    def set_launch_form(self, form):
+        """1: one persistent cooperative launch per two steps (2D); 0: one
+        launch per phase."""
+        self._check(lib().lbm_batch_set_launch_form(self.b, int(form)))
+
+    def launch_form(self):
+        f = ct.c_int()
+        self._check(lib().lbm_batch_get_launch_form(self.b, ct.byref(f)))
+        return f.value
 
     def autotune(self, steps=10, cache_path=None):
         best = ct.c_double()

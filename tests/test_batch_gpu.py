@@ -1,6 +1,6 @@
-"""Batched stepping (several uneven cases in one fused launch, graph
-replay) gives the same states bit for bit as stepping each case alone; the
-autotuner leaves the state unchanged."""
+"""Batched stepping (several uneven cases in one persistent launch or in one
+launch per phase, graph replay) gives the same states bit for bit as
+stepping each case alone; the autotuner leaves the state unchanged."""
 import numpy as np
 import pytest
 
@@ -31,11 +31,14 @@ def _geometry(c, spec, theta):
     return inputs.cylinder(center, 2 * spec["a"], spec["n_points"], tbc=0, t_value=1.05 * theta)
 
 
+@pytest.mark.parametrize("form", [1, 0])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batched_equals_individual(precision):
+def test_batched_equals_individual(precision, form):
     from paper_2607_07432_b300 import lbmib
     cases, specs = _cases()
     b = lbmib.Batch("D2Q9", precision, cases)
+    assert b.launch_form() == 1    # 2D default: one persistent launch
+    b.set_launch_form(form)
     solo = []
     for k, c in enumerate(cases):
         s = lbmib.Solver("D2Q9", precision, c["shape"], mach=c["mach"], reynolds=c["reynolds"],
@@ -96,6 +99,9 @@ def test_batched_3d_equals_individual():
     geos = [lambda th: inputs.icosphere((12.3, 12.1, 11.8), 8.0, 4, tbc=0, t_value=1.05 * th),
             lambda th: inputs.icosphere((10.2, 9.7, 14.1), 7.0, 3, tbc=0, t_value=1.05 * th)]
     b = lbmib.Batch("D3Q19", "fp32", cases)
+    assert b.launch_form() == 0
+    with pytest.raises(lbmib.LBMError):
+        b.set_launch_form(1)
     solo = []
     for k, c in enumerate(cases):
         s = lbmib.Solver("D3Q19", "fp32", c["shape"], mach=c["mach"], reynolds=c["reynolds"],
