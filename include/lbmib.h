@@ -413,6 +413,13 @@ lbm_status lbm_batch_sync(lbm_batch* b);
  * once), 0 = one launch per phase.  LBM_EINVAL for form 1 on D3Q19. */
 lbm_status lbm_batch_set_launch_form(lbm_batch* b, int form);
 lbm_status lbm_batch_get_launch_form(const lbm_batch* b, int* form);
+/* Test aid for the failure path of form 1: sets the barrier's arrival count
+ * so that the next persistent launch cannot pass its first grid barrier;
+ * every CTA then waits out its limit and leaves, and the following
+ * lbm_batch_sync returns LBM_ETIMEOUT (and clears the barrier).  The cases
+ * are left part-way through a step.  LBM_EINVAL unless the form is 1.  No
+ * counterpart in the paper. */
+lbm_status lbm_batch_test_stall_barrier(lbm_batch* b);
 /* Fused-launch plan: tile_rows 0 (default tile), 16 or 32 (2D FP32 only), and
  * schedule 0 = case-major, 1 = round-robin over cases, 2 = largest first. */
 lbm_status lbm_batch_set_plan(lbm_batch* b, int tile_rows, int schedule);

@@ -196,6 +196,21 @@ lbm_status lbm_batch_set_launch_form(lbm_batch* b, int form) {
   return LBM_OK;
 }
 
+lbm_status lbm_batch_test_stall_barrier(lbm_batch* b) {
+  if (!b || b->plan.launch_form != 1) return LBM_EINVAL;
+  DeviceGuard dg(b->plan.cases[0]->cfg.device);
+  if (!plan_current(b)) {
+    lbm_status s = rebuild(b);
+    if (s) return s;
+  }
+  // an arrival count past any grid size: the next barrier cannot complete
+  const unsigned stuck = 0x40000000u;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess ||
+      cudaMemcpy(b->plan.bar, &stuck, sizeof(stuck), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bfail(b, LBM_ECUDA, "barrier state write");
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_get_launch_form(const lbm_batch* b, int* form) {
   if (!b || !form) return LBM_EINVAL;
   *form = b->plan.launch_form;

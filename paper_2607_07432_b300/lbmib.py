@@ -31,7 +31,7 @@ EXPORTS = ["lbm_config_default", "lbm_create", "lbm_destroy", "lbm_last_error", 
            "lbm_get_profile", "lbm_launch_count", "lbm_get_wall_loads_noalloc", "lbm_get_wall_loads_async", "lbm_sync", "lbm_batch_create",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_case", "lbm_batch_step",
            "lbm_batch_step_sequential", "lbm_batch_sync", "lbm_batch_set_plan", "lbm_batch_get_plan",
-           "lbm_batch_set_launch_form", "lbm_batch_get_launch_form",
+           "lbm_batch_set_launch_form", "lbm_batch_get_launch_form", "lbm_batch_test_stall_barrier",
            "lbm_batch_autotune", "lbm_save_state", "lbm_load_state", "lbm_create_slab", "lbm_slab_info",
            "lbm_slab_exchange_bytes", "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_points",
            "lbm_slab_plan", "lbm_slab_keep", "lbm_refined_create", "lbm_refined_destroy",
@@ -529,6 +529,10 @@ class Batch:
         """1: one persistent cooperative launch per two steps (2D); 0: one
         launch per phase."""
         self._check(lib().lbm_batch_set_launch_form(self.b, int(form)))
+
+    def test_stall_barrier(self):
+        """Failure-path test aid (see lbm_batch_test_stall_barrier)."""
+        self._check(lib().lbm_batch_test_stall_barrier(self.b))
 
     def launch_form(self):
         f = ct.c_int()

@@ -191,3 +191,26 @@ def test_batched_mixed_stencils_equal_individual():
         assert np.array_equal(fa, fb) and np.array_equal(Ea, Eb)
         s.close()
     b.close()
+
+
+def test_persistent_barrier_timeout_is_reported():
+    """A grid barrier that cannot complete (its arrival count set past the
+    grid size) ends the persistent launch after its bounded wait; the host
+    reads LBM_ETIMEOUT, and the batch steps again afterwards."""
+    from paper_2607_07432_b300 import lbmib
+    cases, specs = _cases()
+    b = lbmib.Batch("D2Q9", "fp32", cases[:2])
+    for k, c in enumerate(cases[:2]):
+        th = b.case(k).constants()["theta_inf"]
+        b.case(k).set_geometry(_geometry(c, specs[k], th))
+    b.step(2)
+    b.sync()
+    b.test_stall_barrier()
+    b.step(2)
+    with pytest.raises(lbmib.LBMError) as e:
+        b.sync()
+    assert e.value.status == 6 and "timed out" in str(e.value)     # LBM_ETIMEOUT
+    b.sync()          # the barrier was cleared
+    b.step(2)
+    b.sync()
+    b.close()
