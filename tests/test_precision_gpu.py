@@ -1,6 +1,8 @@
-"""Reduced-precision population storage (f_i - w_i in FP16 or BF16, FP32
-arithmetic, FP64 immersed-boundary sums) against the plain FP32 path on the
-2D cylinder case, and long-run stability of the 3D sphere workload."""
+"""Reduced-precision population storage (f_i minus the case's free-stream
+equilibrium in FP16 or BF16, FP32 arithmetic, FP64 immersed-boundary sums)
+against the plain FP32 path on the 2D cylinder case and against the FP64
+path on a 3D sphere downscale, and long-run stability of the 3D sphere
+workload."""
 import numpy as np
 import pytest
 
@@ -39,12 +41,14 @@ def test_fp16_drag_and_heat_within_0p1_percent(cylinder_runs):
     assert _rel(r16["Nu"], r32["Nu"]) < 1e-3
 
 
-def test_bf16_drag_and_heat_within_1_percent(cylinder_runs):
-    """BF16 (8-bit mantissa) storage: within 1% of FP32 (its rounding of the
-    populations, 2^-9 relative, is above the 0.1% bar's budget)."""
+def test_bf16_drag_and_heat_within_0p1_percent(cylinder_runs):
+    """BF16 (8-bit mantissa) storage: steady drag and Nusselt number within
+    0.1% of FP32 (measured 6e-5 and 9e-5: the stored deviations from the
+    free-stream equilibrium are small wherever the flow is near the free
+    stream)."""
     r32, rb = cylinder_runs["fp32"], cylinder_runs["bf16"]
-    assert _rel(rb["Cd"], r32["Cd"]) < 1e-2
-    assert _rel(rb["Nu"], r32["Nu"]) < 1e-2
+    assert _rel(rb["Cd"], r32["Cd"]) < 1e-3
+    assert _rel(rb["Nu"], r32["Nu"]) < 1e-3
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
@@ -96,8 +100,12 @@ def test_sphere_fp32_and_fp16_means_within_0p1_percent_of_fp64(sphere_means):
     assert m["fp64"]["Cd"] > 0 and m["fp64"]["Nu"] > 0
 
 
-def test_sphere_bf16_means_within_1_percent_of_fp64(sphere_means):
-    """BF16 storage: drag and Nusselt running means within 1% of FP64."""
+def test_sphere_downscale_bf16_nusselt_within_0p1_percent_drag_misses_it(sphere_means):
+    """BF16 storage on this downscale (D = 8, where the body's neighbourhood
+    is a large share of the flow): the Nusselt running mean within 0.1% of
+    FP64 (measured 6e-4), the drag mean NOT within 0.1% (measured 1.4e-3;
+    held to 0.3% here).  On the full 256x192x192 grid both are within 0.1%
+    of FP32 (the precision study of the sphere workload)."""
     m = sphere_means
-    assert _rel(m["bf16"]["Cd"], m["fp64"]["Cd"]) < 1e-2
-    assert _rel(m["bf16"]["Nu"], m["fp64"]["Nu"]) < 1e-2
+    assert _rel(m["bf16"]["Nu"], m["fp64"]["Nu"]) < 1e-3
+    assert _rel(m["bf16"]["Cd"], m["fp64"]["Cd"]) < 3e-3
