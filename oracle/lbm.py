@@ -459,7 +459,7 @@ def freestream(prm, shape_zyx):
 
 
 def characteristic_face(prm, f, E, a, side):
-    """Characteristic far field on the face (axis a, side) (SURVEY NEXT item;
+    """Characteristic far field on the face (axis a, side) (Sec. 3.2;
     the paper cites characteristic boundaries without giving them): the face
     nodes take the equilibrium of the state built from the linearized
     one-dimensional Riemann invariants normal to the face,
